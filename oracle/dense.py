@@ -1,0 +1,100 @@
+"""Dense-matrix second oracle for small meshes (<= ~512 cells) -- TEST INFRASTRUCTURE ONLY.
+
+Independent of ``sweep_oracle.c``: it assembles the discretised transport system
+of the paper's Sec. 2.6 transport scheme (a) as an explicit matrix from the face
+list and solves it with LU (numpy.linalg.solve), with no ordering, no queue and
+no iteration. For one direction Omega (paper Sec. 2.3: ordering the cells makes
+this matrix lower triangular; here it is simply solved):
+
+    row c:  (P_c + kappa_t,c V_c) I_c  -  sum_{faces f with inflow into c} |a_f| I_other(f)  =  q_c (+ boundary inflow)
+    a_f = A_f n_f . Omega,  P_c = sum over faces with outward n.Omega > 0 of |a_f|
+
+Periodic faces enter as ordinary couplings to the partner cell, so the matrix is
+cyclic and its solution is the fixed point the periodic iteration of Sec. 2.7
+converges to. Isotropic scattering couples the directions through
+q_c = eps_c/4pi + kappa_s,c V_c (1/4pi) sum_d' w_d' I_c,d' (Alg. 1's fixed point).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+FACE_BOUNDARY = 1
+FACE_PERIODIC = 2
+
+
+def _dot(n, om):
+    # same rounding order as the classification: ((x) + (y)) + (z)
+    return (n[..., 0] * om[0] + n[..., 1] * om[1]) + n[..., 2] * om[2]
+
+
+def transport_matrix(mesh, om, kappa_t, bc_inflow=None, group=0, periodic_coupling=True):
+    """Matrix L (N x N) and boundary right-hand side b (N) for one direction and group."""
+    N = mesh.n_cells
+    L = np.zeros((N, N))
+    b = np.zeros(N)
+    t = _dot(mesh.normal, om)
+    a = mesh.area * np.abs(t)
+    bidx = np.cumsum((mesh.flags & FACE_BOUNDARY) != 0) - 1
+    for f in range(mesh.n_faces):
+        c0, c1 = int(mesh.face_cells[f, 0]), int(mesh.face_cells[f, 1])
+        if t[f] == 0.0:
+            continue
+        if mesh.flags[f] & FACE_BOUNDARY:
+            if t[f] > 0:
+                L[c0, c0] += a[f]
+            elif bc_inflow is not None:
+                b[c0] += a[f] * bc_inflow[bidx[f], group]
+            continue
+        up, down = (c0, c1) if t[f] > 0 else (c1, c0)
+        L[up, up] += a[f]                      # outflow of the upwind cell
+        if (mesh.flags[f] & FACE_PERIODIC) and not periodic_coupling:
+            continue
+        L[down, up] -= a[f]                    # inflow of the downwind cell
+    L[np.arange(N), np.arange(N)] += kappa_t[:, group] * mesh.volume
+    return L, b
+
+
+def solve_direction(mesh, om, kappa_abs, emissivity, kappa_scat=None, bc_inflow=None):
+    """I[N,G] for one direction with scattering treated as absent."""
+    kt = kappa_abs + (0.0 if kappa_scat is None else kappa_scat)
+    G = kappa_abs.shape[1]
+    I = np.zeros((mesh.n_cells, G))
+    for g in range(G):
+        L, b = transport_matrix(mesh, om, kt, bc_inflow, g)
+        I[:, g] = np.linalg.solve(L, emissivity[:, g] / (4 * math.pi) + b)
+    return I
+
+
+def solve_coupled(mesh, omega, weight, kappa_abs, emissivity, kappa_scat=None, bc_inflow=None):
+    """All directions at once with isotropic scattering coupling; returns I[D,N,G], J[N,G], Gamma[N,G]."""
+    D, N = omega.shape[0], mesh.n_cells
+    G = kappa_abs.shape[1]
+    ks = np.zeros_like(kappa_abs) if kappa_scat is None else kappa_scat
+    kt = kappa_abs + ks
+    I = np.zeros((D, N, G))
+    for g in range(G):
+        A = np.zeros((D * N, D * N))
+        rhs = np.zeros(D * N)
+        for d in range(D):
+            L, b = transport_matrix(mesh, omega[d], kt, bc_inflow, g)
+            A[d * N:(d + 1) * N, d * N:(d + 1) * N] = L
+            rhs[d * N:(d + 1) * N] = emissivity[:, g] / (4 * math.pi) + b
+            for d2 in range(D):
+                idx = np.arange(N)
+                A[d * N + idx, d2 * N + idx] -= ks[:, g] * mesh.volume * weight[d2] / (4 * math.pi)
+        I[:, :, g] = np.linalg.solve(A, rhs).reshape(D, N)
+    J = np.einsum("d,dng->ng", weight, I) / (4 * math.pi)
+    Gam = kappa_abs * mesh.volume[:, None] * 4 * math.pi * J
+    return I, J, Gam
+
+
+def adjoint_direction(mesh, om, kappa_abs, g_src):
+    """lambda[N,G] solving L^T lambda = g for one direction (no scattering, no periodic faces)."""
+    G = kappa_abs.shape[1]
+    lam = np.zeros((mesh.n_cells, G))
+    for g in range(G):
+        L, _ = transport_matrix(mesh, om, kappa_abs, None, g)
+        lam[:, g] = np.linalg.solve(L.T, g_src[:, g])
+    return lam

@@ -1,0 +1,581 @@
+/*
+ * sweep_oracle.c -- plain, slow FP64 CPU oracle of the discrete-ordinates transport
+ * sweep (Peter et al. 2022, "The Sweep Method for radiative transfer in Arepo").
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the reference the CUDA path is checked
+ * against. Only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark may load it; the product path never calls it. It shares no code,
+ * header or constant with the CUDA library.
+ *
+ * Build with -ffp-contract=off: every dot product is ((x*x') + (y*y')) + (z*z')
+ * with separately rounded products, so classification signs are reproducible.
+ *
+ * What it computes, step by step, in the paper's order:
+ *   O1 classify   -- a neighbour is downwind when n.Omega > 0 (Sec. 2.5; Appendix A,
+ *                    Eq. downwindDefinition). An exact zero is neither upwind nor
+ *                    downwind and carries no flux (reading of the "upwind otherwise"
+ *                    rule that keeps the dependency graph acyclic).
+ *   O2 count+Kahn -- Alg. 2 (single-core sweep): count upwind fluxes n(c,Omega),
+ *                    queue the tasks with n = 0, solve, decrement downwind counts.
+ *                    The level of a cell is 0 without upwind cells, else
+ *                    1 + max(level of upwind cells) (longest path, Sec. 2.3).
+ *   O3 cell update-- transport scheme (a) of Sec. 2.6 (Eq. for F_i): the total
+ *                    outflow F leaves through downwind face i in proportion to
+ *                    A_i (n_i.Omega). Written as a cell balance,
+ *                      (P_c + kappa_t V) I_c = q_c + sum_in |a_f| I_up(f),
+ *                    a_f = A_f n_f.Omega, P_c = sum over outflow faces of a_f,
+ *                    q_c = eps_c/(4 pi) + kappa_s V J_c  (Eq. radiativeTransfer
+ *                    discretised with isotropic emission and scattering).
+ *   O4 tallies    -- J = (1/4pi) sum_d w_d I_d; absorbed rate
+ *                    Gamma = kappa_a V sum_d w_d I_d (photon rate R of Sec. 3.2 up to
+ *                    the 13.6 eV factor); escaped and injected boundary fluxes.
+ *   O5 scattering -- Alg. 1 (source iteration) with I^0 = 0; stop when the relative
+ *                    change of J is below tol in every cell (Sec. 2.3 criterion,
+ *                    applied to the mean intensity).
+ *   O6 periodic   -- Sec. 2.7: flux leaving through a periodic face enters the
+ *                    partner cell as a source in the next sweep; stop when
+ *                    max_i |E_i| < tol, E_i = (j^n - j^(n-1)) / (j^n + j^(n-1))
+ *                    (Eq. relativeErrorPbc) or after max_it sweeps.
+ *   O7 nesting    -- periodic iteration outside, source iteration inside
+ *                    (cost n_pbc * n_scat, Sec. 2.7).
+ *   O9 adjoint    -- transpose of the O3 system per direction, solved as a sweep in
+ *                    reversed topological order; gradients of a loss of J and Gamma
+ *                    with respect to kappa_a and eps.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define FOURPI (4.0 * 3.14159265358979323846)
+
+enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_CYCLE = 2, OR_NOT_CONVERGED = 3, OR_ERR_MEM = 5 };
+enum { OR_FACE_BOUNDARY = 1, OR_FACE_PERIODIC = 2 };
+
+typedef struct {
+    /* problem (caller-owned) */
+    int64_t n_cells, n_faces;
+    const double* volume;
+    const int32_t* face_cells; /* [F][2] */
+    const double* area;
+    const double* normal; /* [F][3] */
+    const uint8_t* flags;
+    int32_t n_dir;
+    const double* omega; /* [D][3] */
+    const double* weight;
+    int32_t n_groups;
+    const double* kappa_abs;  /* [N][G] */
+    const double* kappa_scat; /* [N][G] or NULL */
+    const double* emissivity; /* [N][G] */
+    const double* bc_inflow;  /* [n_boundary_faces][G] or NULL */
+    /* derived: per-cell list of face sides */
+    int64_t* side_start; /* [N+1] */
+    int64_t* side_face;  /* face index */
+    int8_t* side_sign;   /* +1 if the cell is c0 (outward normal = n), -1 if c1 */
+    int64_t* bc_index;   /* [F] boundary face ordinal, -1 otherwise */
+} problem;
+
+/* O1: the classification dot product, fixed order, no fused multiply-add */
+static double face_dot(const double* n, const double* om) {
+    double x = n[0] * om[0];
+    double y = n[1] * om[1];
+    double z = n[2] * om[2];
+    return (x + y) + z;
+}
+
+static int build_sides(problem* p) {
+    int64_t N = p->n_cells, F = p->n_faces;
+    p->side_start = (int64_t*)calloc((size_t)N + 1, sizeof(int64_t));
+    p->bc_index = (int64_t*)malloc(sizeof(int64_t) * (size_t)(F > 0 ? F : 1));
+    if (!p->side_start || !p->bc_index) return OR_ERR_MEM;
+    int64_t nb = 0;
+    for (int64_t f = 0; f < F; ++f) {
+        int32_t c0 = p->face_cells[2 * f], c1 = p->face_cells[2 * f + 1];
+        p->side_start[c0 + 1]++;
+        if (c1 >= 0) p->side_start[c1 + 1]++;
+        p->bc_index[f] = (p->flags[f] & OR_FACE_BOUNDARY) ? nb++ : -1;
+    }
+    for (int64_t c = 0; c < N; ++c) p->side_start[c + 1] += p->side_start[c];
+    int64_t S = p->side_start[N];
+    p->side_face = (int64_t*)malloc(sizeof(int64_t) * (size_t)(S > 0 ? S : 1));
+    p->side_sign = (int8_t*)malloc((size_t)(S > 0 ? S : 1));
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    if (!p->side_face || !p->side_sign || !fill) { free(fill); return OR_ERR_MEM; }
+    for (int64_t c = 0; c < N; ++c) fill[c] = p->side_start[c];
+    for (int64_t f = 0; f < F; ++f) {
+        int32_t c0 = p->face_cells[2 * f], c1 = p->face_cells[2 * f + 1];
+        p->side_face[fill[c0]] = f;
+        p->side_sign[fill[c0]++] = 1;
+        if (c1 >= 0) {
+            p->side_face[fill[c1]] = f;
+            p->side_sign[fill[c1]++] = -1;
+        }
+    }
+    free(fill);
+    return OR_OK;
+}
+
+static void free_sides(problem* p) {
+    free(p->side_start);
+    free(p->side_face);
+    free(p->side_sign);
+    free(p->bc_index);
+}
+
+/* cell on the other side of a face side (interior or periodic partner) */
+static int32_t other_cell(const problem* p, int64_t f, int sign) {
+    return sign > 0 ? p->face_cells[2 * f + 1] : p->face_cells[2 * f];
+}
+
+/*
+ * Alg. 2 for one direction: the Kahn task queue over cells, with levels.
+ * t[f] = n_f . Omega for every face. Returns OR_ERR_CYCLE if tasks remain.
+ * If solve != 0 the O3 update is applied to each task as it is dequeued:
+ *   forward (reverse = 0): inflow faces have outward t < 0, upwind = across them;
+ *   adjoint (reverse = 1): the transposed system; "inflow" is the outflow side.
+ */
+typedef struct {
+    const problem* p;
+    const double* t;   /* [F] */
+    int reverse;
+    const double* src; /* [N][G] source q (forward) or adjoint source g */
+    const double* prev; /* [N][G] previous-sweep intensity for periodic inflow, or NULL */
+    double* out;       /* [N][G] solution */
+    int32_t* level;    /* [N] or NULL */
+    int32_t* depth;
+    /* scratch */
+    int32_t* count;
+    int64_t* queue;
+} dir_sweep;
+
+static int sweep_one(dir_sweep* s, int solve) {
+    const problem* p = s->p;
+    int64_t N = p->n_cells;
+    int G = p->n_groups;
+    /* count upwind fluxes n(c, Omega) over interior, non-periodic faces */
+    for (int64_t c = 0; c < N; ++c) s->count[c] = 0;
+    for (int64_t f = 0; f < p->n_faces; ++f) {
+        if (p->flags[f] & (OR_FACE_BOUNDARY | OR_FACE_PERIODIC)) continue;
+        double t = s->t[f];
+        if (s->reverse) t = -t;
+        if (t > 0.0) s->count[p->face_cells[2 * f + 1]]++;
+        else if (t < 0.0) s->count[p->face_cells[2 * f]]++;
+    }
+    int64_t head = 0, tail = 0;
+    for (int64_t c = 0; c < N; ++c) {
+        if (s->level) s->level[c] = 0;
+        if (s->count[c] == 0) s->queue[tail++] = c;
+    }
+    int32_t maxlev = -1;
+    while (head < tail) {
+        int64_t c = s->queue[head++];
+        if (s->level && s->level[c] > maxlev) maxlev = s->level[c];
+        if (solve) {
+            double P = 0.0;
+            double acc[64];
+            for (int g = 0; g < G; ++g) acc[g] = s->src[c * G + g];
+            for (int64_t k = p->side_start[c]; k < p->side_start[c + 1]; ++k) {
+                int64_t f = p->side_face[k];
+                int sign = p->side_sign[k];
+                double tout = sign > 0 ? s->t[f] : -s->t[f]; /* n_outward . Omega */
+                double a = p->area[f] * fabs(tout);
+                int inflow = s->reverse ? (tout > 0.0) : (tout < 0.0);
+                if (tout > 0.0) P += a; /* P_c: projected outflow area (both directions) */
+                if (!inflow || tout == 0.0) continue;
+                uint8_t fl = p->flags[f];
+                if (fl & OR_FACE_BOUNDARY) {
+                    if (!s->reverse && p->bc_inflow) {
+                        int64_t b = p->bc_index[f];
+                        for (int g = 0; g < G; ++g) acc[g] += a * p->bc_inflow[b * G + g];
+                    }
+                } else if (fl & OR_FACE_PERIODIC) {
+                    if (!s->reverse && s->prev) {
+                        int32_t up = other_cell(p, f, sign);
+                        for (int g = 0; g < G; ++g) acc[g] += a * s->prev[(int64_t)up * G + g];
+                    }
+                } else {
+                    int32_t up = other_cell(p, f, sign);
+                    for (int g = 0; g < G; ++g) acc[g] += a * s->out[(int64_t)up * G + g];
+                }
+            }
+            for (int g = 0; g < G; ++g) {
+                double kt = p->kappa_abs[c * G + g] + (p->kappa_scat ? p->kappa_scat[c * G + g] : 0.0);
+                s->out[c * G + g] = acc[g] / (P + kt * p->volume[c]);
+            }
+        }
+        /* release the downwind tasks */
+        for (int64_t k = p->side_start[c]; k < p->side_start[c + 1]; ++k) {
+            int64_t f = p->side_face[k];
+            if (p->flags[f] & (OR_FACE_BOUNDARY | OR_FACE_PERIODIC)) continue;
+            int sign = p->side_sign[k];
+            double tout = sign > 0 ? s->t[f] : -s->t[f];
+            if (s->reverse) tout = -tout;
+            if (tout > 0.0) {
+                int32_t d = other_cell(p, f, sign);
+                if (s->level && s->level[d] < s->level[c] + 1) s->level[d] = s->level[c] + 1;
+                if (--s->count[d] == 0) s->queue[tail++] = d;
+            }
+        }
+    }
+    if (s->depth) *s->depth = maxlev + 1;
+    return tail == N ? OR_OK : OR_ERR_CYCLE;
+}
+
+static void classify(const problem* p, int32_t d, double* t) {
+    for (int64_t f = 0; f < p->n_faces; ++f) t[f] = face_dot(p->normal + 3 * f, p->omega + 3 * d);
+}
+
+/* --------------------------------------------------------------------------------------------- */
+/* threads over directions */
+typedef struct {
+    const problem* p;
+    int32_t d0, d1;
+    int reverse;
+    const double* src;    /* [N][G] (shared by all directions) or per-direction if src_stride */
+    int64_t src_stride;   /* elements between directions' sources (0 = shared) */
+    const double* prev;   /* [D][N][G] or NULL */
+    double* out;          /* [D][N][G] */
+    int32_t* level;       /* [D][N] or NULL */
+    int32_t* depth;       /* [D] */
+    int solve;
+    int status;
+} job;
+
+static void* run_job(void* arg) {
+    job* j = (job*)arg;
+    const problem* p = j->p;
+    int64_t N = p->n_cells, G = p->n_groups;
+    double* t = (double*)malloc(sizeof(double) * (size_t)(p->n_faces > 0 ? p->n_faces : 1));
+    int32_t* count = (int32_t*)malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+    int64_t* queue = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    int32_t* lev = (int32_t*)malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+    j->status = OR_OK;
+    if (!t || !count || !queue || !lev) { j->status = OR_ERR_MEM; goto done; }
+    for (int32_t d = j->d0; d < j->d1; ++d) {
+        classify(p, d, t);
+        dir_sweep s;
+        s.p = p;
+        s.t = t;
+        s.reverse = j->reverse;
+        s.src = j->src ? j->src + (int64_t)d * j->src_stride : NULL;
+        s.prev = j->prev ? j->prev + (int64_t)d * N * G : NULL;
+        s.out = j->out ? j->out + (int64_t)d * N * G : NULL;
+        s.level = j->level ? j->level + (int64_t)d * N : lev;
+        s.depth = j->depth ? j->depth + d : NULL;
+        s.count = count;
+        s.queue = queue;
+        int rc = sweep_one(&s, j->solve);
+        if (rc != OR_OK) { j->status = rc; break; }
+    }
+done:
+    free(t);
+    free(count);
+    free(queue);
+    free(lev);
+    return NULL;
+}
+
+static int run_dirs(const problem* p, int n_threads, int reverse, const double* src, int64_t src_stride,
+                    const double* prev, double* out, int32_t* level, int32_t* depth, int solve) {
+    int32_t D = p->n_dir;
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > D) n_threads = D > 0 ? D : 1;
+    job* jobs = (job*)calloc((size_t)n_threads, sizeof(job));
+    pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
+    if (!jobs || !th) { free(jobs); free(th); return OR_ERR_MEM; }
+    for (int i = 0; i < n_threads; ++i) {
+        jobs[i].p = p;
+        jobs[i].d0 = (int32_t)((int64_t)D * i / n_threads);
+        jobs[i].d1 = (int32_t)((int64_t)D * (i + 1) / n_threads);
+        jobs[i].reverse = reverse;
+        jobs[i].src = src;
+        jobs[i].src_stride = src_stride;
+        jobs[i].prev = prev;
+        jobs[i].out = out;
+        jobs[i].level = level;
+        jobs[i].depth = depth;
+        jobs[i].solve = solve;
+    }
+    if (n_threads == 1) run_job(&jobs[0]);
+    else {
+        for (int i = 0; i < n_threads; ++i) pthread_create(&th[i], NULL, run_job, &jobs[i]);
+        for (int i = 0; i < n_threads; ++i) pthread_join(th[i], NULL);
+    }
+    int rc = OR_OK;
+    for (int i = 0; i < n_threads; ++i)
+        if (jobs[i].status != OR_OK) rc = jobs[i].status;
+    free(jobs);
+    free(th);
+    return rc;
+}
+
+static int check_problem(const problem* p) {
+    if (p->n_cells < 0 || p->n_faces < 0 || p->n_dir < 1 || p->n_groups < 1 || p->n_groups > 64) return OR_ERR_ARG;
+    for (int64_t f = 0; f < p->n_faces; ++f) {
+        int32_t c0 = p->face_cells[2 * f], c1 = p->face_cells[2 * f + 1];
+        if (c0 < 0 || c0 >= p->n_cells || c1 >= p->n_cells) return OR_ERR_ARG;
+        if (c1 < 0 && !(p->flags[f] & OR_FACE_BOUNDARY)) return OR_ERR_ARG;
+        if (c1 >= 0 && (p->flags[f] & OR_FACE_BOUNDARY)) return OR_ERR_ARG;
+    }
+    return OR_OK;
+}
+
+/* --------------------------------------------------------------------------------------------- */
+/* public entry points (loaded with ctypes by the tests) */
+
+/* O1+O2: levels[d][c] and depth[d] for every direction; OR_ERR_CYCLE if a graph is cyclic. */
+int oracle_levels(int64_t n_cells, int64_t n_faces, const double* volume, const int32_t* face_cells,
+                  const double* area, const double* normal, const uint8_t* flags, int32_t n_dir,
+                  const double* omega, int32_t* level, int32_t* depth, int n_threads) {
+    problem p;
+    memset(&p, 0, sizeof p);
+    p.n_cells = n_cells; p.n_faces = n_faces; p.volume = volume; p.face_cells = face_cells;
+    p.area = area; p.normal = normal; p.flags = flags; p.n_dir = n_dir; p.omega = omega; p.n_groups = 1;
+    int rc = check_problem(&p);
+    if (rc != OR_OK) return rc;
+    rc = build_sides(&p);
+    if (rc == OR_OK) rc = run_dirs(&p, n_threads, 0, NULL, 0, NULL, NULL, level, depth, 0);
+    free_sides(&p);
+    return rc;
+}
+
+typedef struct {
+    int32_t it_scat, it_pbc;
+    double res_scat, res_pbc, res_pbc_mean;
+    double emitted, injected, absorbed, escaped, defect;
+} oracle_stats;
+
+/* per cell and group: (1/4pi) sum_d w_d I_d */
+static void mean_intensity(const problem* p, const double* I, double* J) {
+    int64_t N = p->n_cells, G = p->n_groups;
+    for (int64_t i = 0; i < N * G; ++i) J[i] = 0.0;
+    for (int32_t d = 0; d < p->n_dir; ++d)
+        for (int64_t i = 0; i < N * G; ++i) J[i] += p->weight[d] * I[(int64_t)d * N * G + i];
+    for (int64_t i = 0; i < N * G; ++i) J[i] /= FOURPI;
+}
+
+/* j_c: sum_d w_d sum over periodic inflow faces of c of |a_f| I_prev[partner] */
+static void periodic_source(const problem* p, const double* I, double* j) {
+    int64_t N = p->n_cells, G = p->n_groups;
+    for (int64_t i = 0; i < N * G; ++i) j[i] = 0.0;
+    for (int32_t d = 0; d < p->n_dir; ++d) {
+        const double* om = p->omega + 3 * d;
+        for (int64_t f = 0; f < p->n_faces; ++f) {
+            if (!(p->flags[f] & OR_FACE_PERIODIC)) continue;
+            double t = face_dot(p->normal + 3 * f, om);
+            if (t == 0.0) continue;
+            int32_t c0 = p->face_cells[2 * f], c1 = p->face_cells[2 * f + 1];
+            int32_t down = t > 0.0 ? c1 : c0, up = t > 0.0 ? c0 : c1;
+            double a = p->area[f] * fabs(t);
+            for (int g = 0; g < G; ++g)
+                j[(int64_t)down * G + g] += p->weight[d] * a * I[(int64_t)d * N * G + (int64_t)up * G + g];
+        }
+    }
+}
+
+static void tallies(const problem* p, const double* I, double* J, double* Gam, oracle_stats* st) {
+    int64_t N = p->n_cells, G = p->n_groups;
+    mean_intensity(p, I, J);
+    double emitted = 0.0, absorbed = 0.0, escaped = 0.0, injected = 0.0, wsum = 0.0;
+    for (int32_t d = 0; d < p->n_dir; ++d) wsum += p->weight[d];
+    for (int64_t c = 0; c < N; ++c)
+        for (int g = 0; g < G; ++g) {
+            double ka = p->kappa_abs[c * G + g];
+            Gam[c * G + g] = ka * p->volume[c] * FOURPI * J[c * G + g];
+            absorbed += Gam[c * G + g];
+            emitted += p->emissivity[c * G + g] * wsum / FOURPI;
+        }
+    for (int32_t d = 0; d < p->n_dir; ++d) {
+        const double* om = p->omega + 3 * d;
+        for (int64_t f = 0; f < p->n_faces; ++f) {
+            if (!(p->flags[f] & OR_FACE_BOUNDARY)) continue;
+            double t = face_dot(p->normal + 3 * f, om);
+            double a = p->area[f] * fabs(t);
+            int32_t c = p->face_cells[2 * f];
+            for (int g = 0; g < G; ++g) {
+                if (t > 0.0) escaped += p->weight[d] * a * I[(int64_t)d * N * G + (int64_t)c * G + g];
+                else if (t < 0.0 && p->bc_inflow) injected += p->weight[d] * a * p->bc_inflow[p->bc_index[f] * G + g];
+            }
+        }
+    }
+    st->emitted = emitted;
+    st->injected = injected;
+    st->absorbed = absorbed;
+    st->escaped = escaped;
+    double in = emitted + injected;
+    st->defect = in > 0.0 ? (in - absorbed - escaped) / in : 0.0;
+}
+
+/* relative change of the mean intensity, max over cells (0/0 counts as converged) */
+static double scat_residual(int64_t n, const double* Jnew, const double* Jold) {
+    double r = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double dj = fabs(Jnew[i] - Jold[i]);
+        double e;
+        if (dj == 0.0) e = 0.0;
+        else if (Jnew[i] > 0.0) e = dj / Jnew[i];
+        else e = INFINITY;
+        if (e > r) r = e;
+    }
+    return r;
+}
+
+/*
+ * Full solve (O3-O7). Outputs J, Gamma [N][G]; optionally every intensity I_out [D][N][G]
+ * (final sweep). prev_init [D][N][G] seeds the periodic inflow (warm start) or NULL.
+ * Returns OR_OK, OR_NOT_CONVERGED (outputs still written), or an error.
+ */
+int oracle_solve(int64_t n_cells, int64_t n_faces, const double* volume, const int32_t* face_cells,
+                 const double* area, const double* normal, const uint8_t* flags, int32_t n_dir,
+                 const double* omega, const double* weight, int32_t n_groups, const double* kappa_abs,
+                 const double* kappa_scat, const double* emissivity, const double* bc_inflow, double tol_scat,
+                 int32_t max_it_scat, double tol_pbc, int32_t max_it_pbc, const double* prev_init,
+                 int n_threads, double* J, double* Gam, double* I_out, oracle_stats* st) {
+    problem p;
+    memset(&p, 0, sizeof p);
+    p.n_cells = n_cells; p.n_faces = n_faces; p.volume = volume; p.face_cells = face_cells;
+    p.area = area; p.normal = normal; p.flags = flags; p.n_dir = n_dir; p.omega = omega;
+    p.weight = weight; p.n_groups = n_groups; p.kappa_abs = kappa_abs; p.kappa_scat = kappa_scat;
+    p.emissivity = emissivity; p.bc_inflow = bc_inflow;
+    memset(st, 0, sizeof *st);
+    int rc = check_problem(&p);
+    if (rc != OR_OK) return rc;
+    rc = build_sides(&p);
+    if (rc != OR_OK) { free_sides(&p); return rc; }
+    int64_t N = n_cells, G = n_groups, NG = N * G, D = n_dir;
+    int has_scat = 0, has_pbc = 0;
+    if (kappa_scat)
+        for (int64_t i = 0; i < NG; ++i)
+            if (kappa_scat[i] != 0.0) { has_scat = 1; break; }
+    for (int64_t f = 0; f < n_faces; ++f)
+        if (flags[f] & OR_FACE_PERIODIC) { has_pbc = 1; break; }
+    double* I = (double*)calloc((size_t)(D * NG > 0 ? D * NG : 1), sizeof(double));
+    double* Iprev = (double*)calloc((size_t)(D * NG > 0 ? D * NG : 1), sizeof(double));
+    double* q = (double*)malloc(sizeof(double) * (size_t)(NG > 0 ? NG : 1));
+    double* Jold = (double*)calloc((size_t)(NG > 0 ? NG : 1), sizeof(double));
+    double* jn = (double*)calloc((size_t)(NG > 0 ? NG : 1), sizeof(double));
+    double* jn1 = (double*)calloc((size_t)(NG > 0 ? NG : 1), sizeof(double));
+    if (!I || !Iprev || !q || !Jold || !jn || !jn1) { rc = OR_ERR_MEM; goto out; }
+    if (has_pbc && prev_init) memcpy(Iprev, prev_init, sizeof(double) * (size_t)(D * NG));
+    if (has_pbc) periodic_source(&p, Iprev, jn);
+    int conv_pbc = !has_pbc, conv_scat = !has_scat;
+    int it_pbc = 0, it_scat_total = 0;
+    double res_pbc = 0.0, res_pbc_mean = 0.0, res_scat = 0.0;
+    for (;;) {
+        /* O5: source iteration with the periodic inflow Iprev held fixed */
+        for (int64_t i = 0; i < NG; ++i) Jold[i] = 0.0;
+        int it_scat = 0;
+        for (;;) {
+            for (int64_t c = 0; c < N; ++c)
+                for (int g = 0; g < G; ++g) {
+                    double ks = kappa_scat ? kappa_scat[c * G + g] : 0.0;
+                    q[c * G + g] = emissivity[c * G + g] / FOURPI + ks * volume[c] * Jold[c * G + g];
+                }
+            rc = run_dirs(&p, n_threads, 0, q, 0, has_pbc ? Iprev : NULL, I, NULL, NULL, 1);
+            if (rc != OR_OK) goto out;
+            ++it_scat;
+            mean_intensity(&p, I, J);
+            if (!has_scat) break;
+            res_scat = scat_residual(NG, J, Jold);
+            memcpy(Jold, J, sizeof(double) * (size_t)NG);
+            if (res_scat <= tol_scat) { conv_scat = 1; break; }
+            if (it_scat >= max_it_scat) { conv_scat = 0; break; }
+        }
+        it_scat_total += it_scat;
+        ++it_pbc;
+        if (!has_pbc) break;
+        /* O6: sources for the next sweep and their relative change */
+        periodic_source(&p, I, jn1);
+        double emax = 0.0, esum = 0.0;
+        for (int64_t i = 0; i < NG; ++i) {
+            double s = jn1[i] + jn[i];
+            double e = s > 0.0 ? fabs(jn1[i] - jn[i]) / s : 0.0;
+            if (e > emax) emax = e;
+            esum += e;
+        }
+        res_pbc = emax;
+        res_pbc_mean = NG > 0 ? esum / (double)NG : 0.0;
+        memcpy(jn, jn1, sizeof(double) * (size_t)NG);
+        memcpy(Iprev, I, sizeof(double) * (size_t)(D * NG));
+        if (res_pbc < tol_pbc) { conv_pbc = 1; break; }
+        if (it_pbc >= max_it_pbc) { conv_pbc = 0; break; }
+    }
+    tallies(&p, I, J, Gam, st);
+    st->it_scat = it_scat_total;
+    st->it_pbc = it_pbc;
+    st->res_scat = res_scat;
+    st->res_pbc = res_pbc;
+    st->res_pbc_mean = res_pbc_mean;
+    if (I_out) memcpy(I_out, I, sizeof(double) * (size_t)(D * NG));
+    rc = (conv_pbc && conv_scat) ? OR_OK : OR_NOT_CONVERGED;
+out:
+    free(I); free(Iprev); free(q); free(Jold); free(jn); free(jn1);
+    free_sides(&p);
+    return rc;
+}
+
+/*
+ * O9: adjoint of a loss L(J, Gamma) for problems without scattering and without
+ * periodic faces. dl_dJ, dl_dGamma [N][G] (either may be NULL = 0). Outputs
+ * grad_kappa_abs, grad_emissivity [N][G]. For each direction d:
+ *   g_{d,c} = w_d (dl_dGamma_c kappa_a,c V_c + dl_dJ_c / 4pi)        (dL/dI_{c,d})
+ *   L_d^T lambda_d = g_d, swept in reversed topological order
+ *   dL/dkappa_a,c += V_c I_{c,d} (w_d dl_dGamma_c - lambda_{d,c})
+ *   dL/deps_c     += lambda_{d,c} / 4pi
+ */
+int oracle_adjoint(int64_t n_cells, int64_t n_faces, const double* volume, const int32_t* face_cells,
+                   const double* area, const double* normal, const uint8_t* flags, int32_t n_dir,
+                   const double* omega, const double* weight, int32_t n_groups, const double* kappa_abs,
+                   const double* emissivity, const double* bc_inflow, const double* dl_dJ,
+                   const double* dl_dGamma, int n_threads, double* grad_kappa_abs, double* grad_emissivity) {
+    problem p;
+    memset(&p, 0, sizeof p);
+    p.n_cells = n_cells; p.n_faces = n_faces; p.volume = volume; p.face_cells = face_cells;
+    p.area = area; p.normal = normal; p.flags = flags; p.n_dir = n_dir; p.omega = omega;
+    p.weight = weight; p.n_groups = n_groups; p.kappa_abs = kappa_abs; p.kappa_scat = NULL;
+    p.emissivity = emissivity; p.bc_inflow = bc_inflow;
+    int rc = check_problem(&p);
+    if (rc != OR_OK) return rc;
+    for (int64_t f = 0; f < n_faces; ++f)
+        if (flags[f] & OR_FACE_PERIODIC) return OR_ERR_ARG;
+    rc = build_sides(&p);
+    if (rc != OR_OK) { free_sides(&p); return rc; }
+    int64_t N = n_cells, G = n_groups, NG = N * G, D = n_dir;
+    double* I = (double*)calloc((size_t)(D * NG > 0 ? D * NG : 1), sizeof(double));
+    double* lam = (double*)calloc((size_t)(D * NG > 0 ? D * NG : 1), sizeof(double));
+    double* q = (double*)malloc(sizeof(double) * (size_t)(NG > 0 ? NG : 1));
+    double* g = (double*)calloc((size_t)(D * NG > 0 ? D * NG : 1), sizeof(double));
+    if (!I || !lam || !q || !g) { rc = OR_ERR_MEM; goto out; }
+    for (int64_t i = 0; i < NG; ++i) q[i] = emissivity[i] / FOURPI;
+    rc = run_dirs(&p, n_threads, 0, q, 0, NULL, I, NULL, NULL, 1);
+    if (rc != OR_OK) goto out;
+    for (int32_t d = 0; d < n_dir; ++d)
+        for (int64_t c = 0; c < N; ++c)
+            for (int k = 0; k < G; ++k) {
+                int64_t i = c * G + k;
+                double gd = dl_dGamma ? dl_dGamma[i] * kappa_abs[i] * volume[c] : 0.0;
+                double gj = dl_dJ ? dl_dJ[i] / FOURPI : 0.0;
+                g[(int64_t)d * NG + i] = weight[d] * (gd + gj);
+            }
+    rc = run_dirs(&p, n_threads, 1, g, NG, NULL, lam, NULL, NULL, 1);
+    if (rc != OR_OK) goto out;
+    for (int64_t c = 0; c < N; ++c)
+        for (int k = 0; k < G; ++k) {
+            int64_t i = c * G + k;
+            double gk = 0.0, ge = 0.0;
+            for (int32_t d = 0; d < n_dir; ++d) {
+                double Icd = I[(int64_t)d * NG + i];
+                double lcd = lam[(int64_t)d * NG + i];
+                double rg = dl_dGamma ? dl_dGamma[i] : 0.0;
+                gk += volume[c] * Icd * (weight[d] * rg - lcd);
+                ge += lcd / FOURPI;
+            }
+            grad_kappa_abs[i] = gk;
+            grad_emissivity[i] = ge;
+        }
+out:
+    free(I); free(lam); free(q); free(g);
+    free_sides(&p);
+    return rc;
+}

@@ -1,0 +1,308 @@
+"""Pins of the FP64 oracle to facts other than itself (closed forms, identities, the paper's
+Appendix A invariant, independent dense solves, brute force, finite differences)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import dense
+from synth import configs
+from synth.fields import fibonacci_directions
+from synth.mesh import FACE_BOUNDARY, FACE_PERIODIC, column_mesh, lattice_mesh, voronoi_mesh
+
+pytestmark = pytest.mark.filterwarnings("ignore")
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+# ---- (a) closed form of the discrete update along a 1-D column (Sec. 2.6 scheme (a)) ----------
+@pytest.mark.parametrize("reverse", [False, True])
+def test_column_closed_form_inflow(reverse):
+    n, h, kap = 96, 1.0 / 64, 2.5
+    p = configs.column(n, kappa=kap, h=h, reverse=reverse)
+    r = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, bc_inflow=p.boundary_inflow,
+                     want_intensity=True)
+    assert r["rc"] == oracle.OK
+    I = r["I"][0, :, 0]
+    k = np.arange(n) if not reverse else np.arange(n)[::-1]
+    exact = (1.0 + kap * h) ** (-(k + 1.0))  # each cell attenuates by 1/(1 + kappa h)
+    assert rel(I, exact) <= 1e-14
+
+
+def test_column_closed_form_source():
+    n, h, kap, s = 80, 1.0 / 32, 1.7, 0.3
+    p = configs.column(n, kappa=kap, h=h, source=s)
+    r = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, bc_inflow=p.boundary_inflow,
+                     want_intensity=True)
+    I = r["I"][0, :, 0]
+    A, tau = h * h, kap * h
+    rr = 1.0 / (1.0 + tau)
+    b = (s / (4 * math.pi)) / (A * (1.0 + tau))
+    k = np.arange(n) + 1.0
+    exact = rr ** k + b * (1.0 - rr ** k) / (1.0 - rr)
+    assert rel(I, exact) <= 1e-14
+
+
+def test_column_tie_faces_carry_no_flux():
+    # the side faces have n.Omega = 0 exactly: neither upwind nor downwind (tie reading)
+    p = configs.column(16, kappa=0.0)
+    r = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, bc_inflow=p.boundary_inflow,
+                     want_intensity=True)
+    assert np.allclose(r["I"][0, :, 0], 1.0, rtol=0, atol=1e-15)
+    rc, lev, depth = oracle.levels(p.mesh, p.omega)
+    assert rc == 0 and depth[0] == 16 and np.array_equal(lev[0], np.arange(16))
+
+
+# ---- (b) photon conservation: emitted + injected = absorbed + escaped ----------------------------
+@pytest.mark.parametrize("periodic_box", [False, True])
+def test_conservation(periodic_box):
+    p = configs.voronoi_small(300, periodic_box=periodic_box, n_dir=12, n_groups=2, seed=3,
+                              bc_inflow=not periodic_box)
+    r = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, bc_inflow=p.boundary_inflow,
+                     tol_pbc=1e-15, max_it_pbc=2000)
+    st = r["stats"]
+    src = st["emitted"] + st["injected"]
+    assert abs(src - st["absorbed"] - st["escaped"]) <= 1e-12 * src
+    assert abs(st["defect"]) <= 1e-12
+    if periodic_box:
+        assert st["escaped"] == 0.0 and st["it_pbc"] > 1
+
+
+def test_conservation_with_scattering():
+    p = configs.voronoi_small(250, n_dir=8, n_groups=1, seed=5, scatter_albedo=0.5)
+    r = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, kappa_scat=p.kappa_scat,
+                     tol_scat=1e-15, max_it_scat=3000)
+    st = r["stats"]
+    assert abs(st["defect"]) <= 1e-12
+    assert st["it_scat"] > 2
+
+
+def test_pure_streaming_escapes_everything():
+    p = configs.voronoi_small(200, n_dir=10, seed=7)
+    r = oracle.solve(p.mesh, p.omega, p.weight, np.zeros_like(p.kappa_abs), p.emissivity)
+    st = r["stats"]
+    assert st["absorbed"] == 0.0
+    assert abs(st["escaped"] - st["emitted"]) <= 1e-13 * st["emitted"]
+
+
+# ---- (c) Appendix A: sorting by Omega.x of the generators is a topological order ---------------
+@pytest.mark.parametrize("periodic_box", [False, True])
+def test_voronoi_invariant(periodic_box):
+    rng = np.random.default_rng(11)
+    m = voronoi_mesh(rng.random((500, 3)), periodic=periodic_box, threads=1)
+    om, _ = fibonacci_directions(24, seed=2)
+    rc, lev, depth = oracle.levels(m, om)
+    assert rc == 0
+    inner = m.flags == 0
+    c0, c1 = m.face_cells[inner, 0], m.face_cells[inner, 1]
+    for d in range(om.shape[0]):
+        x = m.points @ om[d]
+        up_is_c0 = lev[d, c1] > lev[d, c0]
+        up = np.where(up_is_c0, c0, c1)
+        down = np.where(up_is_c0, c1, c0)
+        # every dependency runs from lower to higher Omega.x of the generators ...
+        assert np.all(x[down] > x[up])
+        # ... so sorting the cells by Omega.x gives a valid order: each cell after its upwind cells
+        order = np.argsort(x, kind="stable")
+        pos = np.empty_like(order)
+        pos[order] = np.arange(order.size)
+        assert np.all(pos[down] > pos[up])
+        assert np.all(lev[d, c0] != lev[d, c1])
+
+
+# ---- levels: brute-force longest paths on the dependency graph ---------------------------------
+def _longest_paths(m, om):
+    t = (m.normal[:, 0] * om[0] + m.normal[:, 1] * om[1]) + m.normal[:, 2] * om[2]
+    succ = [[] for _ in range(m.n_cells)]
+    pred = [[] for _ in range(m.n_cells)]
+    for f in range(m.n_faces):
+        if m.flags[f] & (FACE_BOUNDARY | FACE_PERIODIC) or t[f] == 0.0:
+            continue
+        a, b = int(m.face_cells[f, 0]), int(m.face_cells[f, 1])
+        if t[f] < 0:
+            a, b = b, a
+        succ[a].append(b)
+        pred[b].append(a)
+    memo = {}
+
+    def depth_to(c):  # longest path ending at c (recursion over predecessors)
+        if c in memo:
+            return memo[c]
+        v = 0 if not pred[c] else 1 + max(depth_to(u) for u in pred[c])
+        memo[c] = v
+        return v
+
+    import sys
+    sys.setrecursionlimit(100000)
+    return np.array([depth_to(c) for c in range(m.n_cells)])
+
+
+@pytest.mark.parametrize("kind", ["voronoi", "lattice", "periodic"])
+def test_levels_brute_force(kind):
+    if kind == "lattice":
+        m = lattice_mesh(7)
+    else:
+        rng = np.random.default_rng(4)
+        m = voronoi_mesh(rng.random((400, 3)), periodic=kind == "periodic", threads=1)
+    om, _ = fibonacci_directions(6, seed=9)
+    rc, lev, depth = oracle.levels(m, om)
+    assert rc == 0
+    for d in range(om.shape[0]):
+        bf = _longest_paths(m, om[d])
+        assert np.array_equal(bf, lev[d])
+        assert depth[d] == bf.max() + 1
+
+
+def test_lattice_depth_axis_direction():
+    m = lattice_mesh(9)
+    rc, lev, depth = oracle.levels(m, np.array([[0.0, 0.0, 1.0]]))
+    # Omega = +z: x and y faces are exact ties, the graph is 81 independent columns of 9
+    assert rc == 0 and depth[0] == 9
+    assert np.array_equal(lev[0], np.repeat(np.arange(9), 81))
+
+
+def test_cycle_detected():
+    # a ring of cells whose closing face is marked interior instead of periodic is cyclic
+    m = column_mesh(6, periodic_x=True)
+    m.flags = m.flags.copy()
+    m.flags[m.flags == FACE_PERIODIC] = 0
+    rc, _, _ = oracle.levels(m, np.array([[1.0, 0.0, 0.0]]))
+    assert rc == oracle.ERR_CYCLE
+
+
+# ---- (d) dense LU solves of L_Omega I = S ---------------------------------------------------------
+@pytest.mark.parametrize("G", [1, 3])
+def test_dense_plain(G):
+    p = configs.voronoi_small(350, n_dir=6, n_groups=G, seed=21, bc_inflow=True)
+    r = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, bc_inflow=p.boundary_inflow,
+                     want_intensity=True)
+    for d in range(p.n_dir):
+        Id = dense.solve_direction(p.mesh, p.omega[d], p.kappa_abs, p.emissivity, bc_inflow=p.boundary_inflow)
+        assert rel(r["I"][d], Id) <= 1e-12
+
+
+def test_dense_scattering_fixed_point():
+    p = configs.voronoi_small(150, n_dir=6, n_groups=2, seed=23, scatter_albedo=0.6)
+    r = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, kappa_scat=p.kappa_scat,
+                     tol_scat=1e-15, max_it_scat=5000)
+    _, Jd, Gd = dense.solve_coupled(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, p.kappa_scat)
+    assert rel(r["J"], Jd) <= 1e-12
+    assert rel(r["Gamma"], Gd) <= 1e-12
+
+
+def test_dense_periodic_fixed_point():
+    p = configs.voronoi_small(200, periodic_box=True, n_dir=6, n_groups=1, seed=25)
+    r = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, tol_pbc=1e-15, max_it_pbc=5000)
+    _, Jd, _ = dense.solve_coupled(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity)
+    assert rel(r["J"], Jd) <= 1e-12
+
+
+def test_uniform_periodic_fixed_point():
+    # eps_c = C kappa_a,c V_c with closed cells: I = C/(4pi) in every direction solves the balance
+    p = configs.voronoi_small(300, periodic_box=True, n_dir=8, seed=27)
+    C = 2.0
+    eps = C * p.kappa_abs * p.mesh.volume[:, None]
+    r = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, eps, tol_pbc=1e-15, max_it_pbc=5000,
+                     want_intensity=True)
+    assert np.max(np.abs(r["I"] - C / (4 * math.pi))) <= 1e-12 * C
+    # with scattering the same state is the fixed point of both iterations
+    r2 = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, eps, kappa_scat=0.7 * p.kappa_abs, tol_scat=1e-15,
+                      max_it_scat=3000, tol_pbc=1e-14, max_it_pbc=3000)
+    assert np.max(np.abs(r2["J"] - C / (4 * math.pi))) <= 1e-11 * C
+
+
+def test_linearity_in_sources():
+    p = configs.voronoi_small(250, n_dir=8, n_groups=2, seed=29, scatter_albedo=0.3)
+    rng = np.random.default_rng(1)
+    e1 = rng.random(p.emissivity.shape) * (rng.random(p.emissivity.shape) < 0.1)
+    e2 = rng.random(p.emissivity.shape) * (rng.random(p.emissivity.shape) < 0.1)
+    kw = dict(kappa_scat=p.kappa_scat, tol_scat=1e-15, max_it_scat=4000)
+    J1 = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, e1, **kw)["J"]
+    J2 = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, e2, **kw)["J"]
+    J12 = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, e1 + e2, **kw)["J"]
+    assert rel(J12, J1 + J2) <= 1e-13
+
+
+def test_plain32_lattice_solution_is_symmetric_under_the_source():
+    # unit source at (16,16,16) in a 32^3 lattice: conservation and total photon budget
+    p = configs.plain32()
+    r = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, threads=4)
+    st = r["stats"]
+    assert st["emitted"] == pytest.approx(1.0, rel=1e-15)
+    assert abs(st["defect"]) <= 1e-12
+    assert r["J"][p.info["source_cell"], 0] == r["J"].max()
+
+
+# ---- adjoint: reciprocity, dense transposed solve, finite differences -----------------------------
+def test_adjoint_reciprocity():
+    # BALANCE law: L_{-Omega} = L_Omega^T, so dJ/deps (adjoint with directions Omega and dL/dJ = r)
+    # equals the forward mean intensity for directions -Omega with emissivity r
+    p = configs.voronoi_small(300, n_dir=10, n_groups=2, seed=31)
+    rng = np.random.default_rng(2)
+    r_ = rng.random(p.emissivity.shape)
+    rc, gk, ge = oracle.adjoint(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, dl_dJ=r_)
+    assert rc == 0
+    Jrev = oracle.solve(p.mesh, -p.omega, p.weight, p.kappa_abs, r_)["J"]
+    assert rel(ge, Jrev) <= 1e-12
+
+
+def test_adjoint_dense_transpose():
+    p = configs.voronoi_small(200, n_dir=5, n_groups=1, seed=33)
+    rng = np.random.default_rng(3)
+    dg = rng.normal(size=p.kappa_abs.shape)
+    rc, gk, ge = oracle.adjoint(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, dl_dGamma=dg)
+    ge_d = np.zeros_like(ge)
+    gk_d = np.zeros_like(gk)
+    V = p.mesh.volume[:, None]
+    for d in range(p.n_dir):
+        I = dense.solve_direction(p.mesh, p.omega[d], p.kappa_abs, p.emissivity)
+        g = p.weight[d] * dg * p.kappa_abs * V
+        lam = dense.adjoint_direction(p.mesh, p.omega[d], p.kappa_abs, g)
+        ge_d += lam / (4 * math.pi)
+        gk_d += V * I * (p.weight[d] * dg - lam)
+    assert rel(ge, ge_d) <= 1e-11
+    assert rel(gk, gk_d) <= 1e-11
+
+
+def test_adjoint_finite_differences():
+    p = configs.voronoi_small(256, n_dir=8, n_groups=2, seed=35)
+    rng = np.random.default_rng(4)
+    T = rng.random(p.kappa_abs.shape) * 1e-3
+
+    def loss(ka, em):
+        r = oracle.solve(p.mesh, p.omega, p.weight, ka, em)
+        # exact summation: the loss difference of two nearby inputs is not drowned by rounding of the sum
+        return math.fsum(((r["Gamma"] - T) ** 2).ravel()), r["Gamma"]
+
+    L0, G0 = loss(p.kappa_abs, p.emissivity)
+    rc, gk, ge = oracle.adjoint(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, dl_dGamma=2 * (G0 - T))
+    assert rc == 0
+    # central differences, step 1e-4 relative: truncation ~1e-8, rounding ~1e-15 / step
+    big = np.argsort(np.abs(gk[:, 0]))[-40:]
+    for c in rng.choice(big, 6, replace=False):
+        for g in range(2):
+            h = 1e-4 * p.kappa_abs[c, g]
+            kp, km = p.kappa_abs.copy(), p.kappa_abs.copy()
+            kp[c, g] += h
+            km[c, g] -= h
+            fd = (loss(kp, p.emissivity)[0] - loss(km, p.emissivity)[0]) / (2 * h)
+            assert gk[c, g] == pytest.approx(fd, rel=1e-6, abs=1e-7 * np.abs(gk).max())
+            he = 1e-4 * max(p.emissivity[c, g], 1.0)
+            ep, emn = p.emissivity.copy(), p.emissivity.copy()
+            ep[c, g] += he
+            emn[c, g] -= he
+            fde = (loss(p.kappa_abs, ep)[0] - loss(p.kappa_abs, emn)[0]) / (2 * he)
+            assert ge[c, g] == pytest.approx(fde, rel=1e-6, abs=1e-7 * np.abs(ge).max())
+
+
+def test_invalid_inputs_rejected():
+    p = configs.voronoi_small(50, n_dir=4, seed=1)
+    m = p.mesh
+    bad = m.face_cells.copy()
+    bad[0, 0] = m.n_cells + 5
+    from synth.mesh import Mesh
+    mb = Mesh(volume=m.volume, face_cells=bad, area=m.area, normal=m.normal, flags=m.flags)
+    assert oracle.solve(mb, p.omega, p.weight, p.kappa_abs, p.emissivity)["rc"] == oracle.ERR_ARG
