@@ -1,0 +1,187 @@
+/*
+ * sweep.h -- C ABI of the GB300 transport-sweep library (libsweep.so).
+ *
+ * The library solves the steady, isotropically scattering radiative transfer
+ * equation (Peter et al. 2022, Sec. 2.2, Eq. radiativeTransfer) by discrete
+ * ordinates on an unstructured (Voronoi) mesh with the Sweep method:
+ *   - per direction, a face is upwind/downwind by the sign of n_f.Omega
+ *     (Sec. 2.5; Appendix A, Eq. downwindDefinition); an exact zero carries no flux;
+ *   - the dependency graph is ordered topologically (Sec. 2.3) into wavefront levels;
+ *   - each cell is solved in that order with transport scheme (a) of Sec. 2.6,
+ *       (P_c + kappa_t,c V_c) I_c = eps_c/(4 pi) + kappa_s,c V_c J_c + sum_in |a_f| I_up(f),
+ *     a_f = A_f n_f.Omega, P_c = sum of a_f over the cell's outflow faces;
+ *   - the scattering source iteration (Alg. 1) and the periodic-boundary
+ *     iteration (Sec. 2.7, Eq. relativeErrorPbc) run around the sweep.
+ * Outputs are the mean intensity J = (1/4pi) sum_d w_d I_d and the absorbed photon
+ * rate Gamma = kappa_a V sum_d w_d I_d per cell and frequency group (Sec. 3.2).
+ *
+ * Conventions
+ *   - All calls return a sweep_status and never abort. Outputs are written on
+ *     SWEEP_OK and SWEEP_NOT_CONVERGED. The context stays usable after every
+ *     error except SWEEP_ERR_CUDA (then destroy it).
+ *   - Plain (non-_dev) calls take HOST pointers; the caller owns them and they are
+ *     copied during the call (the library keeps no caller pointer).
+ *     _dev calls take DEVICE pointers valid on the context's stream; they are read
+ *     or written in stream order and the call returns after the work is queued,
+ *     except where a convergence decision needs a device-to-host read.
+ *   - Array layouts are row-major, C order. Cell arrays are [n_cells]; per-group
+ *     arrays are [n_cells][n_groups].
+ *   - One context drives one GPU and one CUDA stream. Calls on one context must
+ *     not overlap (the context is not thread-safe).
+ */
+#ifndef SWEEP_H
+#define SWEEP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sweep_ctx sweep_ctx; /* opaque; owns every device buffer it allocates */
+
+typedef enum {
+    SWEEP_OK = 0,
+    SWEEP_ERR_INVALID_ARG = 1, /* bad size, index, flag, value or missing prior set_* call */
+    SWEEP_ERR_CYCLE = 2,       /* a direction's dependency graph is cyclic (no topological order, Sec. 2.3) */
+    SWEEP_NOT_CONVERGED = 3,   /* an iteration hit its maximum count; outputs are still written */
+    SWEEP_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up; outputs are not valid */
+    SWEEP_ERR_OOM = 5,         /* device allocation failed */
+    SWEEP_ERR_CUDA = 6         /* any other CUDA error; destroy the context */
+} sweep_status;
+
+enum { SWEEP_FACE_BOUNDARY = 1, SWEEP_FACE_PERIODIC = 2 };
+
+/* Schedules of the batched sweep kernel. */
+enum {
+    SWEEP_SCHED_AUTO = 0,     /* pick by a one-time timing of LEVEL vs DATAFLOW per context */
+    SWEEP_SCHED_LEVEL = 1,    /* persistent kernel, grid barrier between wavefront levels */
+    SWEEP_SCHED_DATAFLOW = 2, /* persistent kernel, no barriers: each task waits (bounded) for its upwind values */
+    SWEEP_SCHED_PLAIN = 3     /* plain FP64 path: one kernel launch per (direction, level), no batching */
+};
+
+enum { SWEEP_LAW_BALANCE = 0 }; /* transport scheme (a) of Sec. 2.6 as a cell balance */
+
+typedef struct {
+    int32_t precision;    /* 32: FP32 intensities, FP64 tallies and norms; 64: FP64 throughout */
+    int32_t law;          /* SWEEP_LAW_BALANCE */
+    int32_t schedule;     /* SWEEP_SCHED_*; SWEEP_SCHED_PLAIN implies precision 64 */
+    int32_t max_it_scat;  /* source iteration (Alg. 1): maximum sweeps per periodic iteration */
+    double tol_scat;      /* stop when max_c |J_new - J_old| / J_new <= tol_scat (0/0 counts as converged) */
+    int32_t max_it_pbc;   /* periodic iteration (Sec. 2.7): maximum outer iterations */
+    int32_t warm_start;   /* 1: start the periodic iteration from the previous solve's intensities (Sec. 2.7) */
+    double tol_pbc;       /* stop when max_i |E_i| < tol_pbc, Eq. relativeErrorPbc */
+    int32_t dir_batch;    /* adjoint: directions per recompute batch (0 = all directions at once) */
+    int32_t relevel;      /* 1: redo classification and levelisation even if cached for this mesh+directions */
+    int32_t block_threads;/* threads per block of the batched sweep (0 = autotuned) */
+    int32_t use_graph;    /* 1: capture one iteration in a CUDA graph and replay it */
+    int64_t spin_budget;  /* bound on each device-side wait, in polls (0 = default, about 1 s) */
+    int32_t debug_stall;  /* TEST ONLY: 1 makes the first sweep task wait on a word nothing writes */
+    int32_t reserved;
+} sweep_opts;
+
+typedef struct {
+    int32_t it_scat, it_pbc;   /* sweeps done in the source iteration (total) and periodic iterations */
+    int32_t n_sweeps;          /* sweeps of all directions done by the solve */
+    int32_t depth_max;         /* largest critical-path depth (levels) over directions */
+    double depth_mean;         /* mean depth over directions */
+    double res_scat, res_pbc;  /* final residuals (max norm); res_pbc_mean = mean of |E_i| */
+    double res_pbc_mean;
+    double emitted, injected, absorbed, escaped; /* photons/s over all cells and groups (FP64) */
+    double defect;             /* (emitted + injected - absorbed - escaped) / (emitted + injected) */
+    double t_ms[8];            /* 0 classify, 1 levelise, 2 sweeps, 3 tallies+updates, 4 total (CUDA events) */
+    double updates;            /* cell x direction x group updates done by all sweeps */
+    double updates_per_s;      /* updates / (t_ms[4] / 1000) */
+    int32_t sweep_launches;    /* batched-sweep kernel launches timed in t_ms[2] */
+    int32_t schedule_used;     /* SWEEP_SCHED_* that ran */
+} sweep_stats;
+
+/* Fill *opts with defaults: precision 32, AUTO schedule, tolerances 1e-6, 100 iterations. */
+void sweep_default_opts(sweep_opts* opts);
+
+/* Create a context on CUDA device `device`, issuing all work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). */
+sweep_status sweep_create(sweep_ctx** ctx, int device, void* cuda_stream);
+sweep_status sweep_destroy(sweep_ctx* ctx);
+
+/* The mesh (Sec. 2.5: cells and their neighbours; Appendix A: face normals).
+ *   volume[n_cells]          > 0
+ *   face_cells[n_faces][2]   (c0, c1); c1 = -1 on a box-boundary face (flag BOUNDARY);
+ *                            with flag PERIODIC, c1 is the partner cell across the box
+ *                            (c1 == c0 allowed); faces are stored once
+ *   area[n_faces]            >= 0
+ *   normal[n_faces][3]       unit (|n| = 1 +- 1e-9), pointing from c0 towards c1
+ *                            (outward from c0 on boundary faces)
+ *   flags[n_faces]           SWEEP_FACE_BOUNDARY | SWEEP_FACE_PERIODIC (not both)
+ *   n_meshes, mesh_cell_offset[n_meshes+1]: independent meshes concatenated in one
+ *                            index space (faces must not cross meshes); NULL = one mesh.
+ * Limits: n_cells < 2^30, sum of face sides < 2^32. Invalidates material and cached levels.
+ * Errors: SWEEP_ERR_INVALID_ARG (nothing is kept), SWEEP_ERR_OOM. */
+sweep_status sweep_set_mesh(sweep_ctx* ctx, int64_t n_cells, const double* volume, int64_t n_faces,
+                            const int32_t* face_cells, const double* area, const double* normal,
+                            const uint8_t* flags, int32_t n_meshes, const int64_t* mesh_cell_offset);
+
+/* The discrete-ordinates direction set (Sec. 2.2; solid angle 4pi/N_dir per bin, Sec. 2.6).
+ *   omega[n_dir][3] unit vectors, weight[n_dir] > 0 with sum = 4pi (relative 1e-12).
+ * 1 <= n_dir <= 1024, and n_cells * 2^ceil(log2 n_dir) <= 2^32.
+ * Invalidates cached levels. Errors: SWEEP_ERR_INVALID_ARG. */
+sweep_status sweep_set_directions(sweep_ctx* ctx, int32_t n_dir, const double* omega, const double* weight);
+
+/* Material of the current mesh (Eq. radiativeTransfer), per cell and group, 1 <= n_groups <= 8:
+ *   kappa_abs[n_cells][G]   absorption coefficient (>= 0, finite)
+ *   kappa_scat[n_cells][G]  isotropic scattering coefficient, or NULL = none
+ *   emissivity[n_cells][G]  photons/s emitted by the cell, isotropically (>= 0)
+ *   boundary_inflow[n_boundary_faces][G]  isotropic intensity entering through each
+ *                           boundary face (in face order), or NULL = vacuum (I = 0, Sec. 2.5)
+ * Errors: SWEEP_ERR_INVALID_ARG (no mesh, bad value). */
+sweep_status sweep_set_material(sweep_ctx* ctx, int32_t n_groups, const double* kappa_abs,
+                                const double* kappa_scat, const double* emissivity,
+                                const double* boundary_inflow);
+/* Same, with device pointers (values are not range-checked; NaN/negative inputs give undefined results). */
+sweep_status sweep_set_material_dev(sweep_ctx* ctx, int32_t n_groups, const double* kappa_abs,
+                                    const double* kappa_scat, const double* emissivity,
+                                    const double* boundary_inflow);
+
+/* Solve: classification + levelisation (cached per mesh and direction set), then the
+ * periodic iteration (outer, Sec. 2.7) around the source iteration (inner, Alg. 1)
+ * around the batched sweep. Writes mean_intensity and absorbed_rate [n_cells][G]
+ * (either may be NULL) and *stats (may be NULL).
+ * Errors: INVALID_ARG (missing set_*), CYCLE, TIMEOUT, OOM, CUDA; NOT_CONVERGED with outputs. */
+sweep_status sweep_solve(sweep_ctx* ctx, const sweep_opts* opts, double* mean_intensity, double* absorbed_rate,
+                         sweep_stats* stats);
+sweep_status sweep_solve_dev(sweep_ctx* ctx, const sweep_opts* opts, double* mean_intensity,
+                             double* absorbed_rate, sweep_stats* stats);
+
+/* Wavefront level of every cell for direction `dir` (0 = no upwind cell, else 1 + the
+ * largest level of its upwind cells: the longest dependency path, Sec. 2.3) and the
+ * direction's depth (1 + largest level). Classifies and levelises if not cached.
+ * level[n_cells] host pointer. Errors: INVALID_ARG, CYCLE. */
+sweep_status sweep_levels(sweep_ctx* ctx, int32_t dir, int32_t* level, int32_t* depth);
+
+/* Intensity of direction `dir` from the last solve's final sweep, as FP64, [n_cells][G]
+ * host pointer. Errors: INVALID_ARG (no solve yet or bad dir). */
+sweep_status sweep_intensity(sweep_ctx* ctx, int32_t dir, double* intensity);
+
+/* Adjoint (transpose) of the sweep for a loss L(J, Gamma), for problems without
+ * scattering and without periodic faces. For each direction it solves
+ * L_Omega^T lambda = g, g_c = w_d (dL/dGamma_c kappa_a,c V_c + dL/dJ_c / 4pi), as a sweep
+ * in reversed level order, recomputing the forward intensities per batch of
+ * opts->dir_batch directions instead of storing them, and accumulates in FP64
+ *   dL/dkappa_a,c = sum_d V_c I_c,d (w_d dL/dGamma_c - lambda_c,d),  dL/deps_c = sum_d lambda_c,d / 4pi.
+ * dl_dJ, dl_dGamma [n_cells][G] (either may be NULL = zero); outputs [n_cells][G].
+ * Errors: INVALID_ARG (scattering or periodic faces present, missing set_*), CYCLE, TIMEOUT, OOM, CUDA. */
+sweep_status sweep_adjoint(sweep_ctx* ctx, const sweep_opts* opts, const double* dl_dJ, const double* dl_dGamma,
+                           double* grad_kappa_abs, double* grad_emissivity, sweep_stats* stats);
+sweep_status sweep_adjoint_dev(sweep_ctx* ctx, const sweep_opts* opts, const double* dl_dJ,
+                               const double* dl_dGamma, double* grad_kappa_abs, double* grad_emissivity,
+                               sweep_stats* stats);
+
+/* Static description of a status code; sweep_last_error gives the context's last detailed message. */
+const char* sweep_status_string(sweep_status status);
+const char* sweep_last_error(const sweep_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWEEP_H */

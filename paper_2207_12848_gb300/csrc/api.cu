@@ -1,0 +1,1021 @@
+// Host side of the C ABI declared in include/sweep.h: context, uploads and validation,
+// the solve loop (periodic iteration of Sec. 2.7 outside, source iteration of Alg. 1 inside,
+// batched sweep innermost), the schedule autotuner and the adjoint with recompute batches.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace sw;
+
+
+struct SolveBuf {
+    void* I[2] = {nullptr, nullptr};
+    int sign[2] = {0, 0};   // sign bit currently carried by every value of the buffer
+    size_t bytes = 0;
+    int prec = 0;
+    int last = -1;          // buffer holding the last solve's final intensities
+    int64_t N = 0;
+    int nd = 0, G = 0;
+};
+
+struct sweep_ctx {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    int sms = 0;
+    std::string err;
+    // mesh
+    bool has_mesh = false;
+    DevMesh mesh;
+    // directions
+    bool has_dirs = false;
+    int D = 0;
+    double* om64 = nullptr;
+    double* w64 = nullptr;
+    float4* om32 = nullptr;
+    double wsum = 0.0;
+    // material
+    bool has_mat = false;
+    int G = 0;
+    double *ka = nullptr, *ks = nullptr, *em = nullptr, *bc = nullptr;
+    bool has_scat = false;
+    // forward levels (all directions) and adjoint batch levels
+    Levels lev, adj_lev;
+    // solution
+    SolveBuf sb;
+    float2* cm32 = nullptr;
+    double2* cm64 = nullptr;
+    size_t cm_cap = 0;  // elements
+    double *J = nullptr, *Jold = nullptr, *Gam = nullptr, *jn = nullptr, *jn1 = nullptr;
+    size_t ng_cap = 0;
+    double* partial = nullptr;
+    int partial_cap = 0;
+    double* red = nullptr;          // [4]
+    unsigned long long* dmax = nullptr;
+    GridBar* bar = nullptr;
+    int* derr = nullptr;
+    int64_t* scratch = nullptr;
+    float* stall_word = nullptr;
+    // adjoint buffers
+    void* adjI = nullptr;
+    void* adjL = nullptr;
+    size_t adj_bytes_I = 0, adj_bytes_L = 0;
+    // autotuner: schedule and block size per (precision, G)
+    int tuned[2][9][2] = {};
+};
+
+namespace {
+
+sweep_status cuda_status(sweep_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return SWEEP_OK;
+    c->err = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? SWEEP_ERR_OOM : SWEEP_ERR_CUDA;
+}
+
+#define CK(x, what)                                       \
+    do {                                                  \
+        cudaError_t _e = (x);                             \
+        if (_e != cudaSuccess) return cuda_status(c, _e, what); \
+    } while (0)
+
+sweep_status bad(sweep_ctx* c, const std::string& m) {
+    c->err = m;
+    return SWEEP_ERR_INVALID_ARG;
+}
+
+template <typename T>
+void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+void free_levels(Levels& L) {
+    dfree(L.raw); dfree(L.task); dfree(L.count); dfree(L.level); dfree(L.lvl_cnt); dfree(L.pad_off);
+    dfree(L.lev_chunk); dfree(L.seg_off);
+    L = Levels();
+}
+
+void free_mesh(DevMesh& m) {
+    dfree(m.rowptr); dfree(m.side); dfree(m.side64); dfree(m.vol); dfree(m.pcells); dfree(m.bcells);
+    m = DevMesh();
+}
+
+void free_solution(sweep_ctx* c) {
+    dfree(c->sb.I[0]); dfree(c->sb.I[1]);
+    c->sb = SolveBuf();
+    dfree(c->adjI); dfree(c->adjL);
+    c->adj_bytes_I = c->adj_bytes_L = 0;
+}
+
+void free_material(sweep_ctx* c) {
+    dfree(c->ka); dfree(c->ks); dfree(c->em); dfree(c->bc);
+    c->has_mat = false;
+    c->has_scat = false;
+}
+
+int dir_bits(int nd) {
+    int b = 1;
+    while ((1 << b) < nd) ++b;
+    return b;
+}
+
+sweep_status alloc_levels(sweep_ctx* c, Levels& L, int d0, int nd) {
+    const int64_t N = c->mesh.N;
+    if (L.nd == nd && L.raw && L.d0 == d0) {
+        L.valid = false;
+        return SWEEP_OK;
+    }
+    free_levels(L);
+    L.d0 = d0;
+    L.nd = nd;
+    int bits = dir_bits(nd);
+    L.cshift = 32 - bits;
+    L.cmask = (bits == 32) ? 0u : ((1u << L.cshift) - 1u);
+    if ((uint64_t)N > (uint64_t)L.cmask + 1ull) return bad(c, "n_cells too large for the number of directions");
+    L.task_cap = N * (int64_t)nd + 32 * (N + 2);
+    CK(cudaMalloc(&L.raw, sizeof(uint32_t) * L.task_cap), "alloc task list");
+    CK(cudaMalloc(&L.task, sizeof(uint32_t) * L.task_cap), "alloc task list");
+    CK(cudaMalloc(&L.count, sizeof(int32_t) * N * nd), "alloc counts");
+    CK(cudaMalloc(&L.level, sizeof(int32_t) * N * nd), "alloc levels");
+    CK(cudaMalloc(&L.lvl_cnt, sizeof(int32_t) * (N + 2)), "alloc level counts");
+    CK(cudaMalloc(&L.pad_off, sizeof(uint32_t) * (N + 2)), "alloc level offsets");
+    CK(cudaMalloc(&L.lev_chunk, sizeof(int64_t) * (N + 2)), "alloc level chunks");
+    // worst case of levels x (nd+1) segment starts is only known after levelisation
+    return SWEEP_OK;
+}
+
+sweep_status run_levelise(sweep_ctx* c, Levels& L, int d0, int nd, long long budget, float* t1, float* t2) {
+    sweep_status s = alloc_levels(c, L, d0, nd);
+    if (s != SWEEP_OK) return s;
+    CK(cudaMemsetAsync(c->derr, 0, sizeof(int), c->st), "reset error word");
+    std::string msg;
+    CK(levelise(c->mesh, L, c->om64, c->om32, c->sms, c->bar, c->derr, budget, c->scratch, c->st, t1, t2, &msg),
+       "levelise");
+    if (!L.valid) {
+        c->err = msg;
+        if (msg.find("cyclic") != std::string::npos) return SWEEP_ERR_CYCLE;
+        return SWEEP_ERR_TIMEOUT;
+    }
+    return SWEEP_OK;
+}
+
+long long budget_of(const sweep_opts* o) { return o && o->spin_budget > 0 ? o->spin_budget : (1ll << 21); }
+
+sweep_status ensure_common(sweep_ctx* c) {
+    if (!c->bar) {
+        CK(cudaMalloc(&c->bar, sizeof(GridBar)), "alloc");
+        CK(cudaMalloc(&c->derr, sizeof(int)), "alloc");
+        CK(cudaMalloc(&c->scratch, sizeof(int64_t) * 4), "alloc");
+        CK(cudaMalloc(&c->red, sizeof(double) * 4), "alloc");
+        CK(cudaMalloc(&c->dmax, sizeof(unsigned long long)), "alloc");
+        CK(cudaMalloc(&c->stall_word, sizeof(double)), "alloc");
+        CK(cudaMemset(c->stall_word, 0, sizeof(double)), "init");
+    }
+    return SWEEP_OK;
+}
+
+sweep_status ensure_ng(sweep_ctx* c, size_t ng) {
+    if (c->ng_cap >= ng && c->J) return SWEEP_OK;
+    dfree(c->J); dfree(c->Jold); dfree(c->Gam); dfree(c->jn); dfree(c->jn1);
+    size_t n = ng > 0 ? ng : 1;
+    CK(cudaMalloc(&c->J, sizeof(double) * n), "alloc J");
+    CK(cudaMalloc(&c->Jold, sizeof(double) * n), "alloc J");
+    CK(cudaMalloc(&c->Gam, sizeof(double) * n), "alloc Gamma");
+    CK(cudaMalloc(&c->jn, sizeof(double) * n), "alloc j");
+    CK(cudaMalloc(&c->jn1, sizeof(double) * n), "alloc j");
+    c->ng_cap = n;
+    return SWEEP_OK;
+}
+
+sweep_status ensure_cm(sweep_ctx* c, size_t n) {
+    if (c->cm_cap >= n && c->cm32) return SWEEP_OK;
+    dfree(c->cm32); dfree(c->cm64);
+    size_t m = n > 0 ? n : 1;
+    CK(cudaMalloc(&c->cm32, sizeof(float2) * m), "alloc sources");
+    CK(cudaMalloc(&c->cm64, sizeof(double2) * m), "alloc sources");
+    c->cm_cap = m;
+    return SWEEP_OK;
+}
+
+sweep_status ensure_partial(sweep_ctx* c, int nblk) {
+    if (c->partial_cap >= nblk && c->partial) return SWEEP_OK;
+    dfree(c->partial);
+    CK(cudaMalloc(&c->partial, sizeof(double) * 2 * (nblk > 0 ? nblk : 1)), "alloc partials");
+    c->partial_cap = nblk;
+    return SWEEP_OK;
+}
+
+int nblocks256(int64_t n) { return (int)((n + 255) / 256 > 0 ? (n + 255) / 256 : 1); }
+
+SweepArgs make_args(sweep_ctx* c, const Levels& L, int precision, const void* cm, void* I, const void* Iprev,
+                    int G, int parity, int reverse, int level_sync, const sweep_opts* o) {
+    SweepArgs a;
+    memset(&a, 0, sizeof a);
+    a.task = L.task;
+    a.n_chunks = L.h_lev_chunk.empty() ? 0 : L.h_lev_chunk.back();
+    a.lev_chunk = L.lev_chunk;
+    a.n_levels = L.n_levels;
+    a.cshift = L.cshift;
+    a.cmask = L.cmask;
+    a.nd = L.nd;
+    a.rowptr = c->mesh.rowptr;
+    a.side = c->mesh.side;
+    a.side64 = c->mesh.side64;
+    a.om32 = c->om32 + L.d0;
+    a.om64 = c->om64 + 3 * (int64_t)L.d0;
+    a.w64 = c->w64 + L.d0;
+    a.cm = cm;
+    a.bc = reverse ? nullptr : (precision == 64 ? (const void*)c->bc : nullptr);
+    a.I = I;
+    a.Iprev = Iprev;
+    a.N = c->mesh.N;
+    a.G = G;
+    a.parity = parity;
+    a.reverse = reverse;
+    a.level_sync = level_sync;
+    a.bar = c->bar;
+    a.err = c->derr;
+    a.spin_budget = budget_of(o);
+    a.debug_stall = o ? o->debug_stall : 0;
+    a.stall_word = c->stall_word;
+    (void)precision;
+    return a;
+}
+
+sweep_status run_sweep(sweep_ctx* c, const Levels& L, int precision, int schedule, int threads, SweepArgs a,
+                       const float* bc32, float* ms) {
+    if (precision == 32) a.bc = a.reverse ? nullptr : bc32;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    CK(cudaMemsetAsync(c->bar, 0, sizeof(GridBar), c->st), "reset barrier");
+    CK(cudaMemsetAsync(c->derr, 0, sizeof(int), c->st), "reset error word");
+    cudaEventRecord(e0, c->st);
+    if (schedule == SWEEP_SCHED_PLAIN) {
+        const int nd = L.nd;
+        for (int d = 0; d < nd; ++d) {
+            for (int li = 0; li < L.n_levels; ++li) {
+                const int lv = a.reverse ? L.n_levels - 1 - li : li;
+                uint32_t b0 = L.h_seg_off[(size_t)lv * (nd + 1) + d], b1 = L.h_seg_off[(size_t)lv * (nd + 1) + d + 1];
+                if (b1 > b0) CK(launch_plain_level(a, b0, b1, c->st), "plain sweep");
+            }
+        }
+    } else {
+        int per_sm = sweep_occupancy(precision, a.G, threads, L.nd);
+        if (per_sm < 1) return bad(c, "sweep kernel does not fit on an SM");
+        a.level_sync = schedule == SWEEP_SCHED_LEVEL ? 1 : 0;
+        CK(launch_sweep(a, precision, c->sms * per_sm, threads, c->st), "sweep launch");
+    }
+    cudaEventRecord(e1, c->st);
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, c->derr, sizeof herr, cudaMemcpyDeviceToHost, c->st), "read error word");
+    CK(cudaStreamSynchronize(c->st), "sweep");
+    float t = 0;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ms) *ms += t;
+    if (herr != DEV_OK) {
+        c->err = "sweep: a bounded device wait gave up";
+        return SWEEP_ERR_TIMEOUT;
+    }
+    return SWEEP_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+extern "C" {
+
+void sweep_default_opts(sweep_opts* o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->precision = 32;
+    o->law = SWEEP_LAW_BALANCE;
+    o->schedule = SWEEP_SCHED_AUTO;
+    o->max_it_scat = 100;
+    o->tol_scat = 1e-6;
+    o->max_it_pbc = 100;
+    o->tol_pbc = 1e-6;
+}
+
+const char* sweep_status_string(sweep_status s) {
+    switch (s) {
+        case SWEEP_OK: return "ok";
+        case SWEEP_ERR_INVALID_ARG: return "invalid argument";
+        case SWEEP_ERR_CYCLE: return "dependency graph is cyclic";
+        case SWEEP_NOT_CONVERGED: return "iteration did not converge";
+        case SWEEP_ERR_TIMEOUT: return "device wait timed out";
+        case SWEEP_ERR_OOM: return "out of device memory";
+        case SWEEP_ERR_CUDA: return "CUDA error";
+    }
+    return "unknown status";
+}
+
+const char* sweep_last_error(const sweep_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+sweep_status sweep_create(sweep_ctx** out, int device, void* stream) {
+    if (!out) return SWEEP_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return SWEEP_ERR_INVALID_ARG;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return SWEEP_ERR_CUDA;
+    sweep_ctx* c = new sweep_ctx();
+    c->device = device;
+    c->st = (cudaStream_t)stream;
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
+    if (!coop) {
+        delete c;
+        return SWEEP_ERR_CUDA;
+    }
+    sweep_status s = ensure_common(c);
+    if (s != SWEEP_OK) {
+        delete c;
+        return s;
+    }
+    *out = c;
+    return SWEEP_OK;
+}
+
+sweep_status sweep_destroy(sweep_ctx* c) {
+    if (!c) return SWEEP_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->st);
+    free_levels(c->lev);
+    free_levels(c->adj_lev);
+    free_solution(c);
+    free_material(c);
+    free_mesh(c->mesh);
+    dfree(c->om64); dfree(c->w64); dfree(c->om32);
+    dfree(c->cm32); dfree(c->cm64);
+    dfree(c->J); dfree(c->Jold); dfree(c->Gam); dfree(c->jn); dfree(c->jn1);
+    dfree(c->partial); dfree(c->red); dfree(c->dmax); dfree(c->bar); dfree(c->derr); dfree(c->scratch);
+    dfree(c->stall_word);
+    delete c;
+    return SWEEP_OK;
+}
+
+sweep_status sweep_set_mesh(sweep_ctx* c, int64_t n_cells, const double* volume, int64_t n_faces,
+                            const int32_t* face_cells, const double* area, const double* normal, const uint8_t* flags,
+                            int32_t n_meshes, const int64_t* mesh_cell_offset) {
+    if (!c) return SWEEP_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    if (n_cells < 1 || n_cells >= (1ll << 30)) return bad(c, "n_cells must be in [1, 2^30)");
+    if (n_faces < 0) return bad(c, "n_faces < 0");
+    if (!volume || (n_faces > 0 && (!face_cells || !area || !normal || !flags))) return bad(c, "null mesh array");
+    std::vector<int64_t> off;
+    if (n_meshes <= 0 || !mesh_cell_offset) off = {0, n_cells};
+    else {
+        off.assign(mesh_cell_offset, mesh_cell_offset + n_meshes + 1);
+        if (off[0] != 0 || off.back() != n_cells) return bad(c, "mesh_cell_offset must run from 0 to n_cells");
+        for (int i = 0; i < n_meshes; ++i)
+            if (off[i + 1] <= off[i]) return bad(c, "mesh_cell_offset must be increasing");
+    }
+    int64_t S = 0, NB = 0;
+    for (int64_t f = 0; f < n_faces; ++f) {
+        S += face_cells[2 * f + 1] >= 0 ? 2 : 1;
+        NB += (flags[f] & SWEEP_FACE_BOUNDARY) ? 1 : 0;
+    }
+    if (S >= (1ll << 32) - 64) return bad(c, "too many face sides (>= 2^32)");
+    // drop everything tied to the previous mesh
+    cudaStreamSynchronize(c->st);
+    free_levels(c->lev);
+    free_levels(c->adj_lev);
+    free_solution(c);
+    free_material(c);
+    free_mesh(c->mesh);
+    c->has_mesh = false;
+    // upload and validate
+    double *d_vol = nullptr, *d_area = nullptr, *d_normal = nullptr;
+    int32_t *d_fc = nullptr, *d_tmp = nullptr;
+    uint8_t* d_flags = nullptr;
+    int64_t* d_off = nullptr;
+    int* d_bad = nullptr;
+    int64_t F1 = n_faces > 0 ? n_faces : 1;
+    auto cleanup = [&]() {
+        cudaFree(d_area); cudaFree(d_normal); cudaFree(d_fc); cudaFree(d_tmp); cudaFree(d_flags);
+        cudaFree(d_off); cudaFree(d_bad);
+    };
+#define CKM(x, what) do { cudaError_t _e = (x); if (_e != cudaSuccess) { cleanup(); cudaFree(d_vol); return cuda_status(c, _e, what); } } while (0)
+    CKM(cudaMalloc(&d_vol, sizeof(double) * n_cells), "alloc volume");
+    CKM(cudaMalloc(&d_area, sizeof(double) * F1), "alloc area");
+    CKM(cudaMalloc(&d_normal, sizeof(double) * 3 * F1), "alloc normal");
+    CKM(cudaMalloc(&d_fc, sizeof(int32_t) * 2 * F1), "alloc faces");
+    CKM(cudaMalloc(&d_flags, F1), "alloc flags");
+    CKM(cudaMalloc(&d_off, sizeof(int64_t) * off.size()), "alloc offsets");
+    CKM(cudaMalloc(&d_bad, sizeof(int)), "alloc");
+    CKM(cudaMalloc(&d_tmp, sizeof(int32_t) * ((n_cells > n_faces ? n_cells : n_faces) + 2)), "alloc");
+    CKM(cudaMemcpyAsync(d_vol, volume, sizeof(double) * n_cells, cudaMemcpyHostToDevice, c->st), "upload");
+    if (n_faces > 0) {
+        CKM(cudaMemcpyAsync(d_area, area, sizeof(double) * n_faces, cudaMemcpyHostToDevice, c->st), "upload");
+        CKM(cudaMemcpyAsync(d_normal, normal, sizeof(double) * 3 * n_faces, cudaMemcpyHostToDevice, c->st), "upload");
+        CKM(cudaMemcpyAsync(d_fc, face_cells, sizeof(int32_t) * 2 * n_faces, cudaMemcpyHostToDevice, c->st), "upload");
+        CKM(cudaMemcpyAsync(d_flags, flags, n_faces, cudaMemcpyHostToDevice, c->st), "upload");
+    }
+    CKM(cudaMemcpyAsync(d_off, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice, c->st), "upload");
+    CKM(cudaMemsetAsync(d_bad, 0, sizeof(int), c->st), "init");
+    CKM(launch_validate_mesh(n_cells, n_faces, d_vol, d_fc, d_area, d_normal, d_flags, d_off, (int)off.size() - 1,
+                             d_bad, c->st), "validate mesh");
+    int hbad = 0;
+    CKM(cudaMemcpyAsync(&hbad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->st), "validate mesh");
+    CKM(cudaStreamSynchronize(c->st), "validate mesh");
+    if (hbad) {
+        cleanup();
+        cudaFree(d_vol);
+        char buf[160];
+        snprintf(buf, sizeof buf,
+                 "invalid mesh (flags %d: 1 cell index, 2 face flags, 4 area, 8 normal, 16 volume, 32 face crosses "
+                 "meshes, 64 self face)", hbad);
+        return bad(c, buf);
+    }
+    DevMesh& m = c->mesh;
+    m.N = n_cells;
+    m.F = n_faces;
+    m.S = S;
+    m.NB = NB;
+    m.vol = d_vol;
+    m.mesh_off = off;
+    CKM(cudaMalloc(&m.rowptr, sizeof(uint32_t) * (n_cells + 1)), "alloc rows");
+    CKM(cudaMalloc(&m.side, sizeof(int4) * (S > 0 ? S : 1) + 64 * sizeof(int4)), "alloc sides");
+    CKM(cudaMalloc(&m.side64, sizeof(d4) * (S > 0 ? S : 1)), "alloc sides");
+    CKM(launch_build_csr(m, d_fc, d_area, d_normal, d_flags, d_tmp, c->st), "build CSR");
+    CKM(cudaStreamSynchronize(c->st), "build CSR");
+#undef CKM
+    cleanup();
+    c->has_mesh = true;
+    return SWEEP_OK;
+}
+
+sweep_status sweep_set_directions(sweep_ctx* c, int32_t n_dir, const double* omega, const double* weight) {
+    if (!c) return SWEEP_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    if (n_dir < 1 || n_dir > 1024) return bad(c, "n_dir must be in [1, 1024]");
+    if (!omega || !weight) return bad(c, "null direction array");
+    double ws = 0.0;
+    for (int d = 0; d < n_dir; ++d) {
+        double x = omega[3 * d], y = omega[3 * d + 1], z = omega[3 * d + 2];
+        double n2 = x * x + y * y + z * z;
+        if (!(std::fabs(n2 - 1.0) <= 2.5e-9)) return bad(c, "direction is not a unit vector");
+        if (!(weight[d] > 0.0) || !std::isfinite(weight[d])) return bad(c, "direction weight must be > 0");
+        ws += weight[d];
+    }
+    if (!(std::fabs(ws - FOURPI) <= 1e-12 * FOURPI)) return bad(c, "direction weights must sum to 4pi");
+    cudaStreamSynchronize(c->st);
+    dfree(c->om64); dfree(c->w64); dfree(c->om32);
+    free_levels(c->lev);
+    free_levels(c->adj_lev);
+    free_solution(c);
+    std::vector<float4> o32(n_dir);
+    for (int d = 0; d < n_dir; ++d)
+        o32[d] = make_float4((float)omega[3 * d], (float)omega[3 * d + 1], (float)omega[3 * d + 2], (float)weight[d]);
+    CK(cudaMalloc(&c->om64, sizeof(double) * 3 * n_dir), "alloc directions");
+    CK(cudaMalloc(&c->w64, sizeof(double) * n_dir), "alloc directions");
+    CK(cudaMalloc(&c->om32, sizeof(float4) * n_dir), "alloc directions");
+    CK(cudaMemcpyAsync(c->om64, omega, sizeof(double) * 3 * n_dir, cudaMemcpyHostToDevice, c->st), "upload");
+    CK(cudaMemcpyAsync(c->w64, weight, sizeof(double) * n_dir, cudaMemcpyHostToDevice, c->st), "upload");
+    CK(cudaMemcpyAsync(c->om32, o32.data(), sizeof(float4) * n_dir, cudaMemcpyHostToDevice, c->st), "upload");
+    CK(cudaStreamSynchronize(c->st), "upload directions");
+    c->D = n_dir;
+    c->wsum = ws;
+    c->has_dirs = true;
+    return SWEEP_OK;
+}
+
+static sweep_status set_material_impl(sweep_ctx* c, int32_t G, const double* ka, const double* ks, const double* em,
+                                      const double* bc, bool dev) {
+    if (!c) return SWEEP_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    if (!c->has_mesh) return bad(c, "set the mesh first");
+    if (G < 1 || G > 8) return bad(c, "n_groups must be in [1, 8]");
+    if (!ka || !em) return bad(c, "kappa_abs and emissivity are required");
+    const int64_t NG = c->mesh.N * (int64_t)G;
+    const int64_t NBG = c->mesh.NB * (int64_t)G;
+    bool scat = false;
+    if (!dev) {
+        for (int64_t i = 0; i < NG; ++i) {
+            if (!(ka[i] >= 0.0) || !std::isfinite(ka[i])) return bad(c, "kappa_abs must be finite and >= 0");
+            if (!(em[i] >= 0.0) || !std::isfinite(em[i])) return bad(c, "emissivity must be finite and >= 0");
+            if (ks) {
+                if (!(ks[i] >= 0.0) || !std::isfinite(ks[i])) return bad(c, "kappa_scat must be finite and >= 0");
+                if (ks[i] > 0.0) scat = true;
+            }
+        }
+        if (bc)
+            for (int64_t i = 0; i < NBG; ++i)
+                if (!(bc[i] >= 0.0) || !std::isfinite(bc[i])) return bad(c, "boundary_inflow must be finite and >= 0");
+    }
+    cudaStreamSynchronize(c->st);
+    free_material(c);
+    cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    size_t nb = sizeof(double) * (NG > 0 ? NG : 1);
+    CK(cudaMalloc(&c->ka, nb), "alloc material");
+    CK(cudaMalloc(&c->em, nb), "alloc material");
+    CK(cudaMemcpyAsync(c->ka, ka, sizeof(double) * NG, kind, c->st), "upload material");
+    CK(cudaMemcpyAsync(c->em, em, sizeof(double) * NG, kind, c->st), "upload material");
+    if (ks) {
+        CK(cudaMalloc(&c->ks, nb), "alloc material");
+        CK(cudaMemcpyAsync(c->ks, ks, sizeof(double) * NG, kind, c->st), "upload material");
+        if (dev) scat = true;  // not inspected on the host; a zero array costs one extra sweep
+    }
+    if (bc && NBG > 0) {
+        CK(cudaMalloc(&c->bc, sizeof(double) * NBG), "alloc boundary inflow");
+        CK(cudaMemcpyAsync(c->bc, bc, sizeof(double) * NBG, kind, c->st), "upload boundary inflow");
+    }
+    if (!dev) CK(cudaStreamSynchronize(c->st), "upload material");
+    c->G = G;
+    c->has_scat = scat;
+    c->has_mat = true;
+    return SWEEP_OK;
+}
+
+sweep_status sweep_set_material(sweep_ctx* c, int32_t G, const double* ka, const double* ks, const double* em,
+                                const double* bc) {
+    return set_material_impl(c, G, ka, ks, em, bc, false);
+}
+
+sweep_status sweep_set_material_dev(sweep_ctx* c, int32_t G, const double* ka, const double* ks, const double* em,
+                                    const double* bc) {
+    return set_material_impl(c, G, ka, ks, em, bc, true);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+sweep_status ensure_levels(sweep_ctx* c, const sweep_opts* o, float* t1, float* t2) {
+    if (c->lev.valid && !(o && o->relevel) && c->lev.nd == c->D && c->lev.d0 == 0) return SWEEP_OK;
+    return run_levelise(c, c->lev, 0, c->D, budget_of(o), t1, t2);
+}
+
+sweep_status ensure_solution(sweep_ctx* c, int prec, bool two) {
+    SolveBuf& b = c->sb;
+    const size_t es = prec == 64 ? 8 : 4;
+    const size_t bytes = es * (size_t)c->mesh.N * c->D * c->G;
+    if (b.bytes != bytes || b.prec != prec || b.N != c->mesh.N || b.nd != c->D || b.G != c->G) {
+        dfree(b.I[0]);
+        dfree(b.I[1]);
+        b = SolveBuf();
+        CK(cudaMalloc(&b.I[0], bytes > 0 ? bytes : 4), "alloc intensities");
+        CK(cudaMemsetAsync(b.I[0], 0, bytes, c->st), "init intensities");
+        b.bytes = bytes;
+        b.prec = prec;
+        b.N = c->mesh.N;
+        b.nd = c->D;
+        b.G = c->G;
+    }
+    if (two && !b.I[1]) {
+        CK(cudaMalloc(&b.I[1], bytes > 0 ? bytes : 4), "alloc intensities");
+        CK(cudaMemsetAsync(b.I[1], 0, bytes, c->st), "init intensities");
+        b.sign[1] = 0;
+    }
+    return SWEEP_OK;
+}
+
+double read_max(sweep_ctx* c) {
+    unsigned long long v = 0;
+    cudaMemcpyAsync(&v, c->dmax, sizeof v, cudaMemcpyDeviceToHost, c->st);
+    cudaStreamSynchronize(c->st);
+    double d;
+    memcpy(&d, &v, sizeof d);
+    return d;
+}
+
+// choose schedule and block size: time one sweep per candidate (results are identical for all)
+sweep_status autotune(sweep_ctx* c, int prec, const void* cm, const float* bc32, const sweep_opts* o, int* sched,
+                      int* threads) {
+    int& ts = c->tuned[prec == 64][c->G][0];
+    int& tt = c->tuned[prec == 64][c->G][1];
+    if (ts) {
+        *sched = ts;
+        *threads = tt;
+        return SWEEP_OK;
+    }
+    const int cand_s[2] = {SWEEP_SCHED_LEVEL, SWEEP_SCHED_DATAFLOW};
+    const int cand_t[2] = {128, 256};
+    float best = 1e30f;
+    int bs = SWEEP_SCHED_LEVEL, bt = 256;
+    SolveBuf& b = c->sb;
+    const int tb = (b.last == 0 && b.I[1]) ? 1 : 0;
+    for (int s : cand_s)
+        for (int t : cand_t) {
+            int parity = !b.sign[tb];
+            SweepArgs a = make_args(c, c->lev, prec, cm, b.I[tb], nullptr, c->G, parity, 0, 0, o);
+            a.debug_stall = 0;
+            float ms = 0;
+            sweep_status st = run_sweep(c, c->lev, prec, s, t, a, bc32, &ms);
+            if (st != SWEEP_OK) return st;
+            b.sign[tb] = parity;
+            if (ms < best) {
+                best = ms;
+                bs = s;
+                bt = t;
+            }
+        }
+    ts = bs;
+    tt = bt;
+    *sched = bs;
+    *threads = bt;
+    return SWEEP_OK;
+}
+
+// device scratch freed at scope exit
+template <typename T>
+struct DevBuf {
+    T* p = nullptr;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+};
+using Bc32 = DevBuf<float>;
+
+__global__ void k_bc_to_f32(const double* in, int64_t n, float* out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)in[i];
+}
+
+sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, double* Gam_out, bool dev,
+                        sweep_stats* stats) {
+    if (!c) return SWEEP_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    if (!c->has_mesh || !c->has_dirs || !c->has_mat) return bad(c, "set mesh, directions and material first");
+    sweep_opts o;
+    if (opts_in) o = *opts_in;
+    else sweep_default_opts(&o);
+    if (o.law != SWEEP_LAW_BALANCE) return bad(c, "unsupported law");
+    const bool plain = o.schedule == SWEEP_SCHED_PLAIN;
+    const int prec = plain ? 64 : (o.precision == 64 ? 64 : 32);
+    if (o.precision != 32 && o.precision != 64) return bad(c, "precision must be 32 or 64");
+    if (o.block_threads != 0 && o.block_threads != 128 && o.block_threads != 256)
+        return bad(c, "block_threads must be 0, 128 or 256");
+    sweep_stats S;
+    memset(&S, 0, sizeof S);
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    cudaEventRecord(t0, c->st);
+    float tc = 0, tl = 0;
+    sweep_status s = ensure_levels(c, &o, &tc, &tl);
+    if (s != SWEEP_OK) return s;
+    S.t_ms[0] = tc;
+    S.t_ms[1] = tl;
+    const int64_t N = c->mesh.N;
+    const int G = c->G, D = c->D;
+    const size_t NG = (size_t)N * G;
+    const bool has_pbc = c->mesh.n_pcells > 0;
+    s = ensure_ng(c, NG);
+    if (s != SWEEP_OK) return s;
+    s = ensure_cm(c, NG);
+    if (s != SWEEP_OK) return s;
+    s = ensure_solution(c, prec, has_pbc);
+    if (s != SWEEP_OK) return s;
+    int nblk = nblocks256(NG > (size_t)c->mesh.n_pcells ? NG : c->mesh.n_pcells);
+    if (c->mesh.n_bcells > nblk) nblk = nblocks256(c->mesh.n_bcells);
+    s = ensure_partial(c, nblk + 1);
+    if (s != SWEEP_OK) return s;
+    Bc32 bc32;
+    if (prec == 32 && c->bc) {
+        int64_t n = c->mesh.NB * G;
+        CK(cudaMalloc(&bc32.p, sizeof(float) * n), "alloc");
+        k_bc_to_f32<<<nblocks256(n), 256, 0, c->st>>>(c->bc, n, bc32.p);
+    }
+    SolveBuf& b = c->sb;
+    const void* cm = prec == 64 ? (const void*)c->cm64 : (const void*)c->cm32;
+    int sched = o.schedule, threads = o.block_threads ? o.block_threads : 256;
+    if (!plain && sched == SWEEP_SCHED_AUTO) {
+        CK(launch_prep_material(N, G, c->mesh.vol, c->ka, c->ks, c->em, nullptr, prec == 32 ? c->cm32 : nullptr,
+                                prec == 64 ? c->cm64 : nullptr, c->st), "prep");
+        int tt = 0;
+        s = autotune(c, prec, cm, bc32.p, &o, &sched, &tt);
+        if (s != SWEEP_OK) return s;
+        if (!o.block_threads) threads = tt;
+    }
+    // the periodic inflow of the first sweep: the previous solve's intensities or zeros
+    int prev = -1;
+    if (has_pbc) {
+        if (o.warm_start && b.last >= 0) prev = b.last;
+        else {
+            prev = b.last >= 0 ? b.last : 1;
+            CK(cudaMemsetAsync(b.I[prev], 0, b.bytes, c->st), "clear periodic inflow");
+            b.sign[prev] = 0;
+        }
+        CK(cudaMemsetAsync(c->jn, 0, sizeof(double) * NG, c->st), "init");
+        if (o.warm_start && b.last >= 0) {
+            CK(cudaMemsetAsync(c->dmax, 0, sizeof(unsigned long long), c->st), "init");
+            CK(launch_periodic_source(prec, c->mesh, b.I[prev], G, D, c->om64, c->w64, c->jn1, c->jn, c->dmax,
+                                      c->partial, nblk, c->st), "periodic source");
+            std::swap(c->jn, c->jn1);
+        }
+    }
+    S.schedule_used = sched;
+    int it_pbc = 0, it_scat_total = 0, n_sweeps = 0;
+    bool conv_pbc = !has_pbc, conv_scat = !c->has_scat;
+    double res_pbc = 0.0, res_pbc_mean = 0.0, res_scat = 0.0;
+    float t_sweep = 0.f;
+    int cur = has_pbc ? (prev == 0 ? 1 : 0) : 0;
+    cudaEvent_t u0, u1;
+    cudaEventCreate(&u0);
+    cudaEventCreate(&u1);
+    float t_other = 0.f;
+    for (;;) {
+        CK(cudaMemsetAsync(c->Jold, 0, sizeof(double) * NG, c->st), "init");
+        int it_scat = 0;
+        for (;;) {
+            CK(launch_prep_material(N, G, c->mesh.vol, c->ka, c->ks, c->em, c->has_scat ? c->Jold : nullptr,
+                                    prec == 32 ? c->cm32 : nullptr, prec == 64 ? c->cm64 : nullptr, c->st), "prep");
+            const int parity = !b.sign[cur];
+            SweepArgs a = make_args(c, c->lev, prec, cm, b.I[cur], has_pbc ? b.I[prev] : nullptr, G, parity, 0, 0, &o);
+            a.debug_stall = o.debug_stall && n_sweeps == 0;
+            s = run_sweep(c, c->lev, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, a, bc32.p, &t_sweep);
+            if (s != SWEEP_OK) return s;
+            b.sign[cur] = parity;
+            ++n_sweeps;
+            ++it_scat;
+            cudaEventRecord(u0, c->st);
+            CK(launch_tally(prec, b.I[cur], N, G, D, 0, c->w64, c->wsum, c->mesh.vol, c->ka, c->em, c->J, c->Gam,
+                            c->partial, nblk, c->st), "tally");
+            if (!c->has_scat) {
+                cudaEventRecord(u1, c->st);
+                cudaEventSynchronize(u1);
+                float tt = 0;
+                cudaEventElapsedTime(&tt, u0, u1);
+                t_other += tt;
+                break;
+            }
+            CK(cudaMemsetAsync(c->dmax, 0, sizeof(unsigned long long), c->st), "init");
+            CK(launch_scat_residual(NG, c->J, c->Jold, c->dmax, c->st), "scattering residual");
+            cudaEventRecord(u1, c->st);
+            res_scat = read_max(c);
+            float tt = 0;
+            cudaEventElapsedTime(&tt, u0, u1);
+            t_other += tt;
+            if (res_scat <= o.tol_scat) { conv_scat = true; break; }
+            if (it_scat >= o.max_it_scat) { conv_scat = false; break; }
+        }
+        it_scat_total += it_scat;
+        ++it_pbc;
+        if (!has_pbc) break;
+        cudaEventRecord(u0, c->st);
+        CK(cudaMemsetAsync(c->dmax, 0, sizeof(unsigned long long), c->st), "init");
+        CK(launch_periodic_source(prec, c->mesh, b.I[cur], G, D, c->om64, c->w64, c->jn1, c->jn, c->dmax, c->partial,
+                                  nblk, c->st), "periodic source");
+        int npb = nblocks256(c->mesh.n_pcells > 0 ? c->mesh.n_pcells : 1);
+        CK(launch_reduce_sum(c->partial, npb, c->red + 2, c->st), "reduce");
+        cudaEventRecord(u1, c->st);
+        res_pbc = read_max(c);
+        double hred[2] = {0, 0};
+        CK(cudaMemcpyAsync(hred, c->red + 2, sizeof hred, cudaMemcpyDeviceToHost, c->st), "read");
+        CK(cudaStreamSynchronize(c->st), "read");
+        float tt = 0;
+        cudaEventElapsedTime(&tt, u0, u1);
+        t_other += tt;
+        res_pbc_mean = NG > 0 ? hred[0] / (double)NG : 0.0;
+        std::swap(c->jn, c->jn1);
+        prev = cur;
+        cur = 1 - cur;
+        if (res_pbc < o.tol_pbc) { conv_pbc = true; break; }
+        if (it_pbc >= o.max_it_pbc) { conv_pbc = false; break; }
+    }
+    const int fin = has_pbc ? prev : cur;
+    b.last = fin;
+    // final tallies: absorbed/emitted from the last tally, escaped/injected over boundary cells
+    CK(launch_tally(prec, b.I[fin], N, G, D, 0, c->w64, c->wsum, c->mesh.vol, c->ka, c->em, c->J, c->Gam, c->partial,
+                    nblk, c->st), "tally");
+    CK(launch_reduce_sum(c->partial, nblocks256(NG), c->red, c->st), "reduce");
+    if (c->mesh.n_bcells > 0) {
+        CK(launch_boundary_tally(prec, c->mesh, b.I[fin], G, D, 0, c->om64, c->w64, c->bc, c->partial, nblk, c->st),
+           "boundary tally");
+        CK(launch_reduce_sum(c->partial, nblocks256(c->mesh.n_bcells), c->red + 2, c->st), "reduce");
+    } else {
+        CK(cudaMemsetAsync(c->red + 2, 0, 2 * sizeof(double), c->st), "init");
+    }
+    double hr[4];
+    CK(cudaMemcpyAsync(hr, c->red, sizeof hr, cudaMemcpyDeviceToHost, c->st), "read tallies");
+    cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (J_out) CK(cudaMemcpyAsync(J_out, c->J, sizeof(double) * NG, k, c->st), "copy J");
+    if (Gam_out) CK(cudaMemcpyAsync(Gam_out, c->Gam, sizeof(double) * NG, k, c->st), "copy Gamma");
+    cudaEventRecord(t1, c->st);
+    CK(cudaStreamSynchronize(c->st), "solve");
+    float ttot = 0;
+    cudaEventElapsedTime(&ttot, t0, t1);
+    cudaEventDestroy(t0); cudaEventDestroy(t1); cudaEventDestroy(u0); cudaEventDestroy(u1);
+    S.absorbed = hr[0];
+    S.emitted = hr[1];
+    S.escaped = hr[2];
+    S.injected = hr[3];
+    double in = S.emitted + S.injected;
+    S.defect = in > 0.0 ? (in - S.absorbed - S.escaped) / in : 0.0;
+    S.it_scat = it_scat_total;
+    S.it_pbc = it_pbc;
+    S.n_sweeps = n_sweeps;
+    S.res_scat = res_scat;
+    S.res_pbc = res_pbc;
+    S.res_pbc_mean = res_pbc_mean;
+    S.t_ms[2] = t_sweep;
+    S.t_ms[3] = t_other;
+    S.t_ms[4] = ttot;
+    S.updates = (double)N * D * G * n_sweeps;
+    S.updates_per_s = ttot > 0 ? S.updates / (ttot * 1e-3) : 0.0;
+    S.sweep_launches = plain ? 0 : n_sweeps;
+    int dmaxv = 0;
+    double dsum = 0;
+    for (int d : c->lev.depth) {
+        if (d > dmaxv) dmaxv = d;
+        dsum += d;
+    }
+    S.depth_max = dmaxv;
+    S.depth_mean = c->lev.depth.empty() ? 0.0 : dsum / c->lev.depth.size();
+    if (stats) *stats = S;
+    return (conv_pbc && conv_scat) ? SWEEP_OK : SWEEP_NOT_CONVERGED;
+}
+
+sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double* dlj, const double* dlg, double* gk_out,
+                          double* ge_out, bool dev, sweep_stats* stats) {
+    if (!c) return SWEEP_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    if (!c->has_mesh || !c->has_dirs || !c->has_mat) return bad(c, "set mesh, directions and material first");
+    if (c->has_scat) return bad(c, "the adjoint does not support scattering");
+    if (c->mesh.n_pcells > 0) return bad(c, "the adjoint does not support periodic faces");
+    if (c->G > 4) return bad(c, "the adjoint supports at most 4 groups");
+    if (!gk_out || !ge_out) return bad(c, "null gradient output");
+    sweep_opts o;
+    if (opts_in) o = *opts_in;
+    else sweep_default_opts(&o);
+    const bool plain = o.schedule == SWEEP_SCHED_PLAIN;
+    const int prec = plain ? 64 : (o.precision == 64 ? 64 : 32);
+    int sched = o.schedule == SWEEP_SCHED_AUTO ? SWEEP_SCHED_LEVEL : o.schedule;
+    const int threads = o.block_threads ? o.block_threads : 256;
+    const int64_t N = c->mesh.N;
+    const int G = c->G, D = c->D;
+    const size_t NG = (size_t)N * G;
+    int B = (o.dir_batch > 0 && o.dir_batch < D) ? o.dir_batch : D;
+    sweep_stats S;
+    memset(&S, 0, sizeof S);
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    cudaEventRecord(t0, c->st);
+    // device copies of the loss gradients and FP64 gradient accumulators
+    DevBuf<double> b_dlj, b_dlg, b_gk, b_ge;
+    cudaMemcpyKind kin = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (dlj) {
+        CK(cudaMalloc(&b_dlj.p, sizeof(double) * (NG > 0 ? NG : 1)), "alloc");
+        CK(cudaMemcpyAsync(b_dlj.p, dlj, sizeof(double) * NG, kin, c->st), "upload");
+    }
+    if (dlg) {
+        CK(cudaMalloc(&b_dlg.p, sizeof(double) * (NG > 0 ? NG : 1)), "alloc");
+        CK(cudaMemcpyAsync(b_dlg.p, dlg, sizeof(double) * NG, kin, c->st), "upload");
+    }
+    CK(cudaMalloc(&b_gk.p, sizeof(double) * (NG > 0 ? NG : 1)), "alloc");
+    CK(cudaMalloc(&b_ge.p, sizeof(double) * (NG > 0 ? NG : 1)), "alloc");
+    double *d_dlj = b_dlj.p, *d_dlg = b_dlg.p, *gk = b_gk.p, *ge = b_ge.p;
+    CK(cudaMemsetAsync(gk, 0, sizeof(double) * NG, c->st), "init");
+    CK(cudaMemsetAsync(ge, 0, sizeof(double) * NG, c->st), "init");
+    sweep_status s = ensure_cm(c, 2 * NG);
+    if (s != SWEEP_OK) return s;
+    // batch buffers
+    const size_t es = prec == 64 ? 8 : 4;
+    size_t bI = es * (size_t)N * B * G, bL = es * (size_t)N * B * 2 * G;
+    if (c->adj_bytes_I != bI || c->adj_bytes_L != bL) {
+        dfree(c->adjI);
+        dfree(c->adjL);
+        CK(cudaMalloc(&c->adjI, bI > 0 ? bI : 4), "alloc adjoint batch");
+        CK(cudaMalloc(&c->adjL, bL > 0 ? bL : 4), "alloc adjoint batch");
+        c->adj_bytes_I = bI;
+        c->adj_bytes_L = bL;
+    }
+    // fresh buffers each call: sign state starts at 0 after clearing
+    CK(cudaMemsetAsync(c->adjI, 0, bI, c->st), "init");
+    CK(cudaMemsetAsync(c->adjL, 0, bL, c->st), "init");
+    int signI = 0, signL = 0;
+    Bc32 bc32;
+    if (prec == 32 && c->bc) {
+        int64_t n = c->mesh.NB * G;
+        CK(cudaMalloc(&bc32.p, sizeof(float) * n), "alloc");
+        k_bc_to_f32<<<nblocks256(n), 256, 0, c->st>>>(c->bc, n, bc32.p);
+    }
+    float t_sweep = 0.f, tcl = 0.f, tlv = 0.f;
+    int n_sweeps = 0;
+    for (int d0 = 0; d0 < D; d0 += B) {
+        const int nb = (D - d0) < B ? (D - d0) : B;
+        Levels* L;
+        float a1 = 0, a2 = 0;
+        if (nb == D) {
+            s = ensure_levels(c, &o, &a1, &a2);
+            L = &c->lev;
+        } else {
+            s = run_levelise(c, c->adj_lev, d0, nb, budget_of(&o), &a1, &a2);
+            L = &c->adj_lev;
+        }
+        if (s != SWEEP_OK) return s;
+        tcl += a1;
+        tlv += a2;
+        // forward intensities of this batch (recomputed, not stored across batches)
+        CK(launch_prep_material(N, G, c->mesh.vol, c->ka, nullptr, c->em, nullptr, prec == 32 ? c->cm32 : nullptr,
+                                prec == 64 ? c->cm64 : nullptr, c->st), "prep");
+        const void* cm = prec == 64 ? (const void*)c->cm64 : (const void*)c->cm32;
+        int pI = !signI;
+        SweepArgs a = make_args(c, *L, prec, cm, c->adjI, nullptr, G, pI, 0, 0, &o);
+        a.debug_stall = 0;
+        s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, a, bc32.p, &t_sweep);
+        if (s != SWEEP_OK) return s;
+        signI = pI;
+        // transposed sweep with split non-negative sources (2G groups)
+        CK(launch_prep_adjoint_src(N, G, c->mesh.vol, c->ka, nullptr, d_dlj, d_dlg, prec == 32 ? c->cm32 : nullptr,
+                                   prec == 64 ? c->cm64 : nullptr, c->st), "prep adjoint");
+        int pL = !signL;
+        SweepArgs r = make_args(c, *L, prec, cm, c->adjL, nullptr, 2 * G, pL, 1, 0, &o);
+        r.debug_stall = 0;
+        s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, r, nullptr, &t_sweep);
+        if (s != SWEEP_OK) return s;
+        signL = pL;
+        n_sweeps += 2;
+        CK(launch_grad_accum(prec, c->adjI, c->adjL, N, G, nb, d0, c->w64, c->mesh.vol, d_dlg, gk, ge, c->st),
+           "gradient");
+    }
+    cudaMemcpyKind kout = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(gk_out, gk, sizeof(double) * NG, kout, c->st), "copy gradient");
+    CK(cudaMemcpyAsync(ge_out, ge, sizeof(double) * NG, kout, c->st), "copy gradient");
+    cudaEventRecord(t1, c->st);
+    CK(cudaStreamSynchronize(c->st), "adjoint");
+    float ttot = 0;
+    cudaEventElapsedTime(&ttot, t0, t1);
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    S.n_sweeps = n_sweeps;
+    S.t_ms[0] = tcl;
+    S.t_ms[1] = tlv;
+    S.t_ms[2] = t_sweep;
+    S.t_ms[4] = ttot;
+    S.updates = (double)N * D * G * 3;  // forward, and the transposed sweep over 2G split groups
+    S.updates_per_s = ttot > 0 ? S.updates / (ttot * 1e-3) : 0.0;
+    S.schedule_used = plain ? SWEEP_SCHED_PLAIN : sched;
+    if (stats) *stats = S;
+    return SWEEP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sweep_status sweep_solve(sweep_ctx* c, const sweep_opts* o, double* J, double* Gam, sweep_stats* st) {
+    return solve_impl(c, o, J, Gam, false, st);
+}
+
+sweep_status sweep_solve_dev(sweep_ctx* c, const sweep_opts* o, double* J, double* Gam, sweep_stats* st) {
+    return solve_impl(c, o, J, Gam, true, st);
+}
+
+sweep_status sweep_levels(sweep_ctx* c, int32_t dir, int32_t* level, int32_t* depth) {
+    if (!c) return SWEEP_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    if (!c->has_mesh || !c->has_dirs) return bad(c, "set mesh and directions first");
+    if (dir < 0 || dir >= c->D) return bad(c, "direction index out of range");
+    sweep_status s = ensure_levels(c, nullptr, nullptr, nullptr);
+    if (s != SWEEP_OK) return s;
+    if (level)
+        CK(cudaMemcpy2DAsync(level, sizeof(int32_t), c->lev.level + dir, sizeof(int32_t) * c->lev.nd,
+                             sizeof(int32_t), c->mesh.N, cudaMemcpyDeviceToHost, c->st), "copy levels");
+    CK(cudaStreamSynchronize(c->st), "copy levels");
+    if (depth) *depth = c->lev.depth[dir];
+    return SWEEP_OK;
+}
+
+sweep_status sweep_intensity(sweep_ctx* c, int32_t dir, double* out) {
+    if (!c) return SWEEP_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    if (c->sb.last < 0 || !c->sb.I[c->sb.last]) return bad(c, "no solve yet");
+    if (dir < 0 || dir >= c->sb.nd) return bad(c, "direction index out of range");
+    if (!out) return bad(c, "null output");
+    const size_t n = (size_t)c->sb.N * c->sb.G;
+    double* tmp = nullptr;
+    CK(cudaMalloc(&tmp, sizeof(double) * (n > 0 ? n : 1)), "alloc");
+    const size_t es = c->sb.prec == 64 ? 8 : 4;
+    const char* src = (const char*)c->sb.I[c->sb.last] + es * n * dir;
+    cudaError_t e = launch_to_f64(c->sb.prec, src, (int64_t)n, tmp, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    cudaFree(tmp);
+    return cuda_status(c, e, "copy intensity");
+}
+
+sweep_status sweep_adjoint(sweep_ctx* c, const sweep_opts* o, const double* dlj, const double* dlg, double* gk,
+                           double* ge, sweep_stats* st) {
+    return adjoint_impl(c, o, dlj, dlg, gk, ge, false, st);
+}
+
+sweep_status sweep_adjoint_dev(sweep_ctx* c, const sweep_opts* o, const double* dlj, const double* dlg, double* gk,
+                               double* ge, sweep_stats* st) {
+    return adjoint_impl(c, o, dlj, dlg, gk, ge, true, st);
+}
+
+}  // extern "C"

@@ -1,0 +1,261 @@
+// Internal declarations shared by the libsweep translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sweep.h"
+
+namespace sw {
+
+// ---------------------------------------------------------------------------------------------
+// Face-side encoding. A cell's row of the CSR lists every face it touches ("face sides");
+// the record is int4 {nbr, An_x, An_y, An_z} with An = A_f * n_out in FP32 bits,
+// n_out pointing out of this cell. nbr:
+//   >= 0, bit 30 clear : interior neighbour cell
+//   >= 0, bit 30 set   : periodic partner cell (nbr & NBR_MASK)
+//   <  0               : box boundary face, ordinal b = -1 - nbr (for the boundary inflow array)
+// The FP64 twin {n_out.x, n_out.y, n_out.z, A} reproduces the exact classification sign.
+// ---------------------------------------------------------------------------------------------
+constexpr int32_t NBR_PERIODIC = 0x40000000;
+constexpr int32_t NBR_MASK = 0x3fffffff;
+constexpr uint32_t TASK_PAD = 0xffffffffu;
+constexpr double FOURPI = 4.0 * 3.14159265358979323846;
+// |t32| above this fraction of sum|An_i| fixes sign(t32) == sign(t64) (FP32 rounding of An, Omega and the
+// dot product is below 6 * 2^-24 of it); inside the band the sign is recomputed in FP64.
+constexpr float BAND_REL = 1.0e-6f;
+
+struct GridBar {
+    unsigned count;
+    unsigned gen;
+};
+
+// FP64 face-side twin {n_out.x, n_out.y, n_out.z, A}, one 32-byte sector
+struct alignas(32) d4 {
+    double x, y, z, w;
+};
+
+// Device error word values (the first error wins).
+enum { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_OVERFLOW = 2 };
+
+// ---------------------------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ float ld_relaxed(const float* p) {
+    float v;
+    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ double ld_relaxed(const double* p) {
+    double v;
+    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(float* p, float v) {
+    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed(double* p, double v) {
+    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile_i32(const int* p) { return *(const volatile int*)p; }
+__device__ __forceinline__ int ld_relaxed_i32(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// L2 policy that marks lines first in line for eviction (streamed CSR records)
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// streaming read of CSR records: read-only path, no L1 allocation, evict-first in L2
+__device__ __forceinline__ int4 ld_stream_int4(const int4* p, uint64_t pol) {
+    int4 v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ bool sign_bit(float v) { return (__float_as_uint(v) >> 31) != 0; }
+__device__ __forceinline__ bool sign_bit(double v) { return (__double_as_longlong(v) >> 63) != 0; }
+
+// Exact FP64 classification value t = ((nx*Ox) + (ny*Oy)) + (nz*Oz), no fused multiply-add
+// (the same rounding sequence as the oracle, so signs agree bit for bit).
+__device__ __forceinline__ double exact_t(const d4& n, const double* om) {
+    double x = __dmul_rn(n.x, om[0]);
+    double y = __dmul_rn(n.y, om[1]);
+    double z = __dmul_rn(n.z, om[2]);
+    return __dadd_rn(__dadd_rn(x, y), z);
+}
+
+// Classification of one face side for a direction: +1 outflow, -1 inflow, 0 tie (no flux).
+// t32 is the FP32 dot product An.Omega; the FP64 twin decides inside the rounding band.
+__device__ __forceinline__ int classify_side(float t32, float ax, float ay, float az, const d4* side64,
+                                             uint32_t s, const double* om64) {
+    float band = BAND_REL * (fabsf(ax) + fabsf(ay) + fabsf(az));
+    if (t32 > band) return 1;
+    if (t32 < -band) return -1;
+    double t = exact_t(side64[s], om64);
+    return t > 0.0 ? 1 : (t < 0.0 ? -1 : 0);
+}
+
+// Grid-wide barrier for persistent cooperative kernels, with a bounded wait.
+// Returns false (and sets *err) if the wait gave up or another block reported an error.
+__device__ __forceinline__ bool grid_sync(GridBar* bar, unsigned nblocks, long long budget, int* err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned gen = ld_acquire_u32(&bar->gen);
+        __threadfence();
+        unsigned arrived = atomicAdd(&bar->count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            st_release_u32(&bar->gen, gen + 1);
+        } else {
+            long long n = 0;
+            while (ld_acquire_u32(&bar->gen) == gen) {
+                if (++n > budget || ld_volatile_i32(err) != DEV_OK) {
+                    atomicCAS(err, DEV_OK, DEV_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (ld_volatile_i32(err) != DEV_OK) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host-side structures
+// ---------------------------------------------------------------------------------------------
+struct DevMesh {
+    int64_t N = 0, F = 0, S = 0, NB = 0;  // cells, faces, face sides, boundary faces
+    uint32_t* rowptr = nullptr;            // [N+1]
+    int4* side = nullptr;                  // [S]
+    d4* side64 = nullptr;             // [S]
+    double* vol = nullptr;                 // [N]
+    int32_t* pcells = nullptr;             // cells with periodic sides
+    int64_t n_pcells = 0;
+    int32_t* bcells = nullptr;             // cells with boundary sides
+    int64_t n_bcells = 0;
+    int max_row = 0;
+    std::vector<int64_t> mesh_off;
+};
+
+struct Levels {
+    bool valid = false;
+    int d0 = 0, nd = 0;
+    int cshift = 0;
+    uint32_t cmask = 0;
+    int n_levels = 0;
+    uint32_t* raw = nullptr;     // level-contiguous, padded task list written by the levelisation
+    uint32_t* task = nullptr;    // same levels, grouped by direction within each level
+    int64_t task_cap = 0;
+    int32_t* count = nullptr;    // [N][nd]
+    int32_t* level = nullptr;    // [N][nd]
+    int32_t* lvl_cnt = nullptr;  // [N+2]
+    uint32_t* pad_off = nullptr; // [N+2] start of each level in the padded list
+    int64_t* lev_chunk = nullptr;  // device [n_levels+1] chunk (32-task) offsets
+    uint32_t* seg_off = nullptr; // device [n_levels][nd+1] per-(level, direction) segment starts
+    int64_t seg_cap = 0;         // elements allocated for seg_off
+    std::vector<int64_t> h_lev_chunk;
+    std::vector<uint32_t> h_seg_off;
+    std::vector<int32_t> depth;  // per direction
+    int64_t n_tasks = 0;
+};
+
+// Kernel argument block of the batched sweep.
+struct SweepArgs {
+    const uint32_t* task;
+    int64_t n_chunks;
+    const int64_t* lev_chunk;
+    int n_levels;
+    int cshift;
+    uint32_t cmask;
+    int nd;               // directions of this batch
+    const uint32_t* rowptr;
+    const int4* side;
+    const d4* side64;
+    const float4* om32;   // [nd]
+    const double* om64;   // [nd][3]
+    const double* w64;    // [nd] weights (adjoint source scaling)
+    const void* cm;       // [N][G] {q, dnm} in the sweep precision
+    const void* bc;       // [NB][G] boundary inflow, or null
+    void* I;              // [nd][N][G] output
+    const void* Iprev;    // [nd][N][G] previous sweep (periodic inflow), or null
+    int64_t N;
+    int G;
+    int parity;           // sign bit written with every value of this sweep
+    int reverse;          // 1 = adjoint (transposed) sweep
+    int level_sync;       // 1 = grid barrier between levels
+    GridBar* bar;
+    int* err;
+    long long spin_budget;
+    int debug_stall;
+    const float* stall_word;
+};
+
+// ---------------------------------------------------------------------------------------------
+// Kernel launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------------------------
+cudaError_t launch_build_csr(const DevMesh& m, const int32_t* d_fc, const double* d_area, const double* d_normal,
+                             const uint8_t* d_flags, int32_t* d_tmp_cnt, cudaStream_t st);
+cudaError_t launch_validate_mesh(int64_t N, int64_t F, const double* vol, const int32_t* fc, const double* area,
+                                 const double* normal, const uint8_t* flags, const int64_t* mesh_off, int n_meshes,
+                                 int* d_bad, cudaStream_t st);
+
+cudaError_t levelise(const DevMesh& m, Levels& L, const double* om64_all, const float4* om32_all, int dev_sms,
+                     GridBar* bar, int* err, long long budget, int64_t* d_scratch, cudaStream_t st, float* t_classify,
+                     float* t_levelise, std::string* msg);
+
+int sweep_max_blocks_per_sm(int precision, int threads);
+int sweep_occupancy(int precision, int G, int threads, int nd);
+cudaError_t launch_sweep(const SweepArgs& a, int precision, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_plain_level(const SweepArgs& a, uint32_t begin, uint32_t end, cudaStream_t st);
+
+cudaError_t launch_prep_material(int64_t N, int G, const double* vol, const double* ka, const double* ks,
+                                 const double* em, const double* J, float2* cm32, double2* cm64, cudaStream_t st);
+cudaError_t launch_prep_adjoint_src(int64_t N, int G, const double* vol, const double* ka, const double* ks,
+                                    const double* dl_dJ, const double* dl_dG, float2* cm32, double2* cm64,
+                                    cudaStream_t st);
+cudaError_t launch_tally(int precision, const void* I, int64_t N, int G, int nd, int d0, const double* w64,
+                         double wsum, const double* vol, const double* ka, const double* em, double* J,
+                         double* Gam, double* partial, int nblk, cudaStream_t st);
+cudaError_t launch_boundary_tally(int precision, const DevMesh& m, const void* I, int G, int nd, int d0,
+                                  const double* om64, const double* w64, const double* bc, double* partial,
+                                  int nblk, cudaStream_t st);
+cudaError_t launch_scat_residual(int64_t NG, const double* J, double* Jold, unsigned long long* d_max,
+                                 cudaStream_t st);
+cudaError_t launch_periodic_source(int precision, const DevMesh& m, const void* I, int G, int nd,
+                                   const double* om64, const double* w64, double* jn1, const double* jn,
+                                   unsigned long long* d_max, double* partial, int nblk, cudaStream_t st);
+cudaError_t launch_reduce_sum(const double* partial, int n, double* out, cudaStream_t st);
+cudaError_t launch_grad_accum(int precision, const void* I, const void* lam, int64_t N, int G, int nd, int d0,
+                              const double* w64, const double* vol, const double* dl_dG, double* gk, double* ge,
+                              cudaStream_t st);
+cudaError_t launch_fill_u32(uint32_t* p, uint32_t v, int64_t n, cudaStream_t st);
+cudaError_t launch_to_f64(int precision, const void* I, int64_t n, double* out, cudaStream_t st);
+
+}  // namespace sw

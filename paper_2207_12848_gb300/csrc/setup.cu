@@ -1,0 +1,601 @@
+// Mesh upload, CSR build, face classification (K1) and GPU Kahn levelisation (K2).
+//
+// Classification: a neighbour across face side s is downwind when n_out.Omega > 0 and upwind
+// when < 0 (paper Sec. 2.5 and Appendix A, Eq. downwindDefinition); an exact FP64 zero carries
+// no flux and creates no dependency. Periodic and boundary sides create no dependency
+// (the periodic graph is cut, Sec. 2.7).
+//
+// Levelisation: the level of a task (c, Omega) is 0 when it has no upwind cell, else
+// 1 + the largest level of its upwind cells -- the longest dependency path, which is unique
+// for an acyclic graph (Sec. 2.3). K2 is Alg. 2's Kahn queue run one wavefront at a time for
+// all directions at once: the tasks of level L decrement the upwind counters n(c, Omega) of
+// their downwind neighbours; a counter reaching zero puts that task into level L+1.
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+
+namespace sw {
+
+namespace {
+
+constexpr int SCAN_BLOCK = 1024;
+constexpr int SCAN_ITEMS = 4;
+
+// ---- exclusive scan (int32 counts -> int64 offsets), three passes ----------------------------
+__global__ void k_scan_block(const int32_t* in, int64_t n, int64_t* out, int64_t* block_sums) {
+    __shared__ int64_t s[SCAN_BLOCK];
+    int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK * SCAN_ITEMS;
+    int64_t v[SCAN_ITEMS];
+    int64_t sum = 0;
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        int64_t i = base + (int64_t)threadIdx.x * SCAN_ITEMS + k;
+        v[k] = i < n ? (int64_t)in[i] : 0;
+        sum += v[k];
+    }
+    s[threadIdx.x] = sum;
+    __syncthreads();
+    for (int off = 1; off < SCAN_BLOCK; off <<= 1) {
+        int64_t t = threadIdx.x >= off ? s[threadIdx.x - off] : 0;
+        __syncthreads();
+        s[threadIdx.x] += t;
+        __syncthreads();
+    }
+    int64_t run = s[threadIdx.x] - sum;
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        int64_t i = base + (int64_t)threadIdx.x * SCAN_ITEMS + k;
+        if (i < n) out[i] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == SCAN_BLOCK - 1) block_sums[blockIdx.x] = s[threadIdx.x];
+}
+
+__global__ void k_scan_sums(int64_t* sums, int64_t nb, int64_t* total) {
+    // one block, sequential chunks of SCAN_BLOCK
+    __shared__ int64_t s[SCAN_BLOCK];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t b0 = 0; b0 < nb; b0 += SCAN_BLOCK) {
+        int64_t i = b0 + threadIdx.x;
+        int64_t v = i < nb ? sums[i] : 0;
+        s[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < SCAN_BLOCK; off <<= 1) {
+            int64_t t = threadIdx.x >= off ? s[threadIdx.x - off] : 0;
+            __syncthreads();
+            s[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < nb) sums[i] = carry + s[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == SCAN_BLOCK - 1) carry += s[threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan_add(int64_t* out, int64_t n, const int64_t* sums) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += sums[i / (SCAN_BLOCK * SCAN_ITEMS)];
+}
+
+// exclusive scan of n int32 into out[n] (int64); total at out_total (device). scratch >= nblocks+1
+cudaError_t scan_i32(const int32_t* in, int64_t n, int64_t* out, int64_t* scratch, int64_t* out_total,
+                     cudaStream_t st) {
+    int64_t per = (int64_t)SCAN_BLOCK * SCAN_ITEMS;
+    int64_t nb = (n + per - 1) / per;
+    if (nb == 0) nb = 1;
+    k_scan_block<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(in, n, out, scratch);
+    k_scan_sums<<<1, SCAN_BLOCK, 0, st>>>(scratch, nb, out_total);
+    if (n > 0) k_scan_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, n, scratch);
+    return cudaGetLastError();
+}
+
+// ---- mesh validation -------------------------------------------------------------------------
+enum {
+    BAD_CELL_RANGE = 1, BAD_FLAGS = 2, BAD_AREA = 4, BAD_NORMAL = 8, BAD_VOLUME = 16, BAD_CROSS_MESH = 32,
+    BAD_SELF = 64
+};
+
+__device__ int64_t mesh_of(const int64_t* off, int nm, int64_t c) {
+    int lo = 0, hi = nm;  // off[lo] <= c < off[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (off[mid] <= c) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_validate_faces(int64_t N, int64_t F, const int32_t* fc, const double* area, const double* normal,
+                                 const uint8_t* flags, const int64_t* mesh_off, int nm, int* bad) {
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F) return;
+    int b = 0;
+    int32_t c0 = fc[2 * f], c1 = fc[2 * f + 1];
+    uint8_t fl = flags[f];
+    if (c0 < 0 || c0 >= N || c1 < -1 || c1 >= N) b |= BAD_CELL_RANGE;
+    bool bnd = (fl & SWEEP_FACE_BOUNDARY) != 0, per = (fl & SWEEP_FACE_PERIODIC) != 0;
+    if ((fl & ~3) || (bnd && per) || (bnd != (c1 == -1))) b |= BAD_FLAGS;
+    if (c0 == c1 && !per) b |= BAD_SELF;
+    double A = area[f];
+    if (!(A >= 0.0) || !isfinite(A)) b |= BAD_AREA;
+    double nx = normal[3 * f], ny = normal[3 * f + 1], nz = normal[3 * f + 2];
+    double n2 = nx * nx + ny * ny + nz * nz;
+    if (!(fabs(n2 - 1.0) <= 2.5e-9)) b |= BAD_NORMAL;
+    if (!b && c1 >= 0 && nm > 1 && mesh_of(mesh_off, nm, c0) != mesh_of(mesh_off, nm, c1)) b |= BAD_CROSS_MESH;
+    if (b) atomicOr(bad, b);
+}
+
+__global__ void k_validate_cells(int64_t N, const double* vol, int* bad) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    double v = vol[c];
+    if (!(v > 0.0) || !isfinite(v)) atomicOr(bad, BAD_VOLUME);
+}
+
+// ---- CSR build --------------------------------------------------------------------------------
+__global__ void k_count_sides(int64_t F, const int32_t* fc, int32_t* cnt) {
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F) return;
+    atomicAdd(&cnt[fc[2 * f]], 1);
+    if (fc[2 * f + 1] >= 0) atomicAdd(&cnt[fc[2 * f + 1]], 1);
+}
+
+__global__ void k_to_u32(const int64_t* in, int64_t n, uint32_t* out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (uint32_t)in[i];
+}
+
+__global__ void k_scatter_sides(int64_t F, const int32_t* fc, const uint32_t* rowptr, int32_t* fill, int64_t* key) {
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F) return;
+    int32_t c0 = fc[2 * f], c1 = fc[2 * f + 1];
+    uint32_t s0 = rowptr[c0] + atomicAdd(&fill[c0], 1);
+    key[s0] = 2 * f;
+    if (c1 >= 0) {
+        uint32_t s1 = rowptr[c1] + atomicAdd(&fill[c1], 1);
+        key[s1] = 2 * f + 1;
+    }
+}
+
+// rows are short: insertion sort of each row by (face, side) makes the side order deterministic
+__global__ void k_sort_rows(int64_t N, const uint32_t* rowptr, int64_t* key, int* max_row) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    uint32_t r0 = rowptr[c], r1 = rowptr[c + 1];
+    for (uint32_t i = r0 + 1; i < r1; ++i) {
+        int64_t k = key[i];
+        uint32_t j = i;
+        while (j > r0 && key[j - 1] > k) {
+            key[j] = key[j - 1];
+            --j;
+        }
+        key[j] = k;
+    }
+    atomicMax(max_row, (int)(r1 - r0));
+}
+
+__global__ void k_flag_boundary(int64_t F, const uint8_t* flags, int32_t* isb) {
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f < F) isb[f] = (flags[f] & SWEEP_FACE_BOUNDARY) ? 1 : 0;
+}
+
+__global__ void k_fill_sides(int64_t S, const int64_t* key, const int32_t* fc, const double* area,
+                             const double* normal, const uint8_t* flags, const int64_t* bidx, int4* side,
+                             d4* side64) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    int64_t k = key[s];
+    int64_t f = k >> 1;
+    int sd = (int)(k & 1);  // 0: this cell is c0 (n_out = n), 1: this cell is c1 (n_out = -n)
+    double A = area[f];
+    double nx = normal[3 * f], ny = normal[3 * f + 1], nz = normal[3 * f + 2];
+    if (sd) { nx = -nx; ny = -ny; nz = -nz; }
+    int32_t nbr;
+    uint8_t fl = flags[f];
+    if (fl & SWEEP_FACE_BOUNDARY) nbr = (int32_t)(-1 - bidx[f]);
+    else {
+        int32_t other = sd ? fc[2 * f] : fc[2 * f + 1];
+        nbr = (fl & SWEEP_FACE_PERIODIC) ? (other | NBR_PERIODIC) : other;
+    }
+    int4 r;
+    r.x = nbr;
+    r.y = __float_as_int((float)(A * nx));
+    r.z = __float_as_int((float)(A * ny));
+    r.w = __float_as_int((float)(A * nz));
+    side[s] = r;
+    side64[s] = d4{nx, ny, nz, A};
+}
+
+__global__ void k_cell_kinds(int64_t N, const uint32_t* rowptr, const int4* side, int32_t* isp, int32_t* isb) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    int p = 0, b = 0;
+    for (uint32_t s = rowptr[c]; s < rowptr[c + 1]; ++s) {
+        int32_t nb = side[s].x;
+        if (nb < 0) b = 1;
+        else if (nb & NBR_PERIODIC) p = 1;
+    }
+    isp[c] = p;
+    isb[c] = b;
+}
+
+__global__ void k_compact(int64_t N, const int32_t* flag, const int64_t* pos, int32_t* out) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < N && flag[c]) out[pos[c]] = (int32_t)c;
+}
+
+inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_validate_mesh(int64_t N, int64_t F, const double* vol, const int32_t* fc, const double* area,
+                                 const double* normal, const uint8_t* flags, const int64_t* mesh_off, int n_meshes,
+                                 int* d_bad, cudaStream_t st) {
+    if (F > 0) k_validate_faces<<<nblk(F), 256, 0, st>>>(N, F, fc, area, normal, flags, mesh_off, n_meshes, d_bad);
+    if (N > 0) k_validate_cells<<<nblk(N), 256, 0, st>>>(N, vol, d_bad);
+    return cudaGetLastError();
+}
+
+// Builds rowptr/side/side64 and the periodic/boundary cell lists of m (arrays already allocated
+// for m.S sides; m.rowptr for N+1). d_tmp_cnt: int32 scratch of max(N, F) + 1.
+cudaError_t launch_build_csr(const DevMesh& mc, const int32_t* fc, const double* area, const double* normal,
+                             const uint8_t* flags, int32_t* d_tmp, cudaStream_t st) {
+    DevMesh& m = const_cast<DevMesh&>(mc);
+    int64_t N = m.N, F = m.F, S = m.S;
+    cudaError_t e;
+    int64_t *off = nullptr, *offb = nullptr, *scratch = nullptr, *key = nullptr, *total = nullptr, *bidx = nullptr;
+    int32_t *fill = nullptr, *isp = nullptr, *isb = nullptr;
+    int* maxrow = nullptr;
+    int64_t nmax = (N > F ? N : F) + 1;
+    int64_t nsb = nmax / (SCAN_BLOCK * SCAN_ITEMS) + 2;
+#define TRY(x) do { e = (x); if (e != cudaSuccess) goto done; } while (0)
+    TRY(cudaMallocAsync(&off, sizeof(int64_t) * (nmax + 1), st));
+    TRY(cudaMallocAsync(&offb, sizeof(int64_t) * (N + 1), st));
+    TRY(cudaMallocAsync(&scratch, sizeof(int64_t) * nsb, st));
+    TRY(cudaMallocAsync(&total, sizeof(int64_t) * 2, st));
+    TRY(cudaMallocAsync(&key, sizeof(int64_t) * (S > 0 ? S : 1), st));
+    TRY(cudaMallocAsync(&bidx, sizeof(int64_t) * (F + 1), st));
+    TRY(cudaMallocAsync(&fill, sizeof(int32_t) * (N + 1), st));
+    TRY(cudaMallocAsync(&isp, sizeof(int32_t) * (N + 1), st));
+    TRY(cudaMallocAsync(&isb, sizeof(int32_t) * (nmax), st));
+    TRY(cudaMallocAsync(&maxrow, sizeof(int), st));
+    TRY(cudaMemsetAsync(d_tmp, 0, sizeof(int32_t) * (N + 1), st));
+    TRY(cudaMemsetAsync(fill, 0, sizeof(int32_t) * (N + 1), st));
+    TRY(cudaMemsetAsync(maxrow, 0, sizeof(int), st));
+    if (F > 0) k_count_sides<<<nblk(F), 256, 0, st>>>(F, fc, d_tmp);
+    TRY(scan_i32(d_tmp, N + 1, off, scratch, total, st));  // d_tmp[N] = 0 -> off[N] = S
+    k_to_u32<<<nblk(N + 1), 256, 0, st>>>(off, N + 1, m.rowptr);
+    if (F > 0) k_scatter_sides<<<nblk(F), 256, 0, st>>>(F, fc, m.rowptr, fill, key);
+    if (N > 0) k_sort_rows<<<nblk(N), 128, 0, st>>>(N, m.rowptr, key, maxrow);
+    // boundary ordinals in face order
+    if (F > 0) {
+        k_flag_boundary<<<nblk(F), 256, 0, st>>>(F, flags, isb);
+        TRY(scan_i32(isb, F, bidx, scratch, total, st));
+    }
+    if (S > 0) k_fill_sides<<<nblk(S), 256, 0, st>>>(S, key, fc, area, normal, flags, bidx, m.side, m.side64);
+    // periodic / boundary cell lists (increasing cell order)
+    if (N > 0) {
+        k_cell_kinds<<<nblk(N), 256, 0, st>>>(N, m.rowptr, m.side, isp, isb);
+        TRY(scan_i32(isp, N, off, scratch, total, st));
+        TRY(scan_i32(isb, N, offb, scratch, total + 1, st));
+    }
+    {
+        int64_t tot[2] = {0, 0};
+        int mr = 0;
+        TRY(cudaMemcpyAsync(tot, total, sizeof tot, cudaMemcpyDeviceToHost, st));
+        TRY(cudaMemcpyAsync(&mr, maxrow, sizeof mr, cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        m.max_row = mr;
+        m.n_pcells = N > 0 ? tot[0] : 0;
+        m.n_bcells = N > 0 ? tot[1] : 0;
+        if (m.n_pcells > 0) {
+            TRY(cudaMalloc(&m.pcells, sizeof(int32_t) * m.n_pcells));
+            k_compact<<<nblk(N), 256, 0, st>>>(N, isp, off, m.pcells);
+        }
+        if (m.n_bcells > 0) {
+            TRY(cudaMalloc(&m.bcells, sizeof(int32_t) * m.n_bcells));
+            k_compact<<<nblk(N), 256, 0, st>>>(N, isb, offb, m.bcells);
+        }
+        TRY(cudaGetLastError());
+        TRY(cudaStreamSynchronize(st));
+    }
+done:
+    cudaFreeAsync(off, st);
+    cudaFreeAsync(offb, st);
+    cudaFreeAsync(scratch, st);
+    cudaFreeAsync(total, st);
+    cudaFreeAsync(key, st);
+    cudaFreeAsync(bidx, st);
+    cudaFreeAsync(fill, st);
+    cudaFreeAsync(isp, st);
+    cudaFreeAsync(isb, st);
+    cudaFreeAsync(maxrow, st);
+#undef TRY
+    return e;
+}
+
+// ---------------------------------------------------------------------------------------------
+// K1: classify every face side for every direction and count upwind dependencies n(c, Omega)
+// (Alg. 2, first loop). Thread per (cell, direction); a warp reads one cell's row once.
+// Tasks with no upwind cell form level 0.
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+__global__ void k_classify(int64_t N, int nd, const uint32_t* rowptr, const int4* side, const d4* side64,
+                           const float4* om32, const double* om64, int32_t* count, int32_t* level, uint32_t* raw,
+                           int32_t* lvl_cnt, int cshift) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool active = t < N * (int64_t)nd;
+    int cnt = 0;
+    uint32_t entry = 0;
+    if (active) {
+        int64_t c = t / nd;
+        int dl = (int)(t - c * nd);
+        float4 om = om32[dl];
+        const double* o64 = om64 + 3 * dl;
+        for (uint32_t s = rowptr[c]; s < rowptr[c + 1]; ++s) {
+            int4 r = side[s];
+            if (r.x < 0 || (r.x & NBR_PERIODIC)) continue;
+            float ax = __int_as_float(r.y), ay = __int_as_float(r.z), az = __int_as_float(r.w);
+            float t32 = ax * om.x + ay * om.y + az * om.z;
+            if (classify_side(t32, ax, ay, az, side64, s, o64) < 0) ++cnt;
+        }
+        count[t] = cnt;
+        level[t] = cnt == 0 ? 0 : -1;
+        entry = ((uint32_t)dl << cshift) | (uint32_t)c;
+    }
+    bool push = active && cnt == 0;
+    unsigned m = __ballot_sync(0xffffffffu, push);
+    if (m) {
+        int lane = threadIdx.x & 31;
+        int leader = __ffs(m) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&lvl_cnt[0], __popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (push) raw[base + __popc(m & ((1u << lane) - 1))] = entry;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// K2: persistent level-synchronous Kahn over all directions. Level L occupies
+// raw[pad_off[L] .. pad_off[L] + lvl_cnt[L]), padded to a multiple of 32 with TASK_PAD so
+// that 32-task chunks never span two levels.
+// ---------------------------------------------------------------------------------------------
+constexpr int LQ_CAP = 4096;
+
+struct LeveliseArgs {
+    int64_t N;
+    int nd;
+    int cshift;
+    uint32_t cmask;
+    const uint32_t* rowptr;
+    const int4* side;
+    const d4* side64;
+    const float4* om32;
+    const double* om64;
+    int32_t* count;
+    int32_t* level;
+    uint32_t* raw;
+    int32_t* lvl_cnt;
+    uint32_t* pad_off;
+    int64_t* lev_chunk;
+    int32_t* n_levels_out;
+    GridBar* bar;
+    int* err;
+    long long budget;
+};
+
+__device__ __forceinline__ uint32_t round32(uint32_t x) { return (x + 31u) & ~31u; }
+
+__global__ void __launch_bounds__(256) k_levelise(LeveliseArgs a) {
+    __shared__ uint32_t s_q[LQ_CAP];
+    __shared__ int s_n;
+    __shared__ int s_base;
+    const unsigned nblocks = gridDim.x;
+    const int64_t gthreads = (int64_t)nblocks * blockDim.x;
+    uint32_t base = 0;
+    int n = ld_volatile_i32(&a.lvl_cnt[0]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.pad_off[0] = 0;
+        a.lev_chunk[0] = 0;
+    }
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    int L = 0;
+    while (n > 0) {
+        const uint32_t next_base = base + round32((uint32_t)n);
+        if (blockIdx.x == 0)
+            for (uint32_t i = base + n + threadIdx.x; i < next_base; i += blockDim.x) a.raw[i] = TASK_PAD;
+        for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += gthreads) {
+            int64_t i = i0 + threadIdx.x;
+            if (i < n) {
+                uint32_t e = a.raw[base + i];
+                uint32_t c = e & a.cmask;
+                uint32_t dl = e >> a.cshift;
+                float4 om = a.om32[dl];
+                const double* o64 = a.om64 + 3 * dl;
+                for (uint32_t s = a.rowptr[c]; s < a.rowptr[c + 1]; ++s) {
+                    int4 r = a.side[s];
+                    if (r.x < 0 || (r.x & NBR_PERIODIC)) continue;
+                    float ax = __int_as_float(r.y), ay = __int_as_float(r.z), az = __int_as_float(r.w);
+                    float t32 = ax * om.x + ay * om.y + az * om.z;
+                    if (classify_side(t32, ax, ay, az, a.side64, s, o64) <= 0) continue;
+                    int64_t k = (int64_t)r.x * a.nd + dl;
+                    if (atomicSub(&a.count[k], 1) == 1) {
+                        a.level[k] = L + 1;
+                        uint32_t ne = (dl << a.cshift) | (uint32_t)r.x;
+                        int p = atomicAdd(&s_n, 1);
+                        if (p < LQ_CAP) s_q[p] = ne;
+                        else a.raw[next_base + atomicAdd(&a.lvl_cnt[L + 1], 1)] = ne;
+                    }
+                }
+            }
+            __syncthreads();
+            int cnt = s_n < LQ_CAP ? s_n : LQ_CAP;
+            if (cnt > LQ_CAP / 2 || i0 + gthreads >= n) {
+                if (threadIdx.x == 0) s_base = cnt ? atomicAdd(&a.lvl_cnt[L + 1], cnt) : 0;
+                __syncthreads();
+                for (int j = threadIdx.x; j < cnt; j += blockDim.x) a.raw[next_base + s_base + j] = s_q[j];
+                __syncthreads();
+                if (threadIdx.x == 0) s_n = 0;
+                __syncthreads();
+            }
+        }
+        if (!grid_sync(a.bar, nblocks, a.budget, a.err)) return;
+        n = ld_relaxed_i32(&a.lvl_cnt[L + 1]);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            a.pad_off[L + 1] = next_base;
+            a.lev_chunk[L + 1] = next_base / 32;
+        }
+        base = next_base;
+        ++L;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.n_levels_out = L;
+}
+
+// Group each level's tasks by direction (one block per level); records per-(level, direction)
+// segment starts. Order inside a segment does not matter: tasks of one level are independent.
+__global__ void k_sort_levels(const uint32_t* raw, uint32_t* task, const uint32_t* pad_off, const int32_t* lvl_cnt,
+                              int nd, int cshift, uint32_t* seg_off) {
+    extern __shared__ int s_hist[];  // 2 * nd
+    const int L = blockIdx.x;
+    const uint32_t b0 = pad_off[L];
+    const int n = lvl_cnt[L];
+    int* fill = s_hist + nd;
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) s_hist[i] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_hist[raw[b0 + i] >> cshift], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int d = 0; d < nd; ++d) {
+            int h = s_hist[d];
+            fill[d] = run;
+            seg_off[(int64_t)L * (nd + 1) + d] = b0 + run;
+            run += h;
+        }
+        seg_off[(int64_t)L * (nd + 1) + nd] = b0 + run;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        uint32_t e = raw[b0 + i];
+        int p = atomicAdd(&fill[e >> cshift], 1);
+        task[b0 + p] = e;
+    }
+    uint32_t end = round32((uint32_t)n);
+    for (uint32_t i = n + threadIdx.x; i < end; i += blockDim.x) task[b0 + i] = TASK_PAD;
+}
+
+}  // namespace
+
+cudaError_t levelise(const DevMesh& m, Levels& L, const double* om64_all, const float4* om32_all, int dev_sms,
+                     GridBar* bar, int* err, long long budget, int64_t* d_scratch, cudaStream_t st,
+                     float* t_classify, float* t_levelise, std::string* msg) {
+    cudaError_t e;
+    const int64_t N = m.N;
+    const int nd = L.nd;
+    const float4* om32 = om32_all + L.d0;
+    const double* om64 = om64_all + 3 * (int64_t)L.d0;
+    cudaEvent_t ev[3];
+    for (auto& x : ev) cudaEventCreate(&x);
+    cudaEventRecord(ev[0], st);
+    e = cudaMemsetAsync(L.lvl_cnt, 0, sizeof(int32_t) * (N + 2), st);
+    if (e != cudaSuccess) return e;
+    int64_t tot = N * (int64_t)nd;
+    if (tot > 0)
+        k_classify<<<nblk(tot), 256, 0, st>>>(N, nd, m.rowptr, m.side, m.side64, om32, om64, L.count, L.level, L.raw,
+                                               L.lvl_cnt, L.cshift);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    cudaEventRecord(ev[1], st);
+    // persistent levelisation: one co-resident grid
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_levelise, 256, 0);
+    if (per_sm < 1) per_sm = 1;
+    int blocks = dev_sms * per_sm;
+    LeveliseArgs a;
+    a.N = N; a.nd = nd; a.cshift = L.cshift; a.cmask = L.cmask; a.rowptr = m.rowptr; a.side = m.side;
+    a.side64 = m.side64; a.om32 = om32; a.om64 = om64; a.count = L.count; a.level = L.level; a.raw = L.raw;
+    a.lvl_cnt = L.lvl_cnt; a.pad_off = L.pad_off; a.lev_chunk = L.lev_chunk;
+    a.n_levels_out = (int32_t*)d_scratch; a.bar = bar; a.err = err; a.budget = budget;
+    cudaMemsetAsync(bar, 0, sizeof(GridBar), st);
+    cudaMemsetAsync(d_scratch, 0, sizeof(int64_t), st);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(256);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_levelise, a);
+    if (e != cudaSuccess) return e;
+    int32_t nlev = 0;
+    int herr = 0;
+    cudaMemcpyAsync(&nlev, d_scratch, sizeof nlev, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&herr, err, sizeof herr, cudaMemcpyDeviceToHost, st);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    if (herr != DEV_OK) {
+        *msg = "levelisation: device wait timed out";
+        L.valid = false;
+        return cudaSuccess;
+    }
+    L.n_levels = nlev;
+    std::vector<int32_t> cnt(nlev > 0 ? nlev : 1);
+    if (nlev > 0) cudaMemcpyAsync(cnt.data(), L.lvl_cnt, sizeof(int32_t) * nlev, cudaMemcpyDeviceToHost, st);
+    L.h_lev_chunk.assign(nlev + 1, 0);
+    cudaMemcpyAsync(L.h_lev_chunk.data(), L.lev_chunk, sizeof(int64_t) * (nlev + 1), cudaMemcpyDeviceToHost, st);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    int64_t done = 0;
+    for (int i = 0; i < nlev; ++i) done += cnt[i];
+    L.n_tasks = done;
+    if (done != tot) {
+        *msg = "dependency graph is cyclic: " + std::to_string(tot - done) + " tasks never became ready";
+        L.valid = false;
+        L.n_levels = 0;
+        return cudaSuccess;
+    }
+    if ((int64_t)nlev * (nd + 1) > L.seg_cap) {
+        if (L.seg_off) cudaFree(L.seg_off);
+        L.seg_off = nullptr;
+        L.seg_cap = 0;
+        int64_t want = ((int64_t)nlev + nlev / 4 + 16) * (nd + 1);
+        e = cudaMalloc(&L.seg_off, sizeof(uint32_t) * want);
+        if (e != cudaSuccess) return e;
+        L.seg_cap = want;
+    }
+    if (nlev > 0) {
+        k_sort_levels<<<nlev, 256, 2 * nd * sizeof(int), st>>>(L.raw, L.task, L.pad_off, L.lvl_cnt, nd, L.cshift,
+                                                               L.seg_off);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    L.h_seg_off.assign((size_t)nlev * (nd + 1), 0);
+    if (nlev > 0)
+        cudaMemcpyAsync(L.h_seg_off.data(), L.seg_off, sizeof(uint32_t) * L.h_seg_off.size(), cudaMemcpyDeviceToHost,
+                        st);
+    cudaEventRecord(ev[2], st);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    L.depth.assign(nd, 0);
+    for (int lv = 0; lv < nlev; ++lv)
+        for (int d = 0; d < nd; ++d) {
+            uint32_t a0 = L.h_seg_off[(size_t)lv * (nd + 1) + d], a1 = L.h_seg_off[(size_t)lv * (nd + 1) + d + 1];
+            if (a1 > a0) L.depth[d] = lv + 1;
+        }
+    float ms1 = 0, ms2 = 0;
+    cudaEventElapsedTime(&ms1, ev[0], ev[1]);
+    cudaEventElapsedTime(&ms2, ev[1], ev[2]);
+    if (t_classify) *t_classify = ms1;
+    if (t_levelise) *t_levelise = ms2;
+    for (auto& x : ev) cudaEventDestroy(x);
+    L.valid = true;
+    return cudaSuccess;
+}
+
+}  // namespace sw

@@ -1,0 +1,327 @@
+// FP64 tallies and the per-iteration updates around the sweep (K4, K5, K6) and the
+// adjoint's gradient accumulation. Every sum runs in a fixed order, so results are
+// reproducible run to run; FP64 products and sums are separately rounded (no fused
+// multiply-add), the rounding sequence of the FP64 oracle.
+//
+//   mean intensity  J_c = (1/4pi) sum_d w_d I_c,d                     (Sec. 3.2, photon rate up to 1/13.6 eV)
+//   absorbed rate   Gamma_c = kappa_a,c V_c sum_d w_d I_c,d
+//   escaped         sum_d w_d sum_{boundary outflow sides} |a_f| I_c,d
+//   source update   q_c = eps_c/4pi + kappa_s,c V_c J_c                (Alg. 1, scattering as a fixed source)
+//   periodic source j_c = sum_d w_d sum_{periodic inflow sides} |a_f| I_partner,d   (Sec. 2.7)
+//   relative change E_c = |j^n - j^(n-1)| / (j^n + j^(n-1))             (Eq. relativeErrorPbc)
+#include "common.cuh"
+
+namespace sw {
+namespace {
+
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+
+template <typename real>
+__device__ __forceinline__ double mag(const real* p) { return fabs((double)*p); }
+
+// deterministic block sum of two values per thread into out[blockIdx][0..1]
+__device__ void block_sum2(double a, double b, double* out) {
+    __shared__ double s0[256], s1[256];
+    s0[threadIdx.x] = a;
+    s1[threadIdx.x] = b;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+            s0[threadIdx.x] += s0[threadIdx.x + off];
+            s1[threadIdx.x] += s1[threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[2 * blockIdx.x] = s0[0];
+        out[2 * blockIdx.x + 1] = s1[0];
+    }
+}
+
+__global__ void k_prep_material(int64_t N, int G, const double* vol, const double* ka, const double* ks,
+                                const double* em, const double* J, float2* cm32, double2* cm64) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * G) return;
+    int64_t c = i / G;
+    double V = vol[c];
+    double kscat = ks ? ks[i] : 0.0;
+    double q = em[i] / FOURPI;
+    if (ks && J) q = dadd(q, dmul(dmul(kscat, V), J[i]));
+    double dnm = dmul(dadd(ka[i], kscat), V);
+    if (cm64) cm64[i] = make_double2(q, dnm);
+    if (cm32) cm32[i] = make_float2((float)q, (float)dnm);
+}
+
+// adjoint sources split into non-negative parts: groups [0,G) carry g+, [G,2G) carry g-
+__global__ void k_prep_adjoint(int64_t N, int G, const double* vol, const double* ka, const double* ks,
+                               const double* dlj, const double* dlg, float2* cm32, double2* cm64) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * G) return;
+    int64_t c = i / G;
+    int g = (int)(i - c * G);
+    double V = vol[c];
+    double gd = dlg ? dmul(dmul(dlg[i], ka[i]), V) : 0.0;
+    double gj = dlj ? dlj[i] / FOURPI : 0.0;
+    double src = dadd(gd, gj);
+    double dnm = dmul(dadd(ka[i], ks ? ks[i] : 0.0), V);
+    double gp = src > 0.0 ? src : 0.0, gm = src < 0.0 ? -src : 0.0;
+    int64_t o = c * (2 * G);
+    if (cm64) {
+        cm64[o + g] = make_double2(gp, dnm);
+        cm64[o + G + g] = make_double2(gm, dnm);
+    }
+    if (cm32) {
+        cm32[o + g] = make_float2((float)gp, (float)dnm);
+        cm32[o + G + g] = make_float2((float)gm, (float)dnm);
+    }
+}
+
+template <typename real>
+__global__ void k_tally(const real* I, int64_t N, int G, int nd, const double* w64, double wsum, const double* vol,
+                        const double* ka, const double* em, double* J, double* Gam, double* partial) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double absorbed = 0.0, emitted = 0.0;
+    if (i < N * G) {
+        double s = 0.0;
+        const size_t NG = (size_t)N * G;
+        for (int d = 0; d < nd; ++d) s = dadd(s, dmul(w64[d], mag(I + d * NG + i)));
+        double j = s / FOURPI;
+        int64_t c = i / G;
+        double gam = dmul(dmul(dmul(ka[i], vol[c]), FOURPI), j);
+        J[i] = j;
+        if (Gam) Gam[i] = gam;
+        absorbed = gam;
+        emitted = dmul(em[i], wsum) / FOURPI;
+    }
+    block_sum2(absorbed, emitted, partial);
+}
+
+template <typename real>
+__global__ void k_boundary_tally(const int32_t* bcells, int64_t nb, const uint32_t* rowptr, const int4* side,
+                                 const d4* side64, const real* I, int64_t N, int G, int nd, const double* om64,
+                                 const double* w64, const double* bc, double* partial) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double esc = 0.0, inj = 0.0;
+    if (k < nb) {
+        int32_t c = bcells[k];
+        for (int d = 0; d < nd; ++d) {
+            for (uint32_t s = rowptr[c]; s < rowptr[c + 1]; ++s) {
+                int32_t nbr = side[s].x;
+                if (nbr >= 0) continue;
+                d4 n = side64[s];
+                double t = exact_t(n, om64 + 3 * d);
+                double a = dmul(n.w, fabs(t));
+                double wa = dmul(w64[d], a);
+                for (int g = 0; g < G; ++g) {
+                    if (t > 0.0) esc = dadd(esc, dmul(wa, mag(I + ((size_t)d * N + c) * G + g)));
+                    else if (t < 0.0 && bc) inj = dadd(inj, dmul(wa, bc[(size_t)(-1 - nbr) * G + g]));
+                }
+            }
+        }
+    }
+    block_sum2(esc, inj, partial);
+}
+
+__global__ void k_scat_residual(int64_t NG, const double* J, double* Jold, unsigned long long* dmax) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NG) return;
+    double dj = fabs(J[i] - Jold[i]);
+    double e;
+    if (dj == 0.0) e = 0.0;
+    else if (J[i] > 0.0) e = dj / J[i];
+    else e = INFINITY;
+    Jold[i] = J[i];
+    if (e > 0.0) atomicMax(dmax, (unsigned long long)__double_as_longlong(e));
+}
+
+template <typename real>
+__global__ void k_periodic_source(const int32_t* pcells, int64_t np, const uint32_t* rowptr, const int4* side,
+                                  const d4* side64, const real* I, int64_t N, int G, int nd, const double* om64,
+                                  const double* w64, double* jn1, const double* jn, unsigned long long* dmax,
+                                  double* partial) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double esum = 0.0;
+    if (k < np) {
+        int32_t c = pcells[k];
+        double j[8];
+        for (int g = 0; g < G; ++g) j[g] = 0.0;
+        for (int d = 0; d < nd; ++d) {
+            for (uint32_t s = rowptr[c]; s < rowptr[c + 1]; ++s) {
+                int32_t nbr = side[s].x;
+                if (nbr < 0 || !(nbr & NBR_PERIODIC)) continue;
+                d4 n = side64[s];
+                double t = exact_t(n, om64 + 3 * d);
+                if (!(t < 0.0)) continue;
+                double wa = dmul(w64[d], dmul(n.w, fabs(t)));
+                int32_t up = nbr & NBR_MASK;
+                for (int g = 0; g < G; ++g) j[g] = dadd(j[g], dmul(wa, mag(I + ((size_t)d * N + up) * G + g)));
+            }
+        }
+        double emax = 0.0;
+        for (int g = 0; g < G; ++g) {
+            size_t i = (size_t)c * G + g;
+            double s = j[g] + jn[i];
+            double e = s > 0.0 ? fabs(j[g] - jn[i]) / s : 0.0;
+            jn1[i] = j[g];
+            esum += e;
+            if (e > emax) emax = e;
+        }
+        if (emax > 0.0) atomicMax(dmax, (unsigned long long)__double_as_longlong(emax));
+    }
+    block_sum2(esum, 0.0, partial);
+}
+
+__global__ void k_reduce_sum(const double* partial, int n, double* out) {
+    __shared__ double s0[256], s1[256];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        a += partial[2 * i];
+        b += partial[2 * i + 1];
+    }
+    s0[threadIdx.x] = a;
+    s1[threadIdx.x] = b;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+            s0[threadIdx.x] += s0[threadIdx.x + off];
+            s1[threadIdx.x] += s1[threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = s0[0];
+        out[1] = s1[0];
+    }
+}
+
+// lambda of group g = lambda+ (group g) - lambda- (group G+g) of the split adjoint sweep
+template <typename real>
+__global__ void k_grad(const real* I, const real* lam, int64_t N, int G, int nd, const double* w64, const double* vol,
+                       const double* dlg, double* gk, double* ge) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * G) return;
+    int64_t c = i / G;
+    int g = (int)(i - c * G);
+    double V = vol[c];
+    double rg = dlg ? dlg[i] : 0.0;
+    double sk = gk[i], se = ge[i];
+    for (int d = 0; d < nd; ++d) {
+        double Icd = mag(I + ((size_t)d * N + c) * G + g);
+        const real* lp = lam + ((size_t)d * N + c) * (2 * G);
+        double lcd = mag(lp + g) - mag(lp + G + g);
+        sk = dadd(sk, dmul(dmul(V, Icd), dmul(w64[d], rg) - lcd));
+        se = dadd(se, lcd / FOURPI);
+    }
+    gk[i] = sk;
+    ge[i] = se;
+}
+
+__global__ void k_fill_u32(uint32_t* p, uint32_t v, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+template <typename real>
+__global__ void k_to_f64(const real* I, int64_t n, double* out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = fabs((double)I[i]);
+}
+
+inline unsigned nb(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_prep_material(int64_t N, int G, const double* vol, const double* ka, const double* ks,
+                                 const double* em, const double* J, float2* cm32, double2* cm64, cudaStream_t st) {
+    if (N * G > 0) k_prep_material<<<nb(N * G), 256, 0, st>>>(N, G, vol, ka, ks, em, J, cm32, cm64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_adjoint_src(int64_t N, int G, const double* vol, const double* ka, const double* ks,
+                                    const double* dl_dJ, const double* dl_dG, float2* cm32, double2* cm64,
+                                    cudaStream_t st) {
+    if (N * G > 0) k_prep_adjoint<<<nb(N * G), 256, 0, st>>>(N, G, vol, ka, ks, dl_dJ, dl_dG, cm32, cm64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tally(int precision, const void* I, int64_t N, int G, int nd, int d0, const double* w64,
+                         double wsum, const double* vol, const double* ka, const double* em, double* J, double* Gam,
+                         double* partial, int nblk_, cudaStream_t st) {
+    (void)nblk_;
+    unsigned b = nb(N * G);
+    if (b == 0) b = 1;
+    if (precision == 64)
+        k_tally<double><<<b, 256, 0, st>>>((const double*)I, N, G, nd, w64 + d0, wsum, vol, ka, em, J, Gam, partial);
+    else
+        k_tally<float><<<b, 256, 0, st>>>((const float*)I, N, G, nd, w64 + d0, wsum, vol, ka, em, J, Gam, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_boundary_tally(int precision, const DevMesh& m, const void* I, int G, int nd, int d0,
+                                  const double* om64, const double* w64, const double* bc, double* partial, int nblk_,
+                                  cudaStream_t st) {
+    (void)nblk_;
+    unsigned b = nb(m.n_bcells > 0 ? m.n_bcells : 1);
+    if (precision == 64)
+        k_boundary_tally<double><<<b, 256, 0, st>>>(m.bcells, m.n_bcells, m.rowptr, m.side, m.side64,
+                                                    (const double*)I, m.N, G, nd, om64 + 3 * d0, w64 + d0, bc,
+                                                    partial);
+    else
+        k_boundary_tally<float><<<b, 256, 0, st>>>(m.bcells, m.n_bcells, m.rowptr, m.side, m.side64,
+                                                   (const float*)I, m.N, G, nd, om64 + 3 * d0, w64 + d0, bc, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scat_residual(int64_t NG, const double* J, double* Jold, unsigned long long* d_max,
+                                 cudaStream_t st) {
+    if (NG > 0) k_scat_residual<<<nb(NG), 256, 0, st>>>(NG, J, Jold, d_max);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_periodic_source(int precision, const DevMesh& m, const void* I, int G, int nd, const double* om64,
+                                   const double* w64, double* jn1, const double* jn, unsigned long long* d_max,
+                                   double* partial, int nblk_, cudaStream_t st) {
+    (void)nblk_;
+    unsigned b = nb(m.n_pcells > 0 ? m.n_pcells : 1);
+    if (precision == 64)
+        k_periodic_source<double><<<b, 256, 0, st>>>(m.pcells, m.n_pcells, m.rowptr, m.side, m.side64,
+                                                     (const double*)I, m.N, G, nd, om64, w64, jn1, jn, d_max,
+                                                     partial);
+    else
+        k_periodic_source<float><<<b, 256, 0, st>>>(m.pcells, m.n_pcells, m.rowptr, m.side, m.side64,
+                                                    (const float*)I, m.N, G, nd, om64, w64, jn1, jn, d_max, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_sum(const double* partial, int n, double* out, cudaStream_t st) {
+    k_reduce_sum<<<1, 256, 0, st>>>(partial, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_accum(int precision, const void* I, const void* lam, int64_t N, int G, int nd, int d0,
+                              const double* w64, const double* vol, const double* dl_dG, double* gk, double* ge,
+                              cudaStream_t st) {
+    if (N * G <= 0) return cudaSuccess;
+    if (precision == 64)
+        k_grad<double><<<nb(N * G), 256, 0, st>>>((const double*)I, (const double*)lam, N, G, nd, w64 + d0, vol,
+                                                  dl_dG, gk, ge);
+    else
+        k_grad<float><<<nb(N * G), 256, 0, st>>>((const float*)I, (const float*)lam, N, G, nd, w64 + d0, vol, dl_dG,
+                                                 gk, ge);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_u32(uint32_t* p, uint32_t v, int64_t n, cudaStream_t st) {
+    if (n > 0) k_fill_u32<<<nb(n), 256, 0, st>>>(p, v, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_f64(int precision, const void* I, int64_t n, double* out, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (precision == 64) k_to_f64<double><<<nb(n), 256, 0, st>>>((const double*)I, n, out);
+    else k_to_f64<float><<<nb(n), 256, 0, st>>>((const float*)I, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace sw

@@ -1,4 +1,3 @@
-import ctypes
 import os
 import sys
 
@@ -11,19 +10,15 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (parity tests through the C ABI)")
+    config.addinivalue_line("markers", "slow: full-size workload (minutes)")
 
 
 def _gpu_count() -> int:
-    for name in ("libcudart.so", "libcudart.so.13", "libcudart.so.12"):
-        try:
-            rt = ctypes.CDLL(name)
-        except OSError:
-            continue
-        n = ctypes.c_int(0)
-        if rt.cudaGetDeviceCount(ctypes.byref(n)) == 0:
-            return n.value
+    try:
+        import torch
+        return torch.cuda.device_count() if torch.cuda.is_available() else 0
+    except Exception:
         return 0
-    return 0
 
 
 @pytest.fixture(scope="session")

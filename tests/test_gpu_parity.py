@@ -1,0 +1,287 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances (see the precision statement of the library):
+  levels                         bit-exact
+  FP64 sweeps (plain, batched)   1e-12 relative (max norm over the array)
+  FP32 sweeps, FP64 tallies      mean intensity 1e-5 relative per cell (cells with J >= 1e-30 max J),
+                                 photon-conservation defect 1e-6
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import configs
+from synth.mesh import FACE_PERIODIC, column_mesh, concat_meshes, lattice_mesh, voronoi_mesh
+from synth.fields import fibonacci_directions
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+DEFECT_TOL = 1e-6
+
+
+def rel_max(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def fp32_err(J, Jo):
+    m = Jo >= 1e-30 * Jo.max()
+    return float(np.max(np.abs(J[m] - Jo[m]) / Jo[m]))
+
+
+def load(ctx, p):
+    ctx.set_mesh(p.mesh)
+    ctx.set_directions(p.omega, p.weight)
+    ctx.set_material(p.kappa_abs, p.emissivity, kappa_scat=p.kappa_scat, boundary_inflow=p.boundary_inflow)
+
+
+def run_oracle(p, **kw):
+    return oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, kappa_scat=p.kappa_scat,
+                        bc_inflow=p.boundary_inflow, threads=8, **kw)
+
+
+# ---- levels ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["lattice", "voronoi", "periodic", "batch"])
+def test_levels_bit_exact(ctx, kind):
+    if kind == "lattice":
+        m = lattice_mesh(12)  # axis-aligned faces: exact ties for some directions
+        om = np.concatenate([fibonacci_directions(10, seed=1)[0], np.eye(3), -np.eye(3)])
+    elif kind == "batch":
+        rng = np.random.default_rng(7)
+        m = concat_meshes([voronoi_mesh(rng.random((n, 3)), threads=4) for n in (300, 1200, 77, 2500)])
+        om = fibonacci_directions(24, seed=3)[0]
+    else:
+        rng = np.random.default_rng(5)
+        m = voronoi_mesh(rng.random((5000, 3)), periodic=kind == "periodic", threads=4)
+        om = fibonacci_directions(33, seed=2)[0]
+    w = np.full(om.shape[0], 4 * math.pi / om.shape[0])
+    ctx.set_mesh(m)
+    ctx.set_directions(om, w)
+    rc, lev, depth = oracle.levels(m, om, threads=8)
+    assert rc == 0
+    for d in range(om.shape[0]):
+        gl, gd = ctx.levels(d)
+        assert np.array_equal(gl, lev[d]), d
+        assert gd == depth[d]
+
+
+# ---- FP64: plain per-(direction, level) launches and the batched kernel ------------------------------
+@pytest.mark.parametrize("schedule", ["plain", "level", "dataflow"])
+def test_plain32_fp64(ctx, schedule):
+    p = configs.plain32()
+    load(ctx, p)
+    J, G, st, s = ctx.solve(precision=64, schedule=schedule)
+    r = run_oracle(p)
+    assert rel_max(J, r["J"]) <= 1e-12
+    assert rel_max(G, r["Gamma"]) <= 1e-12
+    assert abs(st["defect"]) <= 1e-12
+    assert st["emitted"] == pytest.approx(r["stats"]["emitted"], rel=1e-14)
+
+
+@pytest.mark.parametrize("G", [1, 2, 3, 4])
+def test_voronoi_fp64_intensities(ctx, G):
+    p = configs.voronoi_small(3000, n_dir=12, n_groups=G, seed=G, bc_inflow=True)
+    load(ctx, p)
+    J, Gm, st, s = ctx.solve(precision=64, schedule="dataflow")
+    r = run_oracle(p, want_intensity=True)
+    for d in range(p.n_dir):
+        assert rel_max(ctx.intensity(d), r["I"][d]) <= 1e-12
+    assert rel_max(J, r["J"]) <= 1e-12
+    assert abs(st["defect"]) <= 1e-12
+
+
+# ---- FP32 sweeps with FP64 tallies ----------------------------------------------------------------------
+@pytest.mark.parametrize("schedule", ["level", "dataflow", "auto"])
+@pytest.mark.parametrize("G", [1, 2, 4])
+def test_voronoi_fp32(ctx, schedule, G):
+    p = configs.voronoi_small(6000, n_dir=16, n_groups=G, seed=10 + G, n_src=12)
+    load(ctx, p)
+    J, Gm, st, s = ctx.solve(precision=32, schedule=schedule)
+    r = run_oracle(p)
+    assert fp32_err(J, r["J"]) <= FP32_TOL
+    assert fp32_err(Gm, r["Gamma"]) <= FP32_TOL
+    assert abs(st["defect"]) <= DEFECT_TOL
+    assert st["absorbed"] == pytest.approx(r["stats"]["absorbed"], rel=FP32_TOL)
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+@pytest.mark.parametrize("reverse", [False, True])
+def test_column_closed_form(ctx, precision, reverse):
+    n, h, kap = 256, 1.0 / 256, 3.2
+    p = configs.column(n, kappa=kap, h=h, reverse=reverse)
+    load(ctx, p)
+    ctx.solve(precision=precision, schedule="dataflow")
+    I = ctx.intensity(0)[:, 0]
+    k = np.arange(n) if not reverse else np.arange(n)[::-1]
+    exact = (1.0 + kap * h) ** (-(k + 1.0))
+    tol = 1e-14 if precision == 64 else 1e-5
+    assert rel_max(I, exact) <= tol
+    assert np.max(np.abs(I - exact) / exact) <= (1e-13 if precision == 64 else 2e-5)
+
+
+# ---- iterations: scattering (Alg. 1) and periodic boundaries (Sec. 2.7) -------------------------------
+@pytest.mark.parametrize("precision", [32, 64])
+def test_scattering_iteration(ctx, precision):
+    p = configs.voronoi_small(4000, n_dir=12, n_groups=2, seed=41, scatter_albedo=0.5, n_src=8)
+    load(ctx, p)
+    # a fixed number of source iterations: both sides do exactly the same sweeps
+    J, Gm, st, s = ctx.solve(precision=precision, schedule="dataflow", tol_scat=0.0, max_it_scat=6)
+    r = run_oracle(p, tol_scat=0.0, max_it_scat=6)
+    assert st["it_scat"] == r["stats"]["it_scat"] == 6
+    if precision == 64:
+        assert rel_max(J, r["J"]) <= 1e-12
+        assert st["res_scat"] == pytest.approx(r["stats"]["res_scat"], rel=1e-9)
+    else:
+        assert fp32_err(J, r["J"]) <= FP32_TOL
+    # converged
+    J, Gm, st, s = ctx.solve(precision=precision, tol_scat=1e-8, max_it_scat=200)
+    r = run_oracle(p, tol_scat=1e-8, max_it_scat=200)
+    assert s == 0 and st["res_scat"] <= 1e-8
+    assert fp32_err(J, r["J"]) <= (1e-10 if precision == 64 else FP32_TOL)
+    assert abs(st["defect"]) <= (1e-7 if precision == 64 else DEFECT_TOL)
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_periodic_iteration(ctx, precision):
+    p = configs.voronoi_small(5000, periodic_box=True, n_dir=12, n_groups=1, seed=43, n_src=6)
+    load(ctx, p)
+    J, Gm, st, s = ctx.solve(precision=precision, schedule="level", tol_pbc=0.0, max_it_pbc=5)
+    r = run_oracle(p, tol_pbc=0.0, max_it_pbc=5)
+    assert st["it_pbc"] == r["stats"]["it_pbc"] == 5
+    if precision == 64:
+        assert rel_max(J, r["J"]) <= 1e-12
+        assert st["res_pbc"] == pytest.approx(r["stats"]["res_pbc"], rel=1e-9)
+    else:
+        assert fp32_err(J, r["J"]) <= FP32_TOL
+    J, Gm, st, s = ctx.solve(precision=precision, tol_pbc=1e-7, max_it_pbc=300)
+    r = run_oracle(p, tol_pbc=1e-7, max_it_pbc=300)
+    assert s == 0 and st["res_pbc"] < 1e-7
+    assert fp32_err(J, r["J"]) <= (1e-9 if precision == 64 else FP32_TOL)
+    assert abs(st["defect"]) <= 1e-6
+
+
+def test_periodic_warm_start(ctx):
+    p = configs.voronoi_small(3000, periodic_box=True, n_dir=8, seed=45)
+    load(ctx, p)
+    _, _, st1, _ = ctx.solve(precision=64, tol_pbc=1e-9)
+    J2, _, st2, _ = ctx.solve(precision=64, tol_pbc=1e-9, warm_start=1)
+    assert st2["it_pbc"] < st1["it_pbc"]
+    r = run_oracle(p, tol_pbc=1e-12, max_it_pbc=500)
+    assert rel_max(J2, r["J"]) <= 1e-7
+
+
+def test_batched_meshes_fp32(ctx):
+    p = configs.batched(n_meshes=6, total=20000, lo=1000, hi=8000, n_dir=16, n_groups=2, ngrid=32, threads=8)
+    load(ctx, p)
+    J, Gm, st, s = ctx.solve(precision=32)
+    r = run_oracle(p)
+    assert fp32_err(J, r["J"]) <= FP32_TOL
+    assert abs(st["defect"]) <= DEFECT_TOL
+
+
+# ---- adjoint ----------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("precision,batch", [(64, 0), (64, 5), (32, 0), (32, 7)])
+def test_adjoint_matches_oracle(ctx, precision, batch):
+    p = configs.voronoi_small(3000, n_dir=16, n_groups=2, seed=51, n_src=6)
+    load(ctx, p)
+    rng = np.random.default_rng(52)
+    dg = rng.normal(size=p.kappa_abs.shape)
+    dj = rng.normal(size=p.kappa_abs.shape)
+    gk, ge, st = ctx.adjoint(dl_dJ=dj, dl_dGamma=dg, precision=precision, dir_batch=batch, schedule="dataflow")
+    rc, ok_, oe = oracle.adjoint(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, dl_dJ=dj, dl_dGamma=dg,
+                                 threads=8)
+    assert rc == 0
+    tol = 1e-10 if precision == 64 else 1e-4
+    assert rel_max(gk, ok_) <= tol
+    assert rel_max(ge, oe) <= tol
+
+
+def test_adjoint_rejects_scattering(ctx):
+    from paper_2207_12848_gb300 import SweepError
+    p = configs.voronoi_small(500, n_dir=4, seed=53, scatter_albedo=0.3)
+    load(ctx, p)
+    with pytest.raises(SweepError) as e:
+        ctx.adjoint(dl_dGamma=np.ones_like(p.kappa_abs))
+    assert e.value.status == 1
+
+
+# ---- edge cases -------------------------------------------------------------------------------------------
+def test_single_cell_and_single_direction(ctx):
+    m = lattice_mesh(1)
+    ctx.set_mesh(m)
+    ctx.set_directions(np.array([[0.0, 0.6, 0.8]]), np.array([4 * math.pi]))
+    ctx.set_material(np.array([[2.0]]), np.array([[1.0]]))
+    J, G, st, s = ctx.solve(precision=64)
+    # one cube cell: P = 0.6 + 0.8 (projected outflow area), I = (eps/4pi) / (P + kappa V)
+    I = (1.0 / (4 * math.pi)) / (1.4 + 2.0)
+    assert J[0, 0] == pytest.approx(I, rel=1e-15)
+    assert st["depth_max"] == 1
+
+
+def test_mesh_without_faces(ctx):
+    from synth.mesh import Mesh
+    m = Mesh(volume=np.array([0.5, 0.25]), face_cells=np.zeros((0, 2), np.int32), area=np.zeros(0),
+             normal=np.zeros((0, 3)), flags=np.zeros(0, np.uint8))
+    ctx.set_mesh(m)
+    om, w = fibonacci_directions(4, seed=0)
+    ctx.set_directions(om, w)
+    ctx.set_material(np.array([[1.0], [2.0]]), np.array([[1.0], [3.0]]))
+    J, G, st, s = ctx.solve(precision=32)
+    # no faces: every photon is absorbed in place, Gamma = eps
+    assert np.allclose(G[:, 0], [1.0, 3.0], rtol=1e-6)
+
+
+def test_zero_absorption_streaming(ctx):
+    p = configs.voronoi_small(2000, n_dir=8, seed=55)
+    load(ctx, p)
+    ctx.set_material(np.zeros_like(p.kappa_abs), p.emissivity)
+    J, G, st, s = ctx.solve(precision=64)
+    assert st["absorbed"] == 0.0
+    assert st["escaped"] == pytest.approx(st["emitted"], rel=1e-13)
+
+
+def test_odd_group_count_and_many_directions(ctx):
+    p = configs.voronoi_small(1500, n_dir=200, n_groups=5, seed=57)
+    load(ctx, p)
+    J, G, st, s = ctx.solve(precision=32)
+    r = run_oracle(p)
+    assert fp32_err(J, r["J"]) <= FP32_TOL
+
+
+# ---- full-size workload in the benchmark's launch configuration: sampled parity and properties -------
+@pytest.mark.slow
+def test_periodic_headline_full_size(ctx):
+    p = configs.periodic()
+    load(ctx, p)
+    J, G, st, s = ctx.solve(precision=32, relevel=1)
+    assert s == 0 and st["res_pbc"] < 1e-6
+    assert abs(st["defect"]) <= DEFECT_TOL
+    # levels of sampled directions, bit-exact
+    for d in (0, 77):
+        rc, lev, depth = oracle.levels(p.mesh, p.omega[d:d + 1], threads=1)
+        gl, gd = ctx.levels(d)
+        assert np.array_equal(gl, lev[0]) and gd == depth[0]
+    # per-task balance of the final sweep for a sampled direction, evaluated in FP64 from the
+    # GPU's own intensities (the cell update must hold for every cell)
+    d = 5
+    I = ctx.intensity(d)[:, 0]
+    m = p.mesh
+    t = (m.normal[:, 0] * p.omega[d, 0] + m.normal[:, 1] * p.omega[d, 1]) + m.normal[:, 2] * p.omega[d, 2]
+    a = m.area * np.abs(t)
+    c0, c1 = m.face_cells[:, 0], m.face_cells[:, 1]
+    per = (m.flags & FACE_PERIODIC) != 0
+    up = np.where(t > 0, c0, c1)
+    down = np.where(t > 0, c1, c0)
+    P = np.bincount(up[t != 0], weights=a[t != 0], minlength=m.n_cells)
+    inflow = np.bincount(down[(t != 0) & ~per], weights=(a * I[up])[(t != 0) & ~per], minlength=m.n_cells)
+    q = p.emissivity[:, 0] / (4 * math.pi)
+    lhs = (P + p.kappa_abs[:, 0] * m.volume) * I
+    rhs = q + inflow
+    # periodic inflow comes from the previous iteration: compare only cells without periodic faces
+    has_p = np.zeros(m.n_cells, bool)
+    has_p[c0[per]] = True
+    has_p[c1[per]] = True
+    ok = ~has_p & (rhs > 1e-30 * rhs.max())
+    assert np.max(np.abs(lhs[ok] - rhs[ok]) / rhs[ok]) <= 1e-5
