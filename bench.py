@@ -1,0 +1,458 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 transport sweep (cell x direction x group updates/s, % of HBM roofline).
+
+One step = one solve of the headline workload with the inputs resident in HBM:
+classification + levelisation of all directions, then the periodic-boundary iteration
+(batched FP32 sweep + FP64 tallies + periodic exchange) until max |E_i| < 1e-6.
+Prints ONE JSON line (rank 0). Under torchrun every rank solves its own box (seed + rank):
+weak scaling, no data-path collective.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload periodic|batched]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell·dir·group sweep updates/s and % HBM roofline, batched FP32 vs plain FP64 sweep"
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_sweep_periodic_2p22.txt")
+WORKLOADS = {
+    "periodic": "periodic Voronoi box, 2^22 cells sampled ~rho (lognormal, P(k)~k^-2.5, sigma_ln=1.5), 10^4 "
+                "log-uniform sources, absorption only, 128 directions, 1 group, periodic iteration to E<1e-6",
+    "batched": "64 Poisson-Voronoi meshes of log-uniform size (2^12..2^17, 2^22 cells), lognormal kappa, "
+               "8 sources/mesh, 128 directions, 2 groups, one persistent launch",
+}
+
+
+# ---------------------------------------------------------------------------------------------
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class Dist:
+    """Barrier and max-reduction across ranks (no-op for one rank)."""
+
+    def __init__(self, backend: str | None = None):
+        self.rank, self.world, self.local = dist_env()
+        self.pg = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            if backend is None:
+                backend = "nccl" if torch.cuda.is_available() else "gloo"
+            dist.init_process_group(backend)
+            self.dist = dist
+            self.backend = backend
+            self.pg = True
+
+    def barrier(self):
+        if self.pg:
+            if self.backend == "nccl":
+                import torch
+                self.dist.barrier(device_ids=[self.local])
+            else:
+                self.dist.barrier()
+
+    def reduce(self, vals: list[float], op: str) -> list[float]:
+        if not self.pg:
+            return list(vals)
+        import torch
+        dev = "cuda" if self.backend == "nccl" else "cpu"
+        t = torch.tensor(vals, dtype=torch.float64, device=dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX if op == "max" else self.dist.ReduceOp.SUM)
+        return [float(x) for x in t.cpu()]
+
+    def close(self):
+        if self.pg:
+            self.dist.destroy_process_group()
+
+
+def aggregate(dist: Dist, elapsed_s: float, updates: float) -> tuple[float, float]:
+    """Whole-job throughput: updates summed over ranks / slowest rank's time."""
+    t = dist.reduce([elapsed_s], "max")[0]
+    u = dist.reduce([updates], "sum")[0]
+    return u / t, t
+
+
+# ---------------------------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("sweep.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2207_12848_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch of the batched sweep from the committed ncu summary, if still current."""
+    if workload != "periodic" or not os.path.exists(PROFILE_SUMMARY):
+        return None
+    vals = {}
+    with open(PROFILE_SUMMARY) as f:
+        for line in f:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_sha") != kernel_sha():
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def make_problem(workload: str, rank: int, threads: int | None, cells: int | None = None):
+    from synth import configs
+    if workload == "periodic":
+        return configs.periodic(n_cells=cells or 1 << 22, seed=4 + 100 * rank, threads=threads)
+    if workload == "batched":
+        return configs.batched(total=cells or 1 << 22, seed=1 + 100 * rank, threads=threads)
+    raise ValueError(workload)
+
+
+def bytes_per_update(p) -> float:
+    """Algorithmic DRAM bytes per (cell, direction, group) update.
+
+    Per task (cell, direction): the row bounds (8 B) and every face-side record of the cell
+    (16 B each: neighbour + A n_out in FP32), F_bar = face sides / cells. Per group: the
+    source/denominator pair (8 B, FP32) and the intensity write (4 B); the upwind re-reads
+    hit L2 (the wavefront is on chip) and are not counted.
+    """
+    m = p.mesh
+    S = 2 * m.n_faces - int((m.face_cells[:, 1] < 0).sum())
+    fbar = S / m.n_cells
+    G = p.n_groups
+    return (8.0 + 16.0 * fbar) / G + 12.0, fbar
+
+
+# ---------------------------------------------------------------------------------------------
+def cpu_baseline(p, seconds_target: float = 15.0) -> dict:
+    """The FP64 oracle as it stands, on a bounded sample: one sweep of a subset of directions."""
+    import numpy as np
+
+    import oracle
+    cores = os.cpu_count() or 1
+    N, G = p.mesh.n_cells, p.n_groups
+    # calibrate on one direction, then size the sample to ~seconds_target of CPU work
+    t0 = time.perf_counter()
+    oracle.solve(p.mesh, p.omega[:1], np.full(1, 4 * math.pi), p.kappa_abs, p.emissivity, max_it_pbc=1, threads=1)
+    t1 = time.perf_counter() - t0
+    nd = int(max(cores, min(p.n_dir, round(seconds_target / max(t1, 1e-3)))))
+    nd = min(nd, p.n_dir)
+    nd = max(cores * max(1, nd // cores), 1) if nd >= cores else nd
+    nd = min(nd, p.n_dir)
+    om = p.omega[:nd]
+    w = np.full(nd, 4 * math.pi / nd)
+    t0 = time.perf_counter()
+    oracle.solve(p.mesh, om, w, p.kappa_abs, p.emissivity, max_it_pbc=1, threads=min(cores, nd))
+    dt = time.perf_counter() - t0
+    ups = N * nd * G / dt
+    return {"value": ups, "unit": "updates/s", "cores": min(cores, nd), "kind": "oracle",
+            "sample": "one FP64 sweep of %d of %d directions over all %d cells (Alg. 2 task queue, threads over "
+                      "directions), %.1f s wall" % (nd, p.n_dir, N, dt)}
+
+
+def run_reference(args, dist: Dist):
+    """The reference arm: the FP64 CPU oracle on the host cores, each step a bounded sample."""
+    if dist.rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    p = make_problem(args.workload, 0, None, args.cells)
+    cores = os.cpu_count() or 1
+    nd = min(p.n_dir, cores)
+    om, w = p.omega[:nd], np.full(nd, 4 * math.pi / nd)
+    N, G = p.mesh.n_cells, p.n_groups
+    for _ in range(args.warmup):
+        oracle.solve(p.mesh, om, w, p.kappa_abs, p.emissivity, max_it_pbc=1, threads=nd)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.solve(p.mesh, om, w, p.kappa_abs, p.emissivity, max_it_pbc=1, threads=nd)
+    dt = time.perf_counter() - t0
+    v = N * nd * G * args.steps / dt
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "updates/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOADS[args.workload], "n_cells": N, "n_dir": p.n_dir, "n_groups": G,
+                      "sample_dirs": nd},
+           "cpu_baseline": {"value": v, "unit": "updates/s", "cores": nd, "kind": "oracle",
+                            "sample": "one FP64 sweep of %d of %d directions per step" % (nd, p.n_dir)},
+           "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def run_ours(args, dist: Dist):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_2207_12848_gb300 import Context, default_opts
+
+    torch.cuda.set_device(dist.local)
+    if dist.rank == 0 or dist.world == 1:
+        __graft_entry__.build()
+    dist.barrier()
+    __graft_entry__.build()
+    p = make_problem(args.workload, dist.rank, args.threads, args.cells)
+    stream = torch.cuda.current_stream()
+    N, D, G = p.mesh.n_cells, p.n_dir, p.n_groups
+    ctx = Context(dist.local, stream.cuda_stream)
+    ctx.set_mesh(p.mesh)
+    ctx.set_directions(p.omega, p.weight)
+    ka = torch.from_numpy(p.kappa_abs).cuda()
+    em = torch.from_numpy(p.emissivity).cuda()
+    ctx.set_material(ka, em)
+    J = torch.empty((N, G), dtype=torch.float64, device="cuda")
+    Gm = torch.empty_like(J)
+    opts = default_opts(precision=32, relevel=1, tol_pbc=1e-6, max_it_pbc=200)
+    for _ in range(args.warmup):
+        ctx.solve_dev(J, Gm, opts)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = Clocks(dist.local)
+    clocks.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    dist.barrier()
+    ev0.record(stream)
+    agg = {"updates": 0.0, "sweep_ms": 0.0, "sweeps": 0, "launches": 0, "classify_ms": 0.0, "levelise_ms": 0.0,
+           "it_pbc": [], "defect": [], "res_pbc": []}
+    for _ in range(args.steps):
+        st, s = ctx.solve_dev(J, Gm, opts)
+        agg["updates"] += st["updates"]
+        agg["sweep_ms"] += st["t_sweep_ms"]
+        agg["sweeps"] += st["sweep_launches"]
+        agg["launches"] += st["kernel_launches"]
+        agg["classify_ms"] += st["t_classify_ms"]
+        agg["levelise_ms"] += st["t_levelise_ms"]
+        agg["it_pbc"].append(st["it_pbc"])
+        agg["defect"].append(st["defect"])
+        agg["res_pbc"].append(st["res_pbc"])
+        last = st
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    clk = clocks.stop()
+    value, tmax = aggregate(dist, elapsed, agg["updates"])
+
+    # roofline of the dominant kernel (the batched sweep), CUDA events around each launch
+    bpu, fbar = bytes_per_update(p)
+    avg_launch_s = agg["sweep_ms"] / max(1, agg["sweeps"]) / 1e3
+    alg_bytes = bpu * N * D * G
+    peaks = measured_peaks()
+    achieved = alg_bytes / avg_launch_s / 1e9
+    roof = {"bound": "hbm", "kernel": "k_sweep<float,%d> (dataflow/level persistent sweep)" % G,
+            "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+            "peak_source": peaks["source"], "traffic": profiled_traffic(args.workload),
+            "bytes_per_update": bpu, "face_sides_per_cell": fbar, "updates_per_launch": N * D * G,
+            "avg_launch_ms": avg_launch_s * 1e3}
+
+    extra = {}
+    if dist.rank == 0 and not args.quick:
+        # plain FP64 per-(direction, level) sweep, same mesh, one sweep; and FP32/FP64 batched single sweeps
+        o1 = default_opts(precision=32, max_it_pbc=1, tol_pbc=0.0)
+        st32, _ = ctx.solve_dev(J, Gm, o1)
+        o64 = default_opts(precision=64, max_it_pbc=1, tol_pbc=0.0)
+        st64, _ = ctx.solve_dev(J, Gm, o64)
+        op = default_opts(schedule="plain", max_it_pbc=1, tol_pbc=0.0)
+        stp, _ = ctx.solve_dev(J, Gm, op)
+        u1 = N * D * G
+        extra["plain_fp64"] = {
+            "sweep_ms": stp["t_sweep_ms"], "updates_per_s": u1 / (stp["t_sweep_ms"] / 1e3),
+            "batched_fp32_sweep_ms": st32["t_sweep_ms"], "batched_fp64_sweep_ms": st64["t_sweep_ms"],
+            "speedup_fp32_vs_plain": stp["t_sweep_ms"] / st32["t_sweep_ms"],
+            "speedup_fp64_batched_vs_plain": stp["t_sweep_ms"] / st64["t_sweep_ms"],
+            "plain_launches": stp["kernel_launches"]}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        m = p.mesh
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        hv, hfc, har, hnr, hfl = pin(m.volume), pin(m.face_cells), pin(m.area), pin(m.normal), pin(m.flags)
+        hom, hw, hka, hem = pin(p.omega), pin(p.weight), pin(p.kappa_abs), pin(p.emissivity)
+        h2d = sum(a.nbytes for a in (hv, hfc, har, hnr, hfl, hom, hw, hka, hem))
+        d2h = 2 * N * G * 8
+        ctx2 = Context(dist.local, stream.cuda_stream)
+        o = default_opts(precision=32, tol_pbc=1e-6, max_it_pbc=200)
+
+        def e2e_step():
+            ctx2.set_mesh(volume=hv, face_cells=hfc, area=har, normal=hnr, flags=hfl)
+            ctx2.set_directions(hom, hw)
+            ctx2.set_material(hka, hem)
+            return ctx2.solve(o)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        dist.barrier()
+        n_e2e = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        upd = 0.0
+        for _ in range(n_e2e):
+            _, _, st, _ = e2e_step()
+            upd += st["updates"]
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        dist.barrier()
+        ev, _ = aggregate(dist, te, upd)
+        e2e = {"value": ev, "unit": "updates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": 1e3 * te / n_e2e}
+        ctx2.close()
+
+    cpu = None
+    if dist.rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(p)
+    ctx.close()
+    if dist.rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": dist.world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": WORKLOADS[args.workload], "n_cells": N, "n_dir": D, "n_groups": G,
+                          "face_sides_per_cell": round(fbar, 3), "precision": "FP32 intensities, FP64 tallies",
+                          "l2": "no flush: >10 GB resident working set, 78x the 129 MB L2",
+                          "step": "classify + levelise + periodic iteration to max|E|<1e-6",
+                          "parallelism": "one independent box per GPU" if dist.world > 1 else "1 GPU"},
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": agg["launches"],
+               "clocks": clk,
+               "solve": {"it_pbc": agg["it_pbc"], "defect_max": max(abs(x) for x in agg["defect"]),
+                         "res_pbc": max(agg["res_pbc"]), "depth_max": last["depth_max"],
+                         "depth_mean": last["depth_mean"], "classify_ms": agg["classify_ms"] / args.steps,
+                         "levelise_ms": agg["levelise_ms"] / args.steps,
+                         "sweep_ms_per_launch": avg_launch_s * 1e3,
+                         "schedule": {1: "level", 2: "dataflow"}.get(last["schedule_used"], last["schedule_used"]),
+                         "lanes_per_task": last["lanes_used"], "threads_per_block": last["threads_used"]}}
+        out.update(extra)
+        print(json.dumps(out))
+
+
+def run_profile_case(args):
+    """Small fixed case for ncu captures: one solve with two sweeps, no autotuning, no extras."""
+    import torch
+
+    import __graft_entry__
+    from paper_2207_12848_gb300 import Context, default_opts
+    __graft_entry__.build()
+    p = make_problem(args.workload, 0, args.threads, args.cells or 1 << 20)
+    ctx = Context(0, torch.cuda.current_stream().cuda_stream)
+    ctx.set_mesh(p.mesh)
+    ctx.set_directions(p.omega, p.weight)
+    ctx.set_material(p.kappa_abs, p.emissivity)
+    o = default_opts(precision=32, schedule=args.schedule, lanes_per_task=args.lanes, block_threads=256,
+                     max_it_pbc=2, tol_pbc=0.0)
+    ctx.solve(o)  # warm-up: module loading, first-touch of buffers
+    J, G, st, s = ctx.solve(o)
+    ctx.close()
+    print(json.dumps({"profile_case": args.workload, "n_cells": p.mesh.n_cells, "sweeps": st["n_sweeps"],
+                      "sweep_ms_per_launch": st["t_sweep_ms"] / max(1, st["n_sweeps"]),
+                      "levelise_ms": st["t_levelise_ms"], "depth_max": st["depth_max"]}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="periodic", choices=sorted(WORKLOADS))
+    ap.add_argument("--threads", type=int, default=None)
+    ap.add_argument("--cells", type=int, default=None, help="smaller problem (testing only; not a bench line)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the plain-FP64 comparison sweep")
+    ap.add_argument("--profile-case", action="store_true", help="small fixed solve for ncu captures")
+    ap.add_argument("--schedule", default="dataflow", choices=["level", "dataflow"])
+    ap.add_argument("--lanes", type=int, default=8, choices=[1, 2, 4, 8, 16])
+    args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args)
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    dist = Dist("gloo" if args.impl == "reference" else None)
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist)
+        else:
+            run_ours(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

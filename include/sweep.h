@@ -77,7 +77,7 @@ typedef struct {
     int32_t use_graph;    /* 1: capture one iteration in a CUDA graph and replay it */
     int64_t spin_budget;  /* bound on each device-side wait, in polls (0 = default, about 1 s) */
     int32_t debug_stall;  /* TEST ONLY: 1 makes the first sweep task wait on a word nothing writes */
-    int32_t reserved;
+    int32_t lanes_per_task; /* lanes cooperating on one task in the batched sweep: 1..16, a power of 2 (0 = autotuned) */
 } sweep_opts;
 
 typedef struct {
@@ -94,6 +94,10 @@ typedef struct {
     double updates_per_s;      /* updates / (t_ms[4] / 1000) */
     int32_t sweep_launches;    /* batched-sweep kernel launches timed in t_ms[2] */
     int32_t schedule_used;     /* SWEEP_SCHED_* that ran */
+    int32_t kernel_launches;   /* all kernels this call launched (including the autotuner's) */
+    int32_t lanes_used;        /* lanes per task of the batched sweep that ran */
+    int32_t threads_used;      /* threads per block of the batched sweep that ran */
+    int32_t reserved;
 } sweep_stats;
 
 /* Fill *opts with defaults: precision 32, AUTO schedule, tolerances 1e-6, 100 iterations. */

@@ -35,7 +35,8 @@ class sweep_opts(ctypes.Structure):
                 ("max_it_scat", ctypes.c_int32), ("tol_scat", ctypes.c_double), ("max_it_pbc", ctypes.c_int32),
                 ("warm_start", ctypes.c_int32), ("tol_pbc", ctypes.c_double), ("dir_batch", ctypes.c_int32),
                 ("relevel", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("spin_budget", ctypes.c_int64), ("debug_stall", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("spin_budget", ctypes.c_int64), ("debug_stall", ctypes.c_int32),
+                ("lanes_per_task", ctypes.c_int32)]
 
 
 class sweep_stats(ctypes.Structure):
@@ -45,7 +46,8 @@ class sweep_stats(ctypes.Structure):
                 ("injected", ctypes.c_double), ("absorbed", ctypes.c_double), ("escaped", ctypes.c_double),
                 ("defect", ctypes.c_double), ("t_ms", ctypes.c_double * 8), ("updates", ctypes.c_double),
                 ("updates_per_s", ctypes.c_double), ("sweep_launches", ctypes.c_int32),
-                ("schedule_used", ctypes.c_int32)]
+                ("schedule_used", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
+                ("lanes_used", ctypes.c_int32), ("threads_used", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "t_ms"}

@@ -64,7 +64,8 @@ struct sweep_ctx {
     void* adjL = nullptr;
     size_t adj_bytes_I = 0, adj_bytes_L = 0;
     // autotuner: schedule and block size per (precision, G)
-    int tuned[2][9][2] = {};
+    int tuned[2][9][3] = {};
+    int64_t launches = 0;  // kernels launched by this context
 };
 
 namespace {
@@ -81,6 +82,12 @@ sweep_status cuda_status(sweep_ctx* c, cudaError_t e, const char* what) {
         cudaError_t _e = (x);                             \
         if (_e != cudaSuccess) return cuda_status(c, _e, what); \
     } while (0)
+// a checked call that launches one kernel
+#define CKL(x, what)     \
+    do {                 \
+        ++c->launches;   \
+        CK(x, what);     \
+    } while (0)
 
 sweep_status bad(sweep_ctx* c, const std::string& m) {
     c->err = m;
@@ -94,7 +101,7 @@ void dfree(T*& p) {
 }
 
 void free_levels(Levels& L) {
-    dfree(L.raw); dfree(L.task); dfree(L.count); dfree(L.level); dfree(L.lvl_cnt); dfree(L.pad_off);
+    dfree(L.raw); dfree(L.task); dfree(L.trec); dfree(L.info); dfree(L.level); dfree(L.lvl_cnt); dfree(L.pad_off);
     dfree(L.lev_chunk); dfree(L.seg_off);
     L = Levels();
 }
@@ -139,7 +146,8 @@ sweep_status alloc_levels(sweep_ctx* c, Levels& L, int d0, int nd) {
     L.task_cap = N * (int64_t)nd + 32 * (N + 2);
     CK(cudaMalloc(&L.raw, sizeof(uint32_t) * L.task_cap), "alloc task list");
     CK(cudaMalloc(&L.task, sizeof(uint32_t) * L.task_cap), "alloc task list");
-    CK(cudaMalloc(&L.count, sizeof(int32_t) * N * nd), "alloc counts");
+    CK(cudaMalloc(&L.trec, sizeof(int4) * L.task_cap), "alloc task records");
+    CK(cudaMalloc(&L.info, sizeof(int4) * N * nd), "alloc classification");
     CK(cudaMalloc(&L.level, sizeof(int32_t) * N * nd), "alloc levels");
     CK(cudaMalloc(&L.lvl_cnt, sizeof(int32_t) * (N + 2)), "alloc level counts");
     CK(cudaMalloc(&L.pad_off, sizeof(uint32_t) * (N + 2)), "alloc level offsets");
@@ -155,6 +163,7 @@ sweep_status run_levelise(sweep_ctx* c, Levels& L, int d0, int nd, long long bud
     std::string msg;
     CK(levelise(c->mesh, L, c->om64, c->om32, c->sms, c->bar, c->derr, budget, c->scratch, c->st, t1, t2, &msg),
        "levelise");
+    c->launches += 3;  // classification, levelisation, per-level direction grouping
     if (!L.valid) {
         c->err = msg;
         if (msg.find("cyclic") != std::string::npos) return SWEEP_ERR_CYCLE;
@@ -216,6 +225,7 @@ SweepArgs make_args(sweep_ctx* c, const Levels& L, int precision, const void* cm
     SweepArgs a;
     memset(&a, 0, sizeof a);
     a.task = L.task;
+    a.trec = L.trec;
     a.n_chunks = L.h_lev_chunk.empty() ? 0 : L.h_lev_chunk.back();
     a.lev_chunk = L.lev_chunk;
     a.n_levels = L.n_levels;
@@ -246,9 +256,10 @@ SweepArgs make_args(sweep_ctx* c, const Levels& L, int precision, const void* cm
     return a;
 }
 
-sweep_status run_sweep(sweep_ctx* c, const Levels& L, int precision, int schedule, int threads, SweepArgs a,
-                       const float* bc32, float* ms) {
+sweep_status run_sweep(sweep_ctx* c, const Levels& L, int precision, int schedule, int threads, int lanes,
+                       SweepArgs a, const float* bc32, float* ms) {
     if (precision == 32) a.bc = a.reverse ? nullptr : bc32;
+    a.lanes = lanes;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -261,14 +272,14 @@ sweep_status run_sweep(sweep_ctx* c, const Levels& L, int precision, int schedul
             for (int li = 0; li < L.n_levels; ++li) {
                 const int lv = a.reverse ? L.n_levels - 1 - li : li;
                 uint32_t b0 = L.h_seg_off[(size_t)lv * (nd + 1) + d], b1 = L.h_seg_off[(size_t)lv * (nd + 1) + d + 1];
-                if (b1 > b0) CK(launch_plain_level(a, b0, b1, c->st), "plain sweep");
+                if (b1 > b0) CKL(launch_plain_level(a, b0, b1, c->st), "plain sweep");
             }
         }
     } else {
-        int per_sm = sweep_occupancy(precision, a.G, threads, L.nd);
+        int per_sm = sweep_occupancy(precision, a.G, threads, L.nd, lanes, a.reverse);
         if (per_sm < 1) return bad(c, "sweep kernel does not fit on an SM");
         a.level_sync = schedule == SWEEP_SCHED_LEVEL ? 1 : 0;
-        CK(launch_sweep(a, precision, c->sms * per_sm, threads, c->st), "sweep launch");
+        CKL(launch_sweep(a, precision, c->sms * per_sm, threads, c->st), "sweep launch");
     }
     cudaEventRecord(e1, c->st);
     int herr = 0;
@@ -592,39 +603,44 @@ double read_max(sweep_ctx* c) {
 
 // choose schedule and block size: time one sweep per candidate (results are identical for all)
 sweep_status autotune(sweep_ctx* c, int prec, const void* cm, const float* bc32, const sweep_opts* o, int* sched,
-                      int* threads) {
-    int& ts = c->tuned[prec == 64][c->G][0];
-    int& tt = c->tuned[prec == 64][c->G][1];
-    if (ts) {
-        *sched = ts;
-        *threads = tt;
+                      int* threads, int* lanes) {
+    int* t3 = c->tuned[prec == 64][c->G];
+    if (t3[0]) {
+        *sched = t3[0];
+        *threads = t3[1];
+        *lanes = t3[2];
         return SWEEP_OK;
     }
     const int cand_s[2] = {SWEEP_SCHED_LEVEL, SWEEP_SCHED_DATAFLOW};
     const int cand_t[2] = {128, 256};
+    const int cand_l[5] = {1, 2, 4, 8, 16};
     float best = 1e30f;
-    int bs = SWEEP_SCHED_LEVEL, bt = 256;
+    int bs = SWEEP_SCHED_DATAFLOW, bt = 256, bl = 4;
     SolveBuf& b = c->sb;
     const int tb = (b.last == 0 && b.I[1]) ? 1 : 0;
     for (int s : cand_s)
-        for (int t : cand_t) {
-            int parity = !b.sign[tb];
-            SweepArgs a = make_args(c, c->lev, prec, cm, b.I[tb], nullptr, c->G, parity, 0, 0, o);
-            a.debug_stall = 0;
-            float ms = 0;
-            sweep_status st = run_sweep(c, c->lev, prec, s, t, a, bc32, &ms);
-            if (st != SWEEP_OK) return st;
-            b.sign[tb] = parity;
-            if (ms < best) {
-                best = ms;
-                bs = s;
-                bt = t;
+        for (int t : cand_t)
+            for (int l : cand_l) {
+                int parity = !b.sign[tb];
+                SweepArgs a = make_args(c, c->lev, prec, cm, b.I[tb], nullptr, c->G, parity, 0, 0, o);
+                a.debug_stall = 0;
+                float ms = 0;
+                sweep_status st = run_sweep(c, c->lev, prec, s, t, l, a, bc32, &ms);
+                if (st != SWEEP_OK) return st;
+                b.sign[tb] = parity;
+                if (ms < best) {
+                    best = ms;
+                    bs = s;
+                    bt = t;
+                    bl = l;
+                }
             }
-        }
-    ts = bs;
-    tt = bt;
+    t3[0] = bs;
+    t3[1] = bt;
+    t3[2] = bl;
     *sched = bs;
     *threads = bt;
+    *lanes = bl;
     return SWEEP_OK;
 }
 
@@ -657,8 +673,11 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     if (o.precision != 32 && o.precision != 64) return bad(c, "precision must be 32 or 64");
     if (o.block_threads != 0 && o.block_threads != 128 && o.block_threads != 256)
         return bad(c, "block_threads must be 0, 128 or 256");
+    if (o.lanes_per_task < 0 || o.lanes_per_task > 16 || (o.lanes_per_task & (o.lanes_per_task - 1)))
+        return bad(c, "lanes_per_task must be 0, 1, 2, 4, 8 or 16");
     sweep_stats S;
     memset(&S, 0, sizeof S);
+    const int64_t launches0 = c->launches;
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
@@ -687,17 +706,20 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
         int64_t n = c->mesh.NB * G;
         CK(cudaMalloc(&bc32.p, sizeof(float) * n), "alloc");
         k_bc_to_f32<<<nblocks256(n), 256, 0, c->st>>>(c->bc, n, bc32.p);
+        ++c->launches;
     }
     SolveBuf& b = c->sb;
     const void* cm = prec == 64 ? (const void*)c->cm64 : (const void*)c->cm32;
     int sched = o.schedule, threads = o.block_threads ? o.block_threads : 256;
+    int lanes = o.lanes_per_task ? o.lanes_per_task : 4;
     if (!plain && sched == SWEEP_SCHED_AUTO) {
-        CK(launch_prep_material(N, G, c->mesh.vol, c->ka, c->ks, c->em, nullptr, prec == 32 ? c->cm32 : nullptr,
+        CKL(launch_prep_material(N, G, c->mesh.vol, c->ka, c->ks, c->em, nullptr, prec == 32 ? c->cm32 : nullptr,
                                 prec == 64 ? c->cm64 : nullptr, c->st), "prep");
-        int tt = 0;
-        s = autotune(c, prec, cm, bc32.p, &o, &sched, &tt);
+        int tt = 0, tl = 0;
+        s = autotune(c, prec, cm, bc32.p, &o, &sched, &tt, &tl);
         if (s != SWEEP_OK) return s;
         if (!o.block_threads) threads = tt;
+        if (!o.lanes_per_task) lanes = tl;
     }
     // the periodic inflow of the first sweep: the previous solve's intensities or zeros
     int prev = -1;
@@ -711,12 +733,14 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
         CK(cudaMemsetAsync(c->jn, 0, sizeof(double) * NG, c->st), "init");
         if (o.warm_start && b.last >= 0) {
             CK(cudaMemsetAsync(c->dmax, 0, sizeof(unsigned long long), c->st), "init");
-            CK(launch_periodic_source(prec, c->mesh, b.I[prev], G, D, c->om64, c->w64, c->jn1, c->jn, c->dmax,
+            CKL(launch_periodic_source(prec, c->mesh, b.I[prev], G, D, c->om64, c->w64, c->jn1, c->jn, c->dmax,
                                       c->partial, nblk, c->st), "periodic source");
             std::swap(c->jn, c->jn1);
         }
     }
     S.schedule_used = sched;
+    S.lanes_used = lanes;
+    S.threads_used = threads;
     int it_pbc = 0, it_scat_total = 0, n_sweeps = 0;
     bool conv_pbc = !has_pbc, conv_scat = !c->has_scat;
     double res_pbc = 0.0, res_pbc_mean = 0.0, res_scat = 0.0;
@@ -730,18 +754,18 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
         CK(cudaMemsetAsync(c->Jold, 0, sizeof(double) * NG, c->st), "init");
         int it_scat = 0;
         for (;;) {
-            CK(launch_prep_material(N, G, c->mesh.vol, c->ka, c->ks, c->em, c->has_scat ? c->Jold : nullptr,
+            CKL(launch_prep_material(N, G, c->mesh.vol, c->ka, c->ks, c->em, c->has_scat ? c->Jold : nullptr,
                                     prec == 32 ? c->cm32 : nullptr, prec == 64 ? c->cm64 : nullptr, c->st), "prep");
             const int parity = !b.sign[cur];
             SweepArgs a = make_args(c, c->lev, prec, cm, b.I[cur], has_pbc ? b.I[prev] : nullptr, G, parity, 0, 0, &o);
             a.debug_stall = o.debug_stall && n_sweeps == 0;
-            s = run_sweep(c, c->lev, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, a, bc32.p, &t_sweep);
+            s = run_sweep(c, c->lev, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, lanes, a, bc32.p, &t_sweep);
             if (s != SWEEP_OK) return s;
             b.sign[cur] = parity;
             ++n_sweeps;
             ++it_scat;
             cudaEventRecord(u0, c->st);
-            CK(launch_tally(prec, b.I[cur], N, G, D, 0, c->w64, c->wsum, c->mesh.vol, c->ka, c->em, c->J, c->Gam,
+            CKL(launch_tally(prec, b.I[cur], N, G, D, 0, c->w64, c->wsum, c->mesh.vol, c->ka, c->em, c->J, c->Gam,
                             c->partial, nblk, c->st), "tally");
             if (!c->has_scat) {
                 cudaEventRecord(u1, c->st);
@@ -752,7 +776,7 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
                 break;
             }
             CK(cudaMemsetAsync(c->dmax, 0, sizeof(unsigned long long), c->st), "init");
-            CK(launch_scat_residual(NG, c->J, c->Jold, c->dmax, c->st), "scattering residual");
+            CKL(launch_scat_residual(NG, c->J, c->Jold, c->dmax, c->st), "scattering residual");
             cudaEventRecord(u1, c->st);
             res_scat = read_max(c);
             float tt = 0;
@@ -766,10 +790,10 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
         if (!has_pbc) break;
         cudaEventRecord(u0, c->st);
         CK(cudaMemsetAsync(c->dmax, 0, sizeof(unsigned long long), c->st), "init");
-        CK(launch_periodic_source(prec, c->mesh, b.I[cur], G, D, c->om64, c->w64, c->jn1, c->jn, c->dmax, c->partial,
+        CKL(launch_periodic_source(prec, c->mesh, b.I[cur], G, D, c->om64, c->w64, c->jn1, c->jn, c->dmax, c->partial,
                                   nblk, c->st), "periodic source");
         int npb = nblocks256(c->mesh.n_pcells > 0 ? c->mesh.n_pcells : 1);
-        CK(launch_reduce_sum(c->partial, npb, c->red + 2, c->st), "reduce");
+        CKL(launch_reduce_sum(c->partial, npb, c->red + 2, c->st), "reduce");
         cudaEventRecord(u1, c->st);
         res_pbc = read_max(c);
         double hred[2] = {0, 0};
@@ -788,13 +812,13 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     const int fin = has_pbc ? prev : cur;
     b.last = fin;
     // final tallies: absorbed/emitted from the last tally, escaped/injected over boundary cells
-    CK(launch_tally(prec, b.I[fin], N, G, D, 0, c->w64, c->wsum, c->mesh.vol, c->ka, c->em, c->J, c->Gam, c->partial,
+    CKL(launch_tally(prec, b.I[fin], N, G, D, 0, c->w64, c->wsum, c->mesh.vol, c->ka, c->em, c->J, c->Gam, c->partial,
                     nblk, c->st), "tally");
-    CK(launch_reduce_sum(c->partial, nblocks256(NG), c->red, c->st), "reduce");
+    CKL(launch_reduce_sum(c->partial, nblocks256(NG), c->red, c->st), "reduce");
     if (c->mesh.n_bcells > 0) {
-        CK(launch_boundary_tally(prec, c->mesh, b.I[fin], G, D, 0, c->om64, c->w64, c->bc, c->partial, nblk, c->st),
+        CKL(launch_boundary_tally(prec, c->mesh, b.I[fin], G, D, 0, c->om64, c->w64, c->bc, c->partial, nblk, c->st),
            "boundary tally");
-        CK(launch_reduce_sum(c->partial, nblocks256(c->mesh.n_bcells), c->red + 2, c->st), "reduce");
+        CKL(launch_reduce_sum(c->partial, nblocks256(c->mesh.n_bcells), c->red + 2, c->st), "reduce");
     } else {
         CK(cudaMemsetAsync(c->red + 2, 0, 2 * sizeof(double), c->st), "init");
     }
@@ -834,6 +858,7 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     }
     S.depth_max = dmaxv;
     S.depth_mean = c->lev.depth.empty() ? 0.0 : dsum / c->lev.depth.size();
+    S.kernel_launches = (int32_t)(c->launches - launches0);
     if (stats) *stats = S;
     return (conv_pbc && conv_scat) ? SWEEP_OK : SWEEP_NOT_CONVERGED;
 }
@@ -852,7 +877,8 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
     else sweep_default_opts(&o);
     const bool plain = o.schedule == SWEEP_SCHED_PLAIN;
     const int prec = plain ? 64 : (o.precision == 64 ? 64 : 32);
-    int sched = o.schedule == SWEEP_SCHED_AUTO ? SWEEP_SCHED_LEVEL : o.schedule;
+    int sched = o.schedule == SWEEP_SCHED_AUTO ? SWEEP_SCHED_DATAFLOW : o.schedule;
+    const int lanes = o.lanes_per_task ? o.lanes_per_task : 4;
     const int threads = o.block_threads ? o.block_threads : 256;
     const int64_t N = c->mesh.N;
     const int G = c->G, D = c->D;
@@ -860,6 +886,7 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
     int B = (o.dir_batch > 0 && o.dir_batch < D) ? o.dir_batch : D;
     sweep_stats S;
     memset(&S, 0, sizeof S);
+    const int64_t launches0 = c->launches;
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
@@ -902,6 +929,7 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
         int64_t n = c->mesh.NB * G;
         CK(cudaMalloc(&bc32.p, sizeof(float) * n), "alloc");
         k_bc_to_f32<<<nblocks256(n), 256, 0, c->st>>>(c->bc, n, bc32.p);
+        ++c->launches;
     }
     float t_sweep = 0.f, tcl = 0.f, tlv = 0.f;
     int n_sweeps = 0;
@@ -920,26 +948,26 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
         tcl += a1;
         tlv += a2;
         // forward intensities of this batch (recomputed, not stored across batches)
-        CK(launch_prep_material(N, G, c->mesh.vol, c->ka, nullptr, c->em, nullptr, prec == 32 ? c->cm32 : nullptr,
+        CKL(launch_prep_material(N, G, c->mesh.vol, c->ka, nullptr, c->em, nullptr, prec == 32 ? c->cm32 : nullptr,
                                 prec == 64 ? c->cm64 : nullptr, c->st), "prep");
         const void* cm = prec == 64 ? (const void*)c->cm64 : (const void*)c->cm32;
         int pI = !signI;
         SweepArgs a = make_args(c, *L, prec, cm, c->adjI, nullptr, G, pI, 0, 0, &o);
         a.debug_stall = 0;
-        s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, a, bc32.p, &t_sweep);
+        s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, lanes, a, bc32.p, &t_sweep);
         if (s != SWEEP_OK) return s;
         signI = pI;
         // transposed sweep with split non-negative sources (2G groups)
-        CK(launch_prep_adjoint_src(N, G, c->mesh.vol, c->ka, nullptr, d_dlj, d_dlg, prec == 32 ? c->cm32 : nullptr,
+        CKL(launch_prep_adjoint_src(N, G, c->mesh.vol, c->ka, nullptr, d_dlj, d_dlg, prec == 32 ? c->cm32 : nullptr,
                                    prec == 64 ? c->cm64 : nullptr, c->st), "prep adjoint");
         int pL = !signL;
         SweepArgs r = make_args(c, *L, prec, cm, c->adjL, nullptr, 2 * G, pL, 1, 0, &o);
         r.debug_stall = 0;
-        s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, r, nullptr, &t_sweep);
+        s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, lanes, r, nullptr, &t_sweep);
         if (s != SWEEP_OK) return s;
         signL = pL;
         n_sweeps += 2;
-        CK(launch_grad_accum(prec, c->adjI, c->adjL, N, G, nb, d0, c->w64, c->mesh.vol, d_dlg, gk, ge, c->st),
+        CKL(launch_grad_accum(prec, c->adjI, c->adjL, N, G, nb, d0, c->w64, c->mesh.vol, d_dlg, gk, ge, c->st),
            "gradient");
     }
     cudaMemcpyKind kout = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -959,6 +987,7 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
     S.updates = (double)N * D * G * 3;  // forward, and the transposed sweep over 2G split groups
     S.updates_per_s = ttot > 0 ? S.updates / (ttot * 1e-3) : 0.0;
     S.schedule_used = plain ? SWEEP_SCHED_PLAIN : sched;
+    S.kernel_launches = (int32_t)(c->launches - launches0);
     if (stats) *stats = S;
     return SWEEP_OK;
 }

@@ -103,6 +103,12 @@ __device__ __forceinline__ double exact_t(const d4& n, const double* om) {
     return __dadd_rn(__dadd_rn(x, y), z);
 }
 
+// FP32 weight of a face side: An.Omega with one fixed rounding sequence (used by every kernel, so the
+// two sides of a face get weights of exactly equal magnitude)
+__device__ __forceinline__ float dot32(float ax, float ay, float az, const float4& om) {
+    return fmaf(az, om.z, fmaf(ay, om.y, __fmul_rn(ax, om.x)));
+}
+
 // Classification of one face side for a direction: +1 outflow, -1 inflow, 0 tie (no flux).
 // t32 is the FP32 dot product An.Omega; the FP64 twin decides inside the rounding band.
 __device__ __forceinline__ int classify_side(float t32, float ax, float ay, float az, const d4* side64,
@@ -173,7 +179,8 @@ struct Levels {
     uint32_t* raw = nullptr;     // level-contiguous, padded task list written by the levelisation
     uint32_t* task = nullptr;    // same levels, grouped by direction within each level
     int64_t task_cap = 0;
-    int32_t* count = nullptr;    // [N][nd]
+    int4* info = nullptr;        // [N][nd] {upwind count, P_c (FP32), inflow mask, outflow mask}
+    int4* trec = nullptr;        // task records {entry, row start, P_c, inflow mask}, same order as task
     int32_t* level = nullptr;    // [N][nd]
     int32_t* lvl_cnt = nullptr;  // [N+2]
     uint32_t* pad_off = nullptr; // [N+2] start of each level in the padded list
@@ -189,6 +196,7 @@ struct Levels {
 // Kernel argument block of the batched sweep.
 struct SweepArgs {
     const uint32_t* task;
+    const int4* trec;     // task records (FP32 forward sweep)
     int64_t n_chunks;
     const int64_t* lev_chunk;
     int n_levels;
@@ -210,6 +218,7 @@ struct SweepArgs {
     int parity;           // sign bit written with every value of this sweep
     int reverse;          // 1 = adjoint (transposed) sweep
     int level_sync;       // 1 = grid barrier between levels
+    int lanes;            // lanes cooperating on one task (4 or 8) in the batched kernel
     GridBar* bar;
     int* err;
     long long spin_budget;
@@ -230,8 +239,7 @@ cudaError_t levelise(const DevMesh& m, Levels& L, const double* om64_all, const 
                      GridBar* bar, int* err, long long budget, int64_t* d_scratch, cudaStream_t st, float* t_classify,
                      float* t_levelise, std::string* msg);
 
-int sweep_max_blocks_per_sm(int precision, int threads);
-int sweep_occupancy(int precision, int G, int threads, int nd);
+int sweep_occupancy(int precision, int G, int threads, int nd, int lanes, int reverse);
 cudaError_t launch_sweep(const SweepArgs& a, int precision, int blocks, int threads, cudaStream_t st);
 cudaError_t launch_plain_level(const SweepArgs& a, uint32_t begin, uint32_t end, cudaStream_t st);
 

@@ -323,8 +323,12 @@ done:
 // ---------------------------------------------------------------------------------------------
 namespace {
 
+// info[c][d] = {n(c, Omega): upwind interior cells,
+//               P_c: FP32 projected outflow area (sign bit set when the row has more than 32 sides),
+//               bit k: side k (< 32) is an inflow side (any kind),
+//               bit k: side k (< 32) is an outflow side to an interior cell}
 __global__ void k_classify(int64_t N, int nd, const uint32_t* rowptr, const int4* side, const d4* side64,
-                           const float4* om32, const double* om64, int32_t* count, int32_t* level, uint32_t* raw,
+                           const float4* om32, const double* om64, int4* info, int32_t* level, uint32_t* raw,
                            int32_t* lvl_cnt, int cshift) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool active = t < N * (int64_t)nd;
@@ -335,14 +339,27 @@ __global__ void k_classify(int64_t N, int nd, const uint32_t* rowptr, const int4
         int dl = (int)(t - c * nd);
         float4 om = om32[dl];
         const double* o64 = om64 + 3 * dl;
-        for (uint32_t s = rowptr[c]; s < rowptr[c + 1]; ++s) {
+        const uint32_t r0 = rowptr[c], r1 = rowptr[c + 1];
+        float P = 0.f;
+        uint32_t inm = 0u, outm = 0u;
+        for (uint32_t s = r0; s < r1; ++s) {
             int4 r = side[s];
-            if (r.x < 0 || (r.x & NBR_PERIODIC)) continue;
             float ax = __int_as_float(r.y), ay = __int_as_float(r.z), az = __int_as_float(r.w);
-            float t32 = ax * om.x + ay * om.y + az * om.z;
-            if (classify_side(t32, ax, ay, az, side64, s, o64) < 0) ++cnt;
+            float t32 = dot32(ax, ay, az, om);
+            int sgn = classify_side(t32, ax, ay, az, side64, s, o64);
+            if (sgn == 0) continue;
+            const uint32_t k = s - r0;
+            const bool interior = r.x >= 0 && !(r.x & NBR_PERIODIC);
+            if (sgn > 0) {
+                P += fabsf(t32);
+                if (k < 32 && interior) outm |= 1u << k;
+            } else {
+                if (k < 32) inm |= 1u << k;
+                if (interior) ++cnt;
+            }
         }
-        count[t] = cnt;
+        int pbits = __float_as_int(P) | ((r1 - r0 > 32u) ? (int)0x80000000 : 0);
+        info[t] = make_int4(cnt, pbits, (int)inm, (int)outm);
         level[t] = cnt == 0 ? 0 : -1;
         entry = ((uint32_t)dl << cshift) | (uint32_t)c;
     }
@@ -364,6 +381,8 @@ __global__ void k_classify(int64_t N, int nd, const uint32_t* rowptr, const int4
 // that 32-task chunks never span two levels.
 // ---------------------------------------------------------------------------------------------
 constexpr int LQ_CAP = 4096;
+constexpr int KL = 4;  // lanes per task in the levelisation
+constexpr int KU = 8;  // face sides per lane per pass
 
 struct LeveliseArgs {
     int64_t N;
@@ -375,7 +394,7 @@ struct LeveliseArgs {
     const d4* side64;
     const float4* om32;
     const double* om64;
-    int32_t* count;
+    int4* info;
     int32_t* level;
     uint32_t* raw;
     int32_t* lvl_cnt;
@@ -394,7 +413,6 @@ __global__ void __launch_bounds__(256) k_levelise(LeveliseArgs a) {
     __shared__ int s_n;
     __shared__ int s_base;
     const unsigned nblocks = gridDim.x;
-    const int64_t gthreads = (int64_t)nblocks * blockDim.x;
     uint32_t base = 0;
     int n = ld_volatile_i32(&a.lvl_cnt[0]);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -408,25 +426,52 @@ __global__ void __launch_bounds__(256) k_levelise(LeveliseArgs a) {
         const uint32_t next_base = base + round32((uint32_t)n);
         if (blockIdx.x == 0)
             for (uint32_t i = base + n + threadIdx.x; i < next_base; i += blockDim.x) a.raw[i] = TASK_PAD;
-        for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += gthreads) {
-            int64_t i = i0 + threadIdx.x;
+        // KL lanes per task: lane j of a group owns the sides r0 + j + k*KL, loaded together; the
+        // counter decrements of a pass are issued together too
+        const int64_t tpb = blockDim.x / KL;  // tasks per block per round
+        const int64_t tpg = (int64_t)nblocks * tpb;
+        const int gl = threadIdx.x % KL;
+        for (int64_t i0 = (int64_t)blockIdx.x * tpb; i0 < n; i0 += tpg) {
+            const int64_t i = i0 + threadIdx.x / KL;
             if (i < n) {
-                uint32_t e = a.raw[base + i];
-                uint32_t c = e & a.cmask;
-                uint32_t dl = e >> a.cshift;
-                float4 om = a.om32[dl];
+                const uint32_t e = a.raw[base + i];
+                const uint32_t c = e & a.cmask;
+                const uint32_t dl = e >> a.cshift;
+                const float4 om = a.om32[dl];
                 const double* o64 = a.om64 + 3 * dl;
-                for (uint32_t s = a.rowptr[c]; s < a.rowptr[c + 1]; ++s) {
-                    int4 r = a.side[s];
-                    if (r.x < 0 || (r.x & NBR_PERIODIC)) continue;
-                    float ax = __int_as_float(r.y), ay = __int_as_float(r.z), az = __int_as_float(r.w);
-                    float t32 = ax * om.x + ay * om.y + az * om.z;
-                    if (classify_side(t32, ax, ay, az, a.side64, s, o64) <= 0) continue;
-                    int64_t k = (int64_t)r.x * a.nd + dl;
-                    if (atomicSub(&a.count[k], 1) == 1) {
-                        a.level[k] = L + 1;
-                        uint32_t ne = (dl << a.cshift) | (uint32_t)r.x;
-                        int p = atomicAdd(&s_n, 1);
+                const uint32_t r0 = a.rowptr[c], r1 = a.rowptr[c + 1];
+                // downwind interior sides among the first 32 come from the classification mask;
+                // sides past 32 (rare) are classified here
+                const uint32_t outm = (uint32_t)a.info[(int64_t)c * a.nd + dl].w;
+                for (uint32_t b = r0; b < r1; b += KL * KU) {
+                    int4 r[KU];
+#pragma unroll
+                    for (int k = 0; k < KU; ++k) {
+                        const uint32_t s = b + gl + k * KL;
+                        const uint32_t idx = s - r0;
+                        const bool need = s < r1 && (idx >= 32u || ((outm >> idx) & 1u));
+                        r[k] = need ? a.side[s] : make_int4(-1, 0, 0, 0);
+                    }
+                    int old[KU];
+#pragma unroll
+                    for (int k = 0; k < KU; ++k) {
+                        old[k] = 0;
+                        const uint32_t s = b + gl + k * KL;
+                        if (r[k].x < 0 || (r[k].x & NBR_PERIODIC)) continue;
+                        if (s - r0 >= 32u) {
+                            const float ax = __int_as_float(r[k].y), ay = __int_as_float(r[k].z),
+                                        az = __int_as_float(r[k].w);
+                            if (classify_side(dot32(ax, ay, az, om), ax, ay, az, a.side64, s, o64) <= 0) continue;
+                        }
+                        old[k] = atomicSub(&a.info[(int64_t)r[k].x * a.nd + dl].x, 1);
+                    }
+#pragma unroll
+                    for (int k = 0; k < KU; ++k) {
+                        if (old[k] != 1) continue;
+                        const int64_t kk = (int64_t)r[k].x * a.nd + dl;
+                        a.level[kk] = L + 1;
+                        const uint32_t ne = (dl << a.cshift) | (uint32_t)r[k].x;
+                        const int p = atomicAdd(&s_n, 1);
                         if (p < LQ_CAP) s_q[p] = ne;
                         else a.raw[next_base + atomicAdd(&a.lvl_cnt[L + 1], 1)] = ne;
                     }
@@ -434,7 +479,7 @@ __global__ void __launch_bounds__(256) k_levelise(LeveliseArgs a) {
             }
             __syncthreads();
             int cnt = s_n < LQ_CAP ? s_n : LQ_CAP;
-            if (cnt > LQ_CAP / 2 || i0 + gthreads >= n) {
+            if (cnt > LQ_CAP / 2 || i0 + tpg >= n) {
                 if (threadIdx.x == 0) s_base = cnt ? atomicAdd(&a.lvl_cnt[L + 1], cnt) : 0;
                 __syncthreads();
                 for (int j = threadIdx.x; j < cnt; j += blockDim.x) a.raw[next_base + s_base + j] = s_q[j];
@@ -458,7 +503,8 @@ __global__ void __launch_bounds__(256) k_levelise(LeveliseArgs a) {
 // Group each level's tasks by direction (one block per level); records per-(level, direction)
 // segment starts. Order inside a segment does not matter: tasks of one level are independent.
 __global__ void k_sort_levels(const uint32_t* raw, uint32_t* task, const uint32_t* pad_off, const int32_t* lvl_cnt,
-                              int nd, int cshift, uint32_t* seg_off) {
+                              int nd, int cshift, uint32_t* seg_off, uint32_t cmask, const uint32_t* rowptr,
+                              const int4* info, int4* trec) {
     extern __shared__ int s_hist[];  // 2 * nd
     const int L = blockIdx.x;
     const uint32_t b0 = pad_off[L];
@@ -481,11 +527,17 @@ __global__ void k_sort_levels(const uint32_t* raw, uint32_t* task, const uint32_
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         uint32_t e = raw[b0 + i];
-        int p = atomicAdd(&fill[e >> cshift], 1);
+        const uint32_t dl = e >> cshift, c = e & cmask;
+        int p = atomicAdd(&fill[dl], 1);
         task[b0 + p] = e;
+        const int4 inf = info[(int64_t)c * nd + dl];
+        trec[b0 + p] = make_int4((int)e, (int)rowptr[c], inf.y, inf.z);
     }
     uint32_t end = round32((uint32_t)n);
-    for (uint32_t i = n + threadIdx.x; i < end; i += blockDim.x) task[b0 + i] = TASK_PAD;
+    for (uint32_t i = n + threadIdx.x; i < end; i += blockDim.x) {
+        task[b0 + i] = TASK_PAD;
+        trec[b0 + i] = make_int4((int)TASK_PAD, 0, 0, 0);
+    }
 }
 
 }  // namespace
@@ -505,7 +557,7 @@ cudaError_t levelise(const DevMesh& m, Levels& L, const double* om64_all, const 
     if (e != cudaSuccess) return e;
     int64_t tot = N * (int64_t)nd;
     if (tot > 0)
-        k_classify<<<nblk(tot), 256, 0, st>>>(N, nd, m.rowptr, m.side, m.side64, om32, om64, L.count, L.level, L.raw,
+        k_classify<<<nblk(tot), 256, 0, st>>>(N, nd, m.rowptr, m.side, m.side64, om32, om64, L.info, L.level, L.raw,
                                                L.lvl_cnt, L.cshift);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -517,7 +569,7 @@ cudaError_t levelise(const DevMesh& m, Levels& L, const double* om64_all, const 
     int blocks = dev_sms * per_sm;
     LeveliseArgs a;
     a.N = N; a.nd = nd; a.cshift = L.cshift; a.cmask = L.cmask; a.rowptr = m.rowptr; a.side = m.side;
-    a.side64 = m.side64; a.om32 = om32; a.om64 = om64; a.count = L.count; a.level = L.level; a.raw = L.raw;
+    a.side64 = m.side64; a.om32 = om32; a.om64 = om64; a.info = L.info; a.level = L.level; a.raw = L.raw;
     a.lvl_cnt = L.lvl_cnt; a.pad_off = L.pad_off; a.lev_chunk = L.lev_chunk;
     a.n_levels_out = (int32_t*)d_scratch; a.bar = bar; a.err = err; a.budget = budget;
     cudaMemsetAsync(bar, 0, sizeof(GridBar), st);
@@ -571,7 +623,7 @@ cudaError_t levelise(const DevMesh& m, Levels& L, const double* om64_all, const 
     }
     if (nlev > 0) {
         k_sort_levels<<<nlev, 256, 2 * nd * sizeof(int), st>>>(L.raw, L.task, L.pad_off, L.lvl_cnt, nd, L.cshift,
-                                                               L.seg_off);
+                                                               L.seg_off, L.cmask, m.rowptr, L.info, L.trec);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

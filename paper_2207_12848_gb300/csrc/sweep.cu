@@ -12,7 +12,8 @@
 // |a_f| lambda_down(f)) / (P_c + kappa_t,c V_c), i.e. the same row data swept in reversed level order.
 //
 // Schedules (all directions and all meshes of a batch in one persistent launch):
-//   LEVEL    -- warps take 32-task chunks of one wavefront level round-robin; grid barrier per level.
+//   LEVEL    -- warps take chunks (32/L tasks, L lanes each) of one wavefront level round-robin;
+//               grid barrier per level.
 //   DATAFLOW -- no barriers: warp w takes chunks w, w+W, ... in level order and each task waits
 //               (bounded) until its upwind values are written. Every dependency sits in an earlier
 //               level, hence an earlier chunk, so the lowest unfinished chunk can always progress.
@@ -34,10 +35,22 @@ __device__ __forceinline__ double mulr(double a, double b) { return __dmul_rn(a,
 __device__ __forceinline__ float fmar(float a, float b, float c) { return fmaf(a, b, c); }
 // FP64 path: separately rounded multiply and add, the oracle's rounding sequence
 __device__ __forceinline__ double fmar(double a, double b, double c) { return __dadd_rn(c, __dmul_rn(a, b)); }
-__device__ __forceinline__ float divr(float a, float b) { return __fdiv_rn(a, b); }
+// FP32 path: fast division (relative error ~2 ulp, far inside the FP32 tolerance); denominators are
+// projected areas plus kappa*V, never near the 2^126 range where the fast form underflows
+__device__ __forceinline__ float divr(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double divr(double a, double b) { return __ddiv_rn(a, b); }
 
+// Rare paths, kept out of line so the common path stays short:
+// exact FP64 classification inside the FP32 rounding band ...
+__device__ __noinline__ int classify_exact(const d4* side64, uint32_t s, const double* om64) {
+    const double t = exact_t(side64[s], om64);
+    return t > 0.0 ? 1 : (t < 0.0 ? -1 : 0);
+}
+
 // Wait (bounded) until *p carries this sweep's parity; returns the magnitude. false on give-up.
+template <typename real>
+__device__ __noinline__ bool wait_value_slow(const real* p, int parity, const SweepArgs& a, real& out);
+
 template <typename real>
 __device__ __forceinline__ bool wait_value(const real* p, int parity, const SweepArgs& a, real& out) {
     real v = ld_relaxed(p);
@@ -61,181 +74,606 @@ __device__ __forceinline__ bool wait_value(const real* p, int parity, const Swee
     }
 }
 
-// One task (c, Omega) for all groups. GC = compile-time group count (0: runtime a.G <= 8).
-template <typename real, int GC>
-__device__ __forceinline__ bool run_task(const SweepArgs& a, uint32_t entry, const float4* s_om, bool stall) {
+template <typename real>
+__device__ __noinline__ bool wait_value_slow(const real* p, int parity, const SweepArgs& a, real& out) {
+    return wait_value(p, parity, a, out);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batched sweep: L lanes cooperate on one task (c, Omega). Each lane owns the face sides
+// r0 + lane + k*L (k < U = SLOTS/L), so one pass covers SLOTS = 16 sides (a Voronoi cell has 15.5
+// on average) with coalesced 16-byte record loads that are all in flight together; the upwind
+// reads of the pass are issued together too; P_c and the inflow sums are reduced over the L lanes
+// with shuffles.
+// ---------------------------------------------------------------------------------------------
+constexpr int SLOTS = 16;
+// L2 prefetch of a task's face-side row by the bulk-copy engine (the row is contiguous, 16-byte
+// records, so address and size are multiples of 16 bytes)
+__device__ __forceinline__ void prefetch_row(const int4* side, uint32_t r0, uint32_t r1) {
+    if (r1 > r0)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(side + r0), "r"((r1 - r0) * 16u) : "memory");
+}
+
+template <typename real, int GC, int L>
+__device__ __forceinline__ bool group_task(const SweepArgs& a, uint32_t entry, uint32_t r0, uint32_t r1,
+                                           const float4* s_om, int gl, bool stall, uint64_t pol) {
     constexpr bool F64 = sizeof(real) == 8;
     constexpr int GM = GC > 0 ? GC : 8;
+    constexpr int U = L == 1 ? 8 : SLOTS / L;  // face sides per lane per pass
+    constexpr int PASS = L * U;                 // face sides per pass
     const int G = GC > 0 ? GC : a.G;
     using real2 = typename vec2<real>::type;
-    const uint32_t c = entry & a.cmask;
-    const uint32_t dl = entry >> a.cshift;
-    const uint32_t r0 = __ldg(a.rowptr + c), r1 = __ldg(a.rowptr + c + 1);
-    const double* om64 = a.om64 + 3 * dl;
-    const float4 om = F64 ? make_float4(0.f, 0.f, 0.f, 0.f) : s_om[dl];
-    const real2* cm = reinterpret_cast<const real2*>(a.cm) + (size_t)c * G;
-    real acc[GM], dnm[GM];
-    const real wsc = a.reverse ? (real)a.w64[dl] : (real)1;
+    const bool valid = entry != TASK_PAD;
+    const uint32_t c = valid ? (entry & a.cmask) : 0u;
+    const uint32_t dl = valid ? (entry >> a.cshift) : 0u;
+    if (!valid) r1 = r0;
+    // source and denominator of the cell, loaded early (used after the reduction)
+    real2 q[GM];
+    if (valid && gl == 0) {
+        const real2* cm = reinterpret_cast<const real2*>(a.cm) + (size_t)c * G;
 #pragma unroll
-    for (int g = 0; g < GM; ++g) {
-        if (g < G) {
-            real2 v = cm[g];
-            acc[g] = a.reverse ? mulr(wsc, v.x) : v.x;
-            dnm[g] = v.y;
-        }
+        for (int g = 0; g < GM; ++g)
+            if (g < G) q[g] = cm[g];
     }
-    if (stall) {  // test hook: wait on a word that nothing writes
-        real dummy;
-        if (!wait_value(reinterpret_cast<const real*>(a.stall_word), 1, a, dummy)) return false;
-    }
-    real P = 0;
+    const double* om64 = a.om64 + 3 * dl;
+    const float4 om = s_om[dl];
     real* I = reinterpret_cast<real*>(a.I);
     const size_t slab = (size_t)dl * a.N;
-    const uint64_t pol = policy_evict_first();
-    for (uint32_t s = r0; s < r1; ++s) {
-        const int4 rec = ld_stream_int4(a.side + s, pol);
-        real w;
-        int sgn;
-        if (F64) {
-            const d4 n = a.side64[s];
-            const double t = exact_t(n, om64);
-            sgn = t > 0.0 ? 1 : (t < 0.0 ? -1 : 0);
-            w = (real)__dmul_rn(n.w, fabs(t));
-        } else {
-            const float ax = __int_as_float(rec.y), ay = __int_as_float(rec.z), az = __int_as_float(rec.w);
-            const float t32 = fmaf(az, om.z, fmaf(ay, om.y, ax * om.x));
-            sgn = classify_side(t32, ax, ay, az, a.side64, s, om64);
-            w = (real)fabsf(t32);
-        }
-        if (sgn == 0) continue;
-        if (sgn > 0) P = addr(P, w);
-        const bool inflow = a.reverse ? (sgn > 0) : (sgn < 0);
-        if (!inflow) continue;
-        const int32_t nb = rec.x;
-        if (nb >= 0 && !(nb & NBR_PERIODIC)) {
-            const real* src = I + (slab + (uint32_t)nb) * G;
+    bool fail = false;
+    if (stall && gl == 0) {  // test hook: wait on a word that nothing writes
+        real dummy;
+        if (!wait_value(reinterpret_cast<const real*>(a.stall_word), 1, a, dummy)) fail = true;
+    }
+    real P = 0;
+    real acc[GM];
 #pragma unroll
-            for (int g = 0; g < GM; ++g) {
-                if (g < G) {
-                    real v;
-                    if (!wait_value(src + g, a.parity, a, v)) return false;
-                    acc[g] = fmar(w, v, acc[g]);
+    for (int g = 0; g < GM; ++g) acc[g] = 0;
+    for (uint32_t base = r0; base < r1; base += PASS) {
+        int4 rec[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const uint32_t s = base + gl + k * L;
+            rec[k] = s < r1 ? ld_stream_int4(a.side + s, pol) : make_int4(0, 0, 0, 0);
+        }
+        real w[U];
+        int kind[U];  // 0 none, 1 interior inflow, 2 periodic inflow, 3 boundary inflow
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const uint32_t s = base + gl + k * L;
+            kind[k] = 0;
+            w[k] = 0;
+            if (s < r1) {
+                int sgn;
+                if (F64) {
+                    const d4 n = a.side64[s];
+                    const double t = exact_t(n, om64);
+                    sgn = t > 0.0 ? 1 : (t < 0.0 ? -1 : 0);
+                    w[k] = (real)__dmul_rn(n.w, fabs(t));
+                } else {
+                    const float ax = __int_as_float(rec[k].y), ay = __int_as_float(rec[k].z),
+                                az = __int_as_float(rec[k].w);
+                    const float t32 = dot32(ax, ay, az, om);
+                    const float band = BAND_REL * ((fabsf(ax) + fabsf(ay)) + fabsf(az));
+                    sgn = t32 > band ? 1 : (t32 < -band ? -1 : 2);
+                    if (sgn == 2) sgn = classify_exact(a.side64, s, om64);
+                    w[k] = (real)fabsf(t32);
+                }
+                if (sgn > 0) P = addr(P, w[k]);
+                const bool inflow = sgn != 0 && (a.reverse ? (sgn > 0) : (sgn < 0));
+                if (inflow) {
+                    const int32_t nb = rec[k].x;
+                    if (nb >= 0 && !(nb & NBR_PERIODIC)) kind[k] = 1;
+                    else if (!a.reverse) kind[k] = nb >= 0 ? 2 : 3;
                 }
             }
-        } else if (a.reverse) {
-            // the adjoint has no boundary or periodic source
-        } else if (nb >= 0) {
-            if (a.Iprev) {
-                const real* src = reinterpret_cast<const real*>(a.Iprev) + (slab + (uint32_t)(nb & NBR_MASK)) * G;
+        }
+        // upwind reads of the pass, all issued before any is used
+        real v[U][GM];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            if (kind[k] == 1) {
+                const real* src = I + (slab + (uint32_t)rec[k].x) * G;
 #pragma unroll
                 for (int g = 0; g < GM; ++g)
-                    if (g < G) acc[g] = fmar(w, (real)fabs(src[g]), acc[g]);
+                    if (g < G) v[k][g] = ld_relaxed(src + g);
             }
-        } else if (a.bc) {
-            const real* b = reinterpret_cast<const real*>(a.bc) + (size_t)(-1 - nb) * G;
+        }
 #pragma unroll
-            for (int g = 0; g < GM; ++g)
-                if (g < G) acc[g] = fmar(w, b[g], acc[g]);
+        for (int k = 0; k < U; ++k) {
+            if (kind[k] == 1) {
+                const real* src = I + (slab + (uint32_t)rec[k].x) * G;
+#pragma unroll
+                for (int g = 0; g < GM; ++g) {
+                    if (g < G) {
+                        real x = v[k][g];
+                        if (sign_bit(x) != (a.parity != 0)) {
+                            if (fail || !wait_value_slow(src + g, a.parity, a, x)) {
+                                fail = true;
+                                x = 0;
+                            }
+                        } else {
+                            x = a.parity ? -x : x;
+                        }
+                        acc[g] = fmar(w[k], x, acc[g]);
+                    }
+                }
+            } else if (kind[k] == 2) {
+                if (a.Iprev) {
+                    const real* src = reinterpret_cast<const real*>(a.Iprev) +
+                                      (slab + (uint32_t)(rec[k].x & NBR_MASK)) * G;
+#pragma unroll
+                    for (int g = 0; g < GM; ++g)
+                        if (g < G) acc[g] = fmar(w[k], (real)fabs(src[g]), acc[g]);
+                }
+            } else if (kind[k] == 3) {
+                if (a.bc) {
+                    const real* b = reinterpret_cast<const real*>(a.bc) + (size_t)(-1 - rec[k].x) * G;
+#pragma unroll
+                    for (int g = 0; g < GM; ++g)
+                        if (g < G) acc[g] = fmar(w[k], b[g], acc[g]);
+                }
+            }
         }
     }
-    real* dst = I + (slab + c) * G;
+    // reduce over the L lanes of the group (aligned sub-warp, xor offsets stay inside it)
 #pragma unroll
-    for (int g = 0; g < GM; ++g) {
-        if (g < G) {
-            real v = divr(acc[g], addr(P, dnm[g]));
-            st_relaxed(dst + g, a.parity ? -v : v);
+    for (int off = L / 2; off > 0; off >>= 1) {
+        P = addr(P, __shfl_xor_sync(0xffffffffu, P, off));
+#pragma unroll
+        for (int g = 0; g < GM; ++g)
+            if (g < G) acc[g] = addr(acc[g], __shfl_xor_sync(0xffffffffu, acc[g], off));
+    }
+    if (valid && gl == 0 && !fail) {
+        const real wsc = a.reverse ? (real)a.w64[dl] : (real)1;
+        real* dst = I + (slab + c) * G;
+#pragma unroll
+        for (int g = 0; g < GM; ++g) {
+            if (g < G) {
+                const real src = a.reverse ? mulr(wsc, q[g].x) : q[g].x;
+                const real val = divr(addr(src, acc[g]), addr(P, q[g].y));
+                st_relaxed(dst + g, a.parity ? -val : val);
+            }
         }
+    }
+    return !fail;
+}
+
+// row bounds of a task entry (0, 0 for padding)
+__device__ __forceinline__ uint2 row_of(const SweepArgs& a, uint32_t e) {
+    if (e == TASK_PAD) return make_uint2(0u, 0u);
+    const uint32_t c = e & a.cmask;
+    return make_uint2(__ldg(a.rowptr + c), __ldg(a.rowptr + c + 1));
+}
+
+// A warp walks its chunks (32/L tasks, one per lane group) in order. Software pipeline: task entries
+// are loaded PF+1 chunks ahead, row bounds PF chunks ahead, and the face-side rows PF-1 chunks ahead
+// are pulled into L2 by the bulk-copy engine, so a task's records are L2 hits when it runs.
+// chunk(i) gives the i-th chunk of this warp, or -1 past the end.
+template <typename real, int GC, int L, typename ChunkFn>
+__device__ __forceinline__ bool run_chunks(const SweepArgs& a, ChunkFn chunk, const float4* s_om, int grp, int gl,
+                                           bool stall_here) {
+    const uint64_t pol = policy_evict_first();
+    constexpr int CS = 32 / L;
+    constexpr int PF = 3;
+    auto entry_of = [&](int64_t i) -> uint32_t {
+        const int64_t k = chunk(i);
+        return k >= 0 ? a.task[k * CS + grp] : TASK_PAD;
+    };
+    uint32_t E[PF + 1];
+    uint2 R[PF];
+#pragma unroll
+    for (int j = 0; j <= PF; ++j) E[j] = entry_of(j);
+#pragma unroll
+    for (int j = 0; j < PF; ++j) R[j] = row_of(a, E[j]);
+    if (gl == 0) {
+#pragma unroll
+        for (int j = 1; j < PF - 1; ++j) prefetch_row(a.side, R[j].x, R[j].y);
+    }
+    for (int64_t i = 0; chunk(i) >= 0; ++i) {
+        if ((i & 15) == 0 && __any_sync(0xffffffffu, ld_volatile_i32(a.err) != DEV_OK)) return false;
+        const uint32_t e_new = entry_of(i + PF + 1);
+        const uint2 r_new = row_of(a, E[PF]);
+        if (gl == 0) prefetch_row(a.side, R[PF - 1].x, R[PF - 1].y);
+        const bool stall = stall_here && i == 0 && grp == 0;
+        const bool good = group_task<real, GC, L>(a, E[0], R[0].x, R[0].y, s_om, gl, stall, pol);
+        if (__any_sync(0xffffffffu, !good)) return false;
+#pragma unroll
+        for (int j = 0; j < PF; ++j) E[j] = E[j + 1];
+        E[PF] = e_new;
+#pragma unroll
+        for (int j = 0; j < PF - 1; ++j) R[j] = R[j + 1];
+        R[PF - 1] = r_new;
     }
     return true;
 }
 
-template <typename real, int GC>
+// ---------------------------------------------------------------------------------------------
+// FP32 forward sweep from task records. The classification pass already fixed, per task, P_c and
+// which of the first 32 face sides are inflow sides, so a task only visits its inflow sides
+// (about half the row): no classification, no outflow sum. L lanes share a task, lane j taking
+// the inflow sides of rank j, j+L, ...; each batch issues U record loads, then U upwind loads.
+// Rows longer than 32 sides (rare) classify their remaining sides on the spot.
+// ---------------------------------------------------------------------------------------------
+template <int GC>
+__device__ __forceinline__ void add_inflow(const SweepArgs& a, int32_t nb, float w, const float* vpre, size_t slab,
+                                           int G, float* acc, bool& fail) {
+    constexpr int GM = GC > 0 ? GC : 8;
+    if (nb >= 0 && !(nb & NBR_PERIODIC)) {
+        const float* src = reinterpret_cast<const float*>(a.I) + (slab + (uint32_t)nb) * G;
+#pragma unroll
+        for (int g = 0; g < GM; ++g) {
+            if (g < G) {
+                float x = vpre ? vpre[g] : ld_relaxed(src + g);
+                if (sign_bit(x) != (a.parity != 0)) {
+                    if (fail || !wait_value_slow(src + g, a.parity, a, x)) {
+                        fail = true;
+                        x = 0.f;
+                    }
+                } else {
+                    x = a.parity ? -x : x;
+                }
+                acc[g] = fmaf(w, x, acc[g]);
+            }
+        }
+    } else if (nb >= 0) {
+        if (a.Iprev) {
+            const float* src = reinterpret_cast<const float*>(a.Iprev) + (slab + (uint32_t)(nb & NBR_MASK)) * G;
+#pragma unroll
+            for (int g = 0; g < GM; ++g)
+                if (g < G) acc[g] = fmaf(w, fabsf(src[g]), acc[g]);
+        }
+    } else if (a.bc) {
+        const float* b = reinterpret_cast<const float*>(a.bc) + (size_t)(-1 - nb) * G;
+#pragma unroll
+        for (int g = 0; g < GM; ++g)
+            if (g < G) acc[g] = fmaf(w, b[g], acc[g]);
+    }
+}
+
+template <int GC, int L>
+__device__ __forceinline__ bool rec_task(const SweepArgs& a, const int4 tr, const float4* s_om, int gl, bool stall,
+                                         uint64_t pol) {
+    constexpr int GM = GC > 0 ? GC : 8;
+    constexpr int U = 8 / L;  // inflow sides per lane per batch
+    const int G = GC > 0 ? GC : a.G;
+    const uint32_t e = (uint32_t)tr.x;
+    const bool valid = e != TASK_PAD;
+    const uint32_t c = valid ? (e & a.cmask) : 0u;
+    const uint32_t dl = valid ? (e >> a.cshift) : 0u;
+    const uint32_t r0 = (uint32_t)tr.y;
+    const float P = __int_as_float(tr.z & 0x7fffffff);
+    const bool longrow = valid && tr.z < 0;
+    uint32_t m = valid ? (uint32_t)tr.w : 0u;
+#pragma unroll
+    for (int j = 0; j < L - 1; ++j)
+        if (j < gl) m &= m - 1;  // this lane starts at the inflow side of rank gl
+    float2 q[GM];
+    if (valid && gl == 0) {
+        const float2* cm = reinterpret_cast<const float2*>(a.cm) + (size_t)c * G;
+#pragma unroll
+        for (int g = 0; g < GM; ++g)
+            if (g < G) q[g] = cm[g];
+    }
+    const float4 om = s_om[dl];
+    const size_t slab = (size_t)dl * a.N;
+    bool fail = false;
+    if (stall && gl == 0) {
+        float dummy;
+        if (!wait_value(reinterpret_cast<const float*>(a.stall_word), 1, a, dummy)) fail = true;
+    }
+    float acc[GM];
+#pragma unroll
+    for (int g = 0; g < GM; ++g) acc[g] = 0.f;
+    while (m) {
+        uint32_t pos[U];
+        bool ok[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            ok[k] = m != 0u;
+            pos[k] = ok[k] ? (uint32_t)(__ffs(m) - 1) : 0u;
+#pragma unroll
+            for (int j = 0; j < L; ++j) m &= m - 1;
+        }
+        int4 rec[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) rec[k] = ok[k] ? ld_stream_int4(a.side + r0 + pos[k], pol) : make_int4(-1, 0, 0, 0);
+        float v[U][GM];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            if (ok[k] && rec[k].x >= 0 && !(rec[k].x & NBR_PERIODIC)) {
+                const float* src = reinterpret_cast<const float*>(a.I) + (slab + (uint32_t)rec[k].x) * G;
+#pragma unroll
+                for (int g = 0; g < GM; ++g)
+                    if (g < G) v[k][g] = ld_relaxed(src + g);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            if (!ok[k]) continue;
+            const float w = fabsf(dot32(__int_as_float(rec[k].y), __int_as_float(rec[k].z), __int_as_float(rec[k].w), om));
+            add_inflow<GC>(a, rec[k].x, w, v[k], slab, G, acc, fail);
+        }
+    }
+    if (longrow) {
+        const uint32_t r1 = __ldg(a.rowptr + c + 1);
+        const double* om64 = a.om64 + 3 * dl;
+        for (uint32_t s = r0 + 32 + gl; s < r1; s += L) {
+            const int4 r = a.side[s];
+            const float ax = __int_as_float(r.y), ay = __int_as_float(r.z), az = __int_as_float(r.w);
+            const float t32 = dot32(ax, ay, az, om);
+            if (classify_side(t32, ax, ay, az, a.side64, s, om64) < 0)
+                add_inflow<GC>(a, r.x, fabsf(t32), nullptr, slab, G, acc, fail);
+        }
+    }
+#pragma unroll
+    for (int off = L / 2; off > 0; off >>= 1) {
+#pragma unroll
+        for (int g = 0; g < GM; ++g)
+            if (g < G) acc[g] += __shfl_xor_sync(0xffffffffu, acc[g], off);
+    }
+    if (valid && gl == 0 && !fail) {
+        float* dst = reinterpret_cast<float*>(a.I) + (slab + c) * G;
+#pragma unroll
+        for (int g = 0; g < GM; ++g) {
+            if (g < G) {
+                const float val = __fdividef(q[g].x + acc[g], P + q[g].y);
+                st_relaxed(dst + g, a.parity ? -val : val);
+            }
+        }
+    }
+    return !fail;
+}
+
+// the highest inflow side bounds the part of the row a record's task reads
+__device__ __forceinline__ void prefetch_rec(const SweepArgs& a, const int4 tr) {
+    if ((uint32_t)tr.x == TASK_PAD || tr.w == 0) return;
+    const uint32_t n = 32u - __clz((uint32_t)tr.w);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.side + (uint32_t)tr.y), "r"(n * 16u) : "memory");
+}
+
+template <int GC, int L, typename ChunkFn>
+__device__ __forceinline__ bool run_chunks_rec(const SweepArgs& a, ChunkFn chunk, const float4* s_om, int grp, int gl,
+                                               bool stall_here) {
+    constexpr int CS = 32 / L;
+    constexpr int PF = 3;
+    const uint64_t pol = policy_evict_first();
+    auto rec_of = [&](int64_t i) -> int4 {
+        const int64_t k = chunk(i);
+        return k >= 0 ? __ldg(a.trec + k * CS + grp) : make_int4((int)TASK_PAD, 0, 0, 0);
+    };
+    int4 T[PF + 1];
+#pragma unroll
+    for (int j = 0; j <= PF; ++j) T[j] = rec_of(j);
+    if (gl == 0) {
+#pragma unroll
+        for (int j = 1; j < PF; ++j) prefetch_rec(a, T[j]);
+    }
+    for (int64_t i = 0; chunk(i) >= 0; ++i) {
+        if ((i & 15) == 0 && __any_sync(0xffffffffu, ld_volatile_i32(a.err) != DEV_OK)) return false;
+        const int4 t_new = rec_of(i + PF + 1);
+        if (gl == 0) prefetch_rec(a, T[PF]);
+        const bool stall = stall_here && i == 0 && grp == 0;
+        const bool good = rec_task<GC, L>(a, T[0], s_om, gl, stall, pol);
+        if (__any_sync(0xffffffffu, !good)) return false;
+#pragma unroll
+        for (int j = 0; j < PF; ++j) T[j] = T[j + 1];
+        T[PF] = t_new;
+    }
+    return true;
+}
+
+template <int GC, int L>
+#ifndef SWEEP_REC_MINB
+#define SWEEP_REC_MINB 4  // resident 256-thread blocks per SM the record kernel is compiled for
+#endif
+__global__ void __launch_bounds__(256, SWEEP_REC_MINB) k_sweep_rec(SweepArgs a) {
+    extern __shared__ float4 s_om[];
+    for (int i = threadIdx.x; i < a.nd; i += blockDim.x) s_om[i] = a.om32[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / L, gl = lane % L;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nchunks = a.n_chunks * L;
+    if (a.level_sync) {
+        bool ok = true;
+        for (int li = 0; li < a.n_levels; ++li) {
+            const int64_t k0 = a.lev_chunk[li] * L, k1 = a.lev_chunk[li + 1] * L;
+            if (ok) {
+                auto chunk = [=](int64_t i) -> int64_t {
+                    const int64_t k = k0 + warp + i * nwarps;
+                    return k < k1 ? k : -1;
+                };
+                ok = run_chunks_rec<GC, L>(a, chunk, s_om, grp, gl, a.debug_stall && li == 0 && warp == 0);
+            }
+            if (!grid_sync(a.bar, gridDim.x, a.spin_budget, a.err)) return;
+        }
+    } else {
+        auto chunk = [=](int64_t i) -> int64_t {
+            const int64_t k = warp + i * nwarps;
+            return k < nchunks ? k : -1;
+        };
+        run_chunks_rec<GC, L>(a, chunk, s_om, grp, gl, a.debug_stall && warp == 0);
+    }
+}
+
+template <typename real, int GC, int L>
 __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     extern __shared__ float4 s_om[];
     for (int i = threadIdx.x; i < a.nd; i += blockDim.x) s_om[i] = a.om32[i];
     __syncthreads();
     const int lane = threadIdx.x & 31;
+    const int grp = lane / L, gl = lane % L;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nchunks = a.n_chunks * L;  // n_chunks counts 32-task chunks
     if (a.level_sync) {
         bool ok = true;
         for (int li = 0; li < a.n_levels; ++li) {
-            const int L = a.reverse ? a.n_levels - 1 - li : li;
-            const int64_t k0 = a.lev_chunk[L], k1 = a.lev_chunk[L + 1];
+            const int Lv = a.reverse ? a.n_levels - 1 - li : li;
+            const int64_t k0 = a.lev_chunk[Lv] * L, k1 = a.lev_chunk[Lv + 1] * L;
             if (ok) {
-                for (int64_t k = k0 + warp; k < k1; k += nwarps) {
-                    const uint32_t e = a.task[k * 32 + lane];
-                    if (e != TASK_PAD) {
-                        const bool stall = a.debug_stall && k == 0 && lane == 0;
-                        if (!run_task<real, GC>(a, e, s_om, stall)) { ok = false; break; }
-                    }
-                }
+                auto chunk = [=](int64_t i) -> int64_t {
+                    const int64_t k = k0 + warp + i * nwarps;
+                    return k < k1 ? k : -1;
+                };
+                ok = run_chunks<real, GC, L>(a, chunk, s_om, grp, gl, a.debug_stall && li == 0 && warp == 0);
             }
             if (!grid_sync(a.bar, gridDim.x, a.spin_budget, a.err)) return;
         }
     } else {
-        for (int64_t i = 0;; ++i) {
-            const int64_t k = a.reverse ? (a.n_chunks - 1 - warp - i * nwarps) : (warp + i * nwarps);
-            if (k < 0 || k >= a.n_chunks) break;
-            if ((i & 7) == 0 && ld_volatile_i32(a.err) != DEV_OK) return;
-            const uint32_t e = a.task[k * 32 + lane];
-            if (e != TASK_PAD) {
-                const bool stall = a.debug_stall && i == 0 && warp == 0 && lane == 0;
-                if (!run_task<real, GC>(a, e, s_om, stall)) return;
-            }
+        auto chunk = [=](int64_t i) -> int64_t {
+            const int64_t k = a.reverse ? (nchunks - 1 - warp - i * nwarps) : (warp + i * nwarps);
+            return (k >= 0 && k < nchunks) ? k : -1;
+        };
+        run_chunks<real, GC, L>(a, chunk, s_om, grp, gl, a.debug_stall && warp == 0);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// K8: the plain path -- one launch per (direction, level) segment, FP64, one thread per task
+// walking its face sides in order (the oracle's summation order).
+// ---------------------------------------------------------------------------------------------
+template <int GC>
+__device__ __forceinline__ void plain_task(const SweepArgs& a, uint32_t entry) {
+    constexpr int GM = GC > 0 ? GC : 8;
+    const int G = GC > 0 ? GC : a.G;
+    const uint32_t c = entry & a.cmask;
+    const uint32_t dl = entry >> a.cshift;
+    const uint32_t r0 = a.rowptr[c], r1 = a.rowptr[c + 1];
+    const double* om64 = a.om64 + 3 * dl;
+    const double2* cm = reinterpret_cast<const double2*>(a.cm) + (size_t)c * G;
+    double* I = reinterpret_cast<double*>(a.I);
+    const size_t slab = (size_t)dl * a.N;
+    double acc[GM];
+    for (int g = 0; g < GM; ++g)
+        if (g < G) acc[g] = a.reverse ? __dmul_rn(a.w64[dl], cm[g].x) : cm[g].x;
+    double P = 0.0;
+    for (uint32_t s = r0; s < r1; ++s) {
+        const int32_t nb = a.side[s].x;
+        const d4 n = a.side64[s];
+        const double t = exact_t(n, om64);
+        if (t == 0.0) continue;
+        const double w = __dmul_rn(n.w, fabs(t));
+        if (t > 0.0) P = __dadd_rn(P, w);
+        const bool inflow = a.reverse ? t > 0.0 : t < 0.0;
+        if (!inflow) continue;
+        const double* src = nullptr;
+        if (nb >= 0 && !(nb & NBR_PERIODIC)) src = I + (slab + (uint32_t)nb) * G;
+        else if (a.reverse) continue;
+        else if (nb >= 0) src = a.Iprev ? reinterpret_cast<const double*>(a.Iprev) + (slab + (nb & NBR_MASK)) * G
+                                        : nullptr;
+        else src = a.bc ? reinterpret_cast<const double*>(a.bc) + (size_t)(-1 - nb) * G : nullptr;
+        if (!src) continue;
+        for (int g = 0; g < GM; ++g)
+            if (g < G) acc[g] = __dadd_rn(acc[g], __dmul_rn(w, fabs(src[g])));
+    }
+    double* dst = I + (slab + c) * G;
+    for (int g = 0; g < GM; ++g) {
+        if (g < G) {
+            const double v = __ddiv_rn(acc[g], __dadd_rn(P, cm[g].y));
+            dst[g] = a.parity ? -v : v;
         }
     }
 }
 
-// K8: the plain path -- one launch per (direction, level) segment, FP64, thread per task.
 template <int GC>
 __global__ void __launch_bounds__(256) k_plain(SweepArgs a, uint32_t begin, uint32_t end) {
     const uint32_t i = begin + blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= end) return;
-    run_task<double, GC>(a, a.task[i], nullptr, false);
+    plain_task<GC>(a, a.task[i]);
+}
+
+template <typename real, int L>
+cudaError_t launch_lanes(const SweepArgs& a, const cudaLaunchConfig_t& cfg) {
+    switch (a.G) {
+        case 1: return cudaLaunchKernelEx(&cfg, k_sweep<real, 1, L>, a);
+        case 2: return cudaLaunchKernelEx(&cfg, k_sweep<real, 2, L>, a);
+        case 4: return cudaLaunchKernelEx(&cfg, k_sweep<real, 4, L>, a);
+        default: return cudaLaunchKernelEx(&cfg, k_sweep<real, 0, L>, a);
+    }
+}
+
+template <int L>
+cudaError_t launch_rec_lanes(const SweepArgs& a, const cudaLaunchConfig_t& cfg) {
+    switch (a.G) {
+        case 1: return cudaLaunchKernelEx(&cfg, k_sweep_rec<1, L>, a);
+        case 2: return cudaLaunchKernelEx(&cfg, k_sweep_rec<2, L>, a);
+        case 4: return cudaLaunchKernelEx(&cfg, k_sweep_rec<4, L>, a);
+        default: return cudaLaunchKernelEx(&cfg, k_sweep_rec<0, L>, a);
+    }
+}
+
+template <int L>
+int occupancy_rec_lanes(int G, int threads, size_t smem) {
+    int n = 0;
+    switch (G) {
+        case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_rec<1, L>, threads, smem); break;
+        case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_rec<2, L>, threads, smem); break;
+        case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_rec<4, L>, threads, smem); break;
+        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_rec<0, L>, threads, smem); break;
+    }
+    return n;
 }
 
 template <typename real>
 cudaError_t launch_typed(const SweepArgs& a, int blocks, int threads, cudaStream_t st) {
-    size_t smem = sizeof(float4) * (size_t)a.nd;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(blocks);
     cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = smem;
+    cfg.dynamicSmemBytes = sizeof(float4) * (size_t)a.nd;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    switch (a.G) {
-        case 1: return cudaLaunchKernelEx(&cfg, k_sweep<real, 1>, a);
-        case 2: return cudaLaunchKernelEx(&cfg, k_sweep<real, 2>, a);
-        case 4: return cudaLaunchKernelEx(&cfg, k_sweep<real, 4>, a);
-        default: return cudaLaunchKernelEx(&cfg, k_sweep<real, 0>, a);
+    if (sizeof(real) == 4 && !a.reverse) {  // FP32 forward: the record kernel
+        if (a.lanes == 1) return launch_rec_lanes<1>(a, cfg);
+        if (a.lanes == 2) return launch_rec_lanes<2>(a, cfg);
+        if (a.lanes == 4) return launch_rec_lanes<4>(a, cfg);
+        return launch_rec_lanes<8>(a, cfg);
     }
+    if (a.lanes == 16) return launch_lanes<real, 16>(a, cfg);
+    if (a.lanes == 2) return launch_lanes<real, 2>(a, cfg);
+    if (a.lanes == 1) return launch_lanes<real, 1>(a, cfg);
+    if (a.lanes == 8) return launch_lanes<real, 8>(a, cfg);
+    return launch_lanes<real, 4>(a, cfg);
 }
 
-template <typename real>
-int occupancy_typed(int G, int threads, size_t smem) {
+template <typename real, int L>
+int occupancy_lanes(int G, int threads, size_t smem) {
     int n = 0;
     switch (G) {
-        case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<real, 1>, threads, smem); break;
-        case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<real, 2>, threads, smem); break;
-        case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<real, 4>, threads, smem); break;
-        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<real, 0>, threads, smem); break;
+        case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<real, 1, L>, threads, smem); break;
+        case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<real, 2, L>, threads, smem); break;
+        case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<real, 4, L>, threads, smem); break;
+        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<real, 0, L>, threads, smem); break;
     }
     return n;
 }
 
 }  // namespace
 
-int sweep_occupancy(int precision, int G, int threads, int nd) {
+int sweep_occupancy(int precision, int G, int threads, int nd, int lanes, int reverse) {
     size_t smem = sizeof(float4) * (size_t)nd;
-    return precision == 64 ? occupancy_typed<double>(G, threads, smem) : occupancy_typed<float>(G, threads, smem);
+    if (precision == 32 && !reverse) {
+        if (lanes == 1) return occupancy_rec_lanes<1>(G, threads, smem);
+        if (lanes == 2) return occupancy_rec_lanes<2>(G, threads, smem);
+        if (lanes == 4) return occupancy_rec_lanes<4>(G, threads, smem);
+        return occupancy_rec_lanes<8>(G, threads, smem);
+    }
+    if (precision == 64) {
+        if (lanes == 16) return occupancy_lanes<double, 16>(G, threads, smem);
+        if (lanes == 2) return occupancy_lanes<double, 2>(G, threads, smem);
+        if (lanes == 1) return occupancy_lanes<double, 1>(G, threads, smem);
+        return lanes == 8 ? occupancy_lanes<double, 8>(G, threads, smem) : occupancy_lanes<double, 4>(G, threads, smem);
+    }
+    if (lanes == 16) return occupancy_lanes<float, 16>(G, threads, smem);
+    if (lanes == 2) return occupancy_lanes<float, 2>(G, threads, smem);
+    if (lanes == 1) return occupancy_lanes<float, 1>(G, threads, smem);
+    return lanes == 8 ? occupancy_lanes<float, 8>(G, threads, smem) : occupancy_lanes<float, 4>(G, threads, smem);
 }
-
-int sweep_max_blocks_per_sm(int precision, int threads) { return sweep_occupancy(precision, 1, threads, 1024); }
 
 cudaError_t launch_sweep(const SweepArgs& a, int precision, int blocks, int threads, cudaStream_t st) {
     return precision == 64 ? launch_typed<double>(a, blocks, threads, st) : launch_typed<float>(a, blocks, threads, st);
