@@ -396,7 +396,8 @@ def run_ours(args, dist: Dist):
                          "levelise_ms": agg["levelise_ms"] / args.steps,
                          "sweep_ms_per_launch": avg_launch_s * 1e3,
                          "schedule": {1: "level", 2: "dataflow"}.get(last["schedule_used"], last["schedule_used"]),
-                         "lanes_per_task": last["lanes_used"], "threads_per_block": last["threads_used"]}}
+                         "lanes_per_task": last["lanes_used"], "threads_per_block": last["threads_used"],
+                         "blocks_per_sm": last["blocks_per_sm_used"]}}
         out.update(extra)
         print(json.dumps(out))
 
@@ -413,8 +414,8 @@ def run_profile_case(args):
     ctx.set_mesh(p.mesh)
     ctx.set_directions(p.omega, p.weight)
     ctx.set_material(p.kappa_abs, p.emissivity)
-    o = default_opts(precision=32, schedule=args.schedule, lanes_per_task=args.lanes, block_threads=256,
-                     max_it_pbc=2, tol_pbc=0.0)
+    o = default_opts(precision=32, schedule=args.schedule, lanes_per_task=args.lanes,
+                     block_threads=128 if args.lanes == 1 else 256, blocks_per_sm=args.bpsm, max_it_pbc=2, tol_pbc=0.0)
     ctx.solve(o)  # warm-up: module loading, first-touch of buffers
     J, G, st, s = ctx.solve(o)
     ctx.close()
@@ -438,6 +439,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true", help="small fixed solve for ncu captures")
     ap.add_argument("--schedule", default="dataflow", choices=["level", "dataflow"])
     ap.add_argument("--lanes", type=int, default=8, choices=[1, 2, 4, 8, 16])
+    ap.add_argument("--bpsm", type=int, default=0, help="resident blocks per SM (profiling case)")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)

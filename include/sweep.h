@@ -77,7 +77,10 @@ typedef struct {
     int32_t use_graph;    /* 1: capture one iteration in a CUDA graph and replay it */
     int64_t spin_budget;  /* bound on each device-side wait, in polls (0 = default, about 1 s) */
     int32_t debug_stall;  /* TEST ONLY: 1 makes the first sweep task wait on a word nothing writes */
-    int32_t lanes_per_task; /* lanes cooperating on one task in the batched sweep: 1..16, a power of 2 (0 = autotuned) */
+    int32_t lanes_per_task; /* lanes cooperating on one task in the batched sweep: 1..16, a power of 2 (0 = autotuned);
+                               with the assembled operator, 1 = one task per thread with TMA-staged rows */
+    int32_t geometry_only;  /* 1: the FP32 sweep reads the mesh every sweep instead of the assembled operator */
+    int32_t blocks_per_sm;  /* resident blocks per SM of the batched sweep (0 = autotuned / maximum) */
 } sweep_opts;
 
 typedef struct {
@@ -89,7 +92,8 @@ typedef struct {
     double res_pbc_mean;
     double emitted, injected, absorbed, escaped; /* photons/s over all cells and groups (FP64) */
     double defect;             /* (emitted + injected - absorbed - escaped) / (emitted + injected) */
-    double t_ms[8];            /* 0 classify, 1 levelise, 2 sweeps, 3 tallies+updates, 4 total (CUDA events) */
+    double t_ms[8];            /* 0 classify, 1 levelise, 2 sweeps, 3 tallies+updates, 4 total, 5 operator
+                                  assembly (CUDA events) */
     double updates;            /* cell x direction x group updates done by all sweeps */
     double updates_per_s;      /* updates / (t_ms[4] / 1000) */
     int32_t sweep_launches;    /* batched-sweep kernel launches timed in t_ms[2] */
@@ -97,7 +101,7 @@ typedef struct {
     int32_t kernel_launches;   /* all kernels this call launched (including the autotuner's) */
     int32_t lanes_used;        /* lanes per task of the batched sweep that ran */
     int32_t threads_used;      /* threads per block of the batched sweep that ran */
-    int32_t reserved;
+    int32_t blocks_per_sm_used;/* resident blocks per SM it was launched with (0 = maximum) */
 } sweep_stats;
 
 /* Fill *opts with defaults: precision 32, AUTO schedule, tolerances 1e-6, 100 iterations. */

@@ -36,7 +36,8 @@ class sweep_opts(ctypes.Structure):
                 ("warm_start", ctypes.c_int32), ("tol_pbc", ctypes.c_double), ("dir_batch", ctypes.c_int32),
                 ("relevel", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("spin_budget", ctypes.c_int64), ("debug_stall", ctypes.c_int32),
-                ("lanes_per_task", ctypes.c_int32)]
+                ("lanes_per_task", ctypes.c_int32), ("geometry_only", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32)]
 
 
 class sweep_stats(ctypes.Structure):
@@ -47,12 +48,14 @@ class sweep_stats(ctypes.Structure):
                 ("defect", ctypes.c_double), ("t_ms", ctypes.c_double * 8), ("updates", ctypes.c_double),
                 ("updates_per_s", ctypes.c_double), ("sweep_launches", ctypes.c_int32),
                 ("schedule_used", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
-                ("lanes_used", ctypes.c_int32), ("threads_used", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("lanes_used", ctypes.c_int32), ("threads_used", ctypes.c_int32),
+                ("blocks_per_sm_used", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "t_ms"}
         t = list(self.t_ms)
-        d.update(t_classify_ms=t[0], t_levelise_ms=t[1], t_sweep_ms=t[2], t_update_ms=t[3], t_total_ms=t[4])
+        d.update(t_classify_ms=t[0], t_levelise_ms=t[1], t_sweep_ms=t[2], t_update_ms=t[3], t_total_ms=t[4],
+                 t_assemble_ms=t[5])
         return d
 
 

@@ -64,7 +64,7 @@ struct sweep_ctx {
     void* adjL = nullptr;
     size_t adj_bytes_I = 0, adj_bytes_L = 0;
     // autotuner: schedule and block size per (precision, G)
-    int tuned[2][9][3] = {};
+    int tuned[2][9][2][4] = {};  // [precision][groups][operator mode] -> schedule, threads, lanes, blocks/SM
     int64_t launches = 0;  // kernels launched by this context
 };
 
@@ -102,7 +102,7 @@ void dfree(T*& p) {
 
 void free_levels(Levels& L) {
     dfree(L.raw); dfree(L.task); dfree(L.trec); dfree(L.info); dfree(L.level); dfree(L.lvl_cnt); dfree(L.pad_off);
-    dfree(L.lev_chunk); dfree(L.seg_off);
+    dfree(L.lev_chunk); dfree(L.seg_off); dfree(L.op);
     L = Levels();
 }
 
@@ -226,6 +226,9 @@ SweepArgs make_args(sweep_ctx* c, const Levels& L, int precision, const void* cm
     memset(&a, 0, sizeof a);
     a.task = L.task;
     a.trec = L.trec;
+    a.op = (precision == 32 && !reverse && L.op_valid && !(o && o->geometry_only)) ? L.op : nullptr;
+    a.op_ent = a.op ? reinterpret_cast<const int2*>(L.op + (L.h_lev_chunk.empty() ? 0 : L.h_lev_chunk.back() * 32))
+                    : nullptr;
     a.n_chunks = L.h_lev_chunk.empty() ? 0 : L.h_lev_chunk.back();
     a.lev_chunk = L.lev_chunk;
     a.n_levels = L.n_levels;
@@ -256,7 +259,7 @@ SweepArgs make_args(sweep_ctx* c, const Levels& L, int precision, const void* cm
     return a;
 }
 
-sweep_status run_sweep(sweep_ctx* c, const Levels& L, int precision, int schedule, int threads, int lanes,
+sweep_status run_sweep(sweep_ctx* c, const Levels& L, int precision, int schedule, int threads, int lanes, int bpsm,
                        SweepArgs a, const float* bc32, float* ms) {
     if (precision == 32) a.bc = a.reverse ? nullptr : bc32;
     a.lanes = lanes;
@@ -276,8 +279,9 @@ sweep_status run_sweep(sweep_ctx* c, const Levels& L, int precision, int schedul
             }
         }
     } else {
-        int per_sm = sweep_occupancy(precision, a.G, threads, L.nd, lanes, a.reverse);
+        int per_sm = sweep_occupancy(precision, a.G, threads, L.nd, lanes, a.reverse, a.op != nullptr);
         if (per_sm < 1) return bad(c, "sweep kernel does not fit on an SM");
+        if (bpsm > 0 && bpsm < per_sm) per_sm = bpsm;
         a.level_sync = schedule == SWEEP_SCHED_LEVEL ? 1 : 0;
         CKL(launch_sweep(a, precision, c->sms * per_sm, threads, c->st), "sweep launch");
     }
@@ -563,9 +567,47 @@ sweep_status sweep_set_material_dev(sweep_ctx* c, int32_t G, const double* ka, c
 // ---------------------------------------------------------------------------------------------
 namespace {
 
-sweep_status ensure_levels(sweep_ctx* c, const sweep_opts* o, float* t1, float* t2) {
+// Assembles the transport operator of the levelised directions (one 128-byte line per task) when
+// device memory allows; otherwise the FP32 sweep reads the mesh geometry directly.
+sweep_status assemble_operator(sweep_ctx* c, Levels& L, float* t_ms) {
+    L.op_valid = false;
+    const int64_t tasks = L.h_lev_chunk.empty() ? 0 : L.h_lev_chunk.back() * 32;
+    const size_t bytes = (size_t)tasks * 128;
+    if (bytes > L.op_bytes) {
+        dfree(L.op);
+        L.op_bytes = 0;
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        // keep a margin for the solve buffers allocated later
+        if (bytes + (size_t)(2ull << 30) > free_b) return SWEEP_OK;
+        if (cudaMalloc(&L.op, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            L.op = nullptr;
+            return SWEEP_OK;
+        }
+        L.op_bytes = bytes;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, c->st);
+    CKL(build_operator(c->mesh, L, c->om64, c->om32, c->st), "assemble operator");
+    cudaEventRecord(e1, c->st);
+    CK(cudaEventSynchronize(e1), "assemble operator");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (t_ms) *t_ms = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    L.op_valid = true;
+    return SWEEP_OK;
+}
+
+sweep_status ensure_levels(sweep_ctx* c, const sweep_opts* o, float* t1, float* t2, float* t3 = nullptr) {
     if (c->lev.valid && !(o && o->relevel) && c->lev.nd == c->D && c->lev.d0 == 0) return SWEEP_OK;
-    return run_levelise(c, c->lev, 0, c->D, budget_of(o), t1, t2);
+    sweep_status s = run_levelise(c, c->lev, 0, c->D, budget_of(o), t1, t2);
+    if (s != SWEEP_OK) return s;
+    return assemble_operator(c, c->lev, t3);
 }
 
 sweep_status ensure_solution(sweep_ctx* c, int prec, bool two) {
@@ -602,45 +644,52 @@ double read_max(sweep_ctx* c) {
 }
 
 // choose schedule and block size: time one sweep per candidate (results are identical for all)
-sweep_status autotune(sweep_ctx* c, int prec, const void* cm, const float* bc32, const sweep_opts* o, int* sched,
-                      int* threads, int* lanes) {
-    int* t3 = c->tuned[prec == 64][c->G];
-    if (t3[0]) {
-        *sched = t3[0];
-        *threads = t3[1];
-        *lanes = t3[2];
+struct LaunchCfg {
+    int sched, threads, lanes, bpsm;
+};
+
+// choose the batched-sweep configuration: time one sweep per candidate (results are identical for all)
+sweep_status autotune(sweep_ctx* c, int prec, const void* cm, const float* bc32, const sweep_opts* o, LaunchCfg* out) {
+    const bool op = prec == 32 && c->lev.op_valid && !(o && o->geometry_only);
+    int* t4 = c->tuned[prec == 64][c->G][op ? 1 : 0];
+    if (t4[0]) {
+        *out = LaunchCfg{t4[0], t4[1], t4[2], t4[3]};
         return SWEEP_OK;
     }
-    const int cand_s[2] = {SWEEP_SCHED_LEVEL, SWEEP_SCHED_DATAFLOW};
-    const int cand_t[2] = {128, 256};
-    const int cand_l[5] = {1, 2, 4, 8, 16};
+    std::vector<LaunchCfg> cand;
+    if (op) {
+        // one task per thread with TMA-staged rows at 1..4 resident blocks per SM (tasks in flight),
+        // and 8 lanes per task
+        for (int b : {2, 4}) cand.push_back({SWEEP_SCHED_DATAFLOW, 128, 1, b});
+        cand.push_back({SWEEP_SCHED_DATAFLOW, 256, 8, 0});
+        cand.push_back({SWEEP_SCHED_LEVEL, 256, 8, 0});
+    } else {
+        for (int s : {SWEEP_SCHED_LEVEL, SWEEP_SCHED_DATAFLOW})
+            for (int t : {128, 256})
+                for (int l : {1, 2, 4, 8, 16}) cand.push_back({s, t, l, 0});
+    }
     float best = 1e30f;
-    int bs = SWEEP_SCHED_DATAFLOW, bt = 256, bl = 4;
+    LaunchCfg bc = cand[0];
     SolveBuf& b = c->sb;
     const int tb = (b.last == 0 && b.I[1]) ? 1 : 0;
-    for (int s : cand_s)
-        for (int t : cand_t)
-            for (int l : cand_l) {
-                int parity = !b.sign[tb];
-                SweepArgs a = make_args(c, c->lev, prec, cm, b.I[tb], nullptr, c->G, parity, 0, 0, o);
-                a.debug_stall = 0;
-                float ms = 0;
-                sweep_status st = run_sweep(c, c->lev, prec, s, t, l, a, bc32, &ms);
-                if (st != SWEEP_OK) return st;
-                b.sign[tb] = parity;
-                if (ms < best) {
-                    best = ms;
-                    bs = s;
-                    bt = t;
-                    bl = l;
-                }
-            }
-    t3[0] = bs;
-    t3[1] = bt;
-    t3[2] = bl;
-    *sched = bs;
-    *threads = bt;
-    *lanes = bl;
+    for (const LaunchCfg& k : cand) {
+        int parity = !b.sign[tb];
+        SweepArgs a = make_args(c, c->lev, prec, cm, b.I[tb], nullptr, c->G, parity, 0, 0, o);
+        a.debug_stall = 0;
+        float ms = 0;
+        sweep_status st = run_sweep(c, c->lev, prec, k.sched, k.threads, k.lanes, k.bpsm, a, bc32, &ms);
+        if (st != SWEEP_OK) return st;
+        b.sign[tb] = parity;
+        if (ms < best) {
+            best = ms;
+            bc = k;
+        }
+    }
+    t4[0] = bc.sched;
+    t4[1] = bc.threads;
+    t4[2] = bc.lanes;
+    t4[3] = bc.bpsm;
+    *out = bc;
     return SWEEP_OK;
 }
 
@@ -682,11 +731,12 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
     cudaEventRecord(t0, c->st);
-    float tc = 0, tl = 0;
-    sweep_status s = ensure_levels(c, &o, &tc, &tl);
+    float tc = 0, tl = 0, top = 0;
+    sweep_status s = ensure_levels(c, &o, &tc, &tl, &top);
     if (s != SWEEP_OK) return s;
     S.t_ms[0] = tc;
     S.t_ms[1] = tl;
+    S.t_ms[5] = top;
     const int64_t N = c->mesh.N;
     const int G = c->G, D = c->D;
     const size_t NG = (size_t)N * G;
@@ -712,11 +762,15 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     const void* cm = prec == 64 ? (const void*)c->cm64 : (const void*)c->cm32;
     int sched = o.schedule, threads = o.block_threads ? o.block_threads : 256;
     int lanes = o.lanes_per_task ? o.lanes_per_task : 4;
+    int bpsm = o.blocks_per_sm;
     if (!plain && sched == SWEEP_SCHED_AUTO) {
         CKL(launch_prep_material(N, G, c->mesh.vol, c->ka, c->ks, c->em, nullptr, prec == 32 ? c->cm32 : nullptr,
                                 prec == 64 ? c->cm64 : nullptr, c->st), "prep");
-        int tt = 0, tl = 0;
-        s = autotune(c, prec, cm, bc32.p, &o, &sched, &tt, &tl);
+        LaunchCfg best;
+        s = autotune(c, prec, cm, bc32.p, &o, &best);
+        sched = best.sched;
+        const int tt = best.threads, tl = best.lanes;
+        if (!o.blocks_per_sm) bpsm = best.bpsm;
         if (s != SWEEP_OK) return s;
         if (!o.block_threads) threads = tt;
         if (!o.lanes_per_task) lanes = tl;
@@ -741,6 +795,7 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     S.schedule_used = sched;
     S.lanes_used = lanes;
     S.threads_used = threads;
+    S.blocks_per_sm_used = bpsm;
     int it_pbc = 0, it_scat_total = 0, n_sweeps = 0;
     bool conv_pbc = !has_pbc, conv_scat = !c->has_scat;
     double res_pbc = 0.0, res_pbc_mean = 0.0, res_scat = 0.0;
@@ -759,7 +814,8 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
             const int parity = !b.sign[cur];
             SweepArgs a = make_args(c, c->lev, prec, cm, b.I[cur], has_pbc ? b.I[prev] : nullptr, G, parity, 0, 0, &o);
             a.debug_stall = o.debug_stall && n_sweeps == 0;
-            s = run_sweep(c, c->lev, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, lanes, a, bc32.p, &t_sweep);
+            s = run_sweep(c, c->lev, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, lanes, bpsm, a, bc32.p,
+                          &t_sweep);
             if (s != SWEEP_OK) return s;
             b.sign[cur] = parity;
             ++n_sweeps;
@@ -954,7 +1010,7 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
         int pI = !signI;
         SweepArgs a = make_args(c, *L, prec, cm, c->adjI, nullptr, G, pI, 0, 0, &o);
         a.debug_stall = 0;
-        s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, lanes, a, bc32.p, &t_sweep);
+        s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, lanes, 0, a, bc32.p, &t_sweep);
         if (s != SWEEP_OK) return s;
         signI = pI;
         // transposed sweep with split non-negative sources (2G groups)
@@ -963,7 +1019,7 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
         int pL = !signL;
         SweepArgs r = make_args(c, *L, prec, cm, c->adjL, nullptr, 2 * G, pL, 1, 0, &o);
         r.debug_stall = 0;
-        s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, lanes, r, nullptr, &t_sweep);
+        s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, lanes, 0, r, nullptr, &t_sweep);
         if (s != SWEEP_OK) return s;
         signL = pL;
         n_sweeps += 2;

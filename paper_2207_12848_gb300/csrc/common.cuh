@@ -27,6 +27,8 @@ constexpr double FOURPI = 4.0 * 3.14159265358979323846;
 // |t32| above this fraction of sum|An_i| fixes sign(t32) == sign(t64) (FP32 rounding of An, Omega and the
 // dot product is below 6 * 2^-24 of it); inside the band the sign is recomputed in FP64.
 constexpr float BAND_REL = 1.0e-6f;
+// inflow sides held in a 128-byte operator line; tasks with more take the geometry path
+constexpr int OP_MAX = 14;
 
 struct GridBar {
     unsigned count;
@@ -46,19 +48,19 @@ enum { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_OVERFLOW = 2 };
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ float ld_relaxed(const float* p) {
     float v;
-    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
     return v;
 }
 __device__ __forceinline__ double ld_relaxed(const double* p) {
     double v;
-    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
     return v;
 }
 __device__ __forceinline__ void st_relaxed(float* p, float v) {
-    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v));
 }
 __device__ __forceinline__ void st_relaxed(double* p, double v) {
-    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v));
 }
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
@@ -71,7 +73,7 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
 __device__ __forceinline__ int ld_volatile_i32(const int* p) { return *(const volatile int*)p; }
 __device__ __forceinline__ int ld_relaxed_i32(const int* p) {
     int v;
-    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p));
     return v;
 }
 
@@ -181,6 +183,9 @@ struct Levels {
     int64_t task_cap = 0;
     int4* info = nullptr;        // [N][nd] {upwind count, P_c (FP32), inflow mask, outflow mask}
     int4* trec = nullptr;        // task records {entry, row start, P_c, inflow mask}, same order as task
+    int4* op = nullptr;          // assembled operator: headers then entries (see build_operator), or null
+    size_t op_bytes = 0;
+    bool op_valid = false;
     int32_t* level = nullptr;    // [N][nd]
     int32_t* lvl_cnt = nullptr;  // [N+2]
     uint32_t* pad_off = nullptr; // [N+2] start of each level in the padded list
@@ -197,6 +202,8 @@ struct Levels {
 struct SweepArgs {
     const uint32_t* task;
     const int4* trec;     // task records (FP32 forward sweep)
+    const int4* op;       // assembled operator headers (one int4 per task), or null (FP32 forward sweep)
+    const int2* op_ent;   // assembled operator entries (OP_MAX int2 per task)
     int64_t n_chunks;
     const int64_t* lev_chunk;
     int n_levels;
@@ -235,11 +242,13 @@ cudaError_t launch_validate_mesh(int64_t N, int64_t F, const double* vol, const 
                                  const double* normal, const uint8_t* flags, const int64_t* mesh_off, int n_meshes,
                                  int* d_bad, cudaStream_t st);
 
+cudaError_t build_operator(const DevMesh& m, const Levels& L, const double* om64_all, const float4* om32_all,
+                           cudaStream_t st);
 cudaError_t levelise(const DevMesh& m, Levels& L, const double* om64_all, const float4* om32_all, int dev_sms,
                      GridBar* bar, int* err, long long budget, int64_t* d_scratch, cudaStream_t st, float* t_classify,
                      float* t_levelise, std::string* msg);
 
-int sweep_occupancy(int precision, int G, int threads, int nd, int lanes, int reverse);
+int sweep_occupancy(int precision, int G, int threads, int nd, int lanes, int reverse, bool op);
 cudaError_t launch_sweep(const SweepArgs& a, int precision, int blocks, int threads, cudaStream_t st);
 cudaError_t launch_plain_level(const SweepArgs& a, uint32_t begin, uint32_t end, cudaStream_t st);
 

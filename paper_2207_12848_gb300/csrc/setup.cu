@@ -540,7 +540,59 @@ __global__ void k_sort_levels(const uint32_t* raw, uint32_t* task, const uint32_
     }
 }
 
+// Assembled transport operator, 128 bytes per task in sweep order, as two arrays:
+//   hdr[t]          int4 {task entry, P_c (FP32 bits), number of inflow sides n (> OP_MAX: entries incomplete), 0}
+//   ent[t][0..13]   int2 {neighbour code, FP32 weight |A_f n_f.Omega|} of each inflow side, in row order
+// This is row c of the lower-triangular system L_Omega I = q (Sec. 2.3), its diagonal P_c plus
+// kappa_t V_c completed from the material at sweep time.
+__global__ void k_build_op(const int4* trec, int64_t n, const uint32_t* rowptr, const int4* side, const d4* side64,
+                           const float4* om32, const double* om64, uint32_t cmask, int cshift, int4* hdr,
+                           int2* ent) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int4 tr = trec[i];
+    if ((uint32_t)tr.x == TASK_PAD) {
+        hdr[i] = make_int4((int)TASK_PAD, 0, 0, 0);
+        return;
+    }
+    const uint32_t c = (uint32_t)tr.x & cmask, dl = (uint32_t)tr.x >> cshift;
+    const uint32_t r0 = (uint32_t)tr.y;
+    const float4 om = om32[dl];
+    int2* E = ent + i * OP_MAX;
+    int nin = 0;
+    for (uint32_t m = (uint32_t)tr.w; m; m &= m - 1) {
+        const uint32_t s = r0 + (uint32_t)(__ffs(m) - 1);
+        const int4 r = side[s];
+        const float w = fabsf(dot32(__int_as_float(r.y), __int_as_float(r.z), __int_as_float(r.w), om));
+        if (nin < OP_MAX) E[nin] = make_int2(r.x, __float_as_int(w));
+        ++nin;
+    }
+    if (tr.z < 0) {  // rows longer than 32 sides
+        const uint32_t r1 = rowptr[c + 1];
+        const double* o64 = om64 + 3 * dl;
+        for (uint32_t s = r0 + 32; s < r1; ++s) {
+            const int4 r = side[s];
+            const float ax = __int_as_float(r.y), ay = __int_as_float(r.z), az = __int_as_float(r.w);
+            const float t32 = dot32(ax, ay, az, om);
+            if (classify_side(t32, ax, ay, az, side64, s, o64) >= 0) continue;
+            if (nin < OP_MAX) E[nin] = make_int2(r.x, __float_as_int(fabsf(t32)));
+            ++nin;
+        }
+    }
+    hdr[i] = make_int4(tr.x, tr.z & 0x7fffffff, nin, 0);  // nin > OP_MAX: entries incomplete
+}
+
 }  // namespace
+
+cudaError_t build_operator(const DevMesh& m, const Levels& L, const double* om64_all, const float4* om32_all,
+                           cudaStream_t st) {
+    const int64_t n = L.h_lev_chunk.empty() ? 0 : L.h_lev_chunk.back() * 32;
+    if (n > 0)
+        k_build_op<<<nblk(n), 256, 0, st>>>(L.trec, n, m.rowptr, m.side, m.side64, om32_all + L.d0,
+                                            om64_all + 3 * (int64_t)L.d0, L.cmask, L.cshift, L.op,
+                                            reinterpret_cast<int2*>(L.op + n));
+    return cudaGetLastError();
+}
 
 cudaError_t levelise(const DevMesh& m, Levels& L, const double* om64_all, const float4* om32_all, int dev_sms,
                      GridBar* bar, int* err, long long budget, int64_t* d_scratch, cudaStream_t st,

@@ -93,17 +93,31 @@ def test_voronoi_fp64_intensities(ctx, G):
 
 
 # ---- FP32 sweeps with FP64 tallies ----------------------------------------------------------------------
+@pytest.mark.parametrize("geometry_only", [0, 1])
 @pytest.mark.parametrize("schedule", ["level", "dataflow", "auto"])
 @pytest.mark.parametrize("G", [1, 2, 4])
-def test_voronoi_fp32(ctx, schedule, G):
+def test_voronoi_fp32(ctx, schedule, G, geometry_only):
     p = configs.voronoi_small(6000, n_dir=16, n_groups=G, seed=10 + G, n_src=12)
     load(ctx, p)
-    J, Gm, st, s = ctx.solve(precision=32, schedule=schedule)
+    J, Gm, st, s = ctx.solve(precision=32, schedule=schedule, geometry_only=geometry_only)
     r = run_oracle(p)
     assert fp32_err(J, r["J"]) <= FP32_TOL
     assert fp32_err(Gm, r["Gamma"]) <= FP32_TOL
     assert abs(st["defect"]) <= DEFECT_TOL
     assert st["absorbed"] == pytest.approx(r["stats"]["absorbed"], rel=FP32_TOL)
+
+
+@pytest.mark.parametrize("lanes,bpsm", [(1, 1), (1, 0), (2, 0), (4, 0), (8, 0)])
+@pytest.mark.parametrize("G", [1, 3])
+def test_operator_kernels(ctx, lanes, bpsm, G):
+    # every form of the FP32 forward sweep over the assembled operator (and the periodic inflow path)
+    p = configs.voronoi_small(5000, periodic_box=True, n_dir=16, n_groups=G, seed=20 + G, n_src=10)
+    load(ctx, p)
+    J, Gm, st, s = ctx.solve(precision=32, schedule="dataflow", lanes_per_task=lanes, blocks_per_sm=bpsm,
+                             tol_pbc=0.0, max_it_pbc=4)
+    assert st["lanes_used"] == lanes
+    r = run_oracle(p, tol_pbc=0.0, max_it_pbc=4)
+    assert fp32_err(J, r["J"]) <= FP32_TOL
 
 
 @pytest.mark.parametrize("precision", [32, 64])
@@ -208,6 +222,36 @@ def test_adjoint_rejects_scattering(ctx):
 
 
 # ---- edge cases -------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("geometry_only", [0, 1])
+def test_high_degree_cell(ctx, geometry_only):
+    # a generator at the centre of a sphere of 60 others: its cell has ~60 faces (rows longer than
+    # 32 sides) and ~30 inflow sides per direction (more than an operator line holds)
+    rng = np.random.default_rng(61)
+    u = rng.normal(size=(60, 3))
+    u /= np.linalg.norm(u, axis=1)[:, None]
+    inner = 0.5 + 0.08 * u
+    outer = rng.random((1500, 3))
+    outer = outer[np.linalg.norm(outer - 0.5, axis=1) > 0.16]
+    pts = np.concatenate([[[0.5, 0.5, 0.5]], inner, outer])
+    m = voronoi_mesh(pts, threads=4)
+    assert m.neighbour_counts()[0] > 40
+    om, w = fibonacci_directions(24, seed=5)
+    ka = np.full((m.n_cells, 2), 3.0)
+    ka[:, 1] = 0.5
+    eps = np.zeros((m.n_cells, 2))
+    eps[0] = 1.0
+    eps[100] = 2.0
+    ctx.set_mesh(m)
+    ctx.set_directions(om, w)
+    ctx.set_material(ka, eps)
+    J, G, st, s = ctx.solve(precision=32, geometry_only=geometry_only)
+    r = oracle.solve(m, om, w, ka, eps, threads=8)
+    assert fp32_err(J, r["J"]) <= FP32_TOL
+    J64, _, _, _ = ctx.solve(precision=64)
+    assert rel_max(J64, r["J"]) <= 1e-12
+
+
+
 def test_single_cell_and_single_direction(ctx):
     m = lattice_mesh(1)
     ctx.set_mesh(m)
