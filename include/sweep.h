@@ -184,6 +184,28 @@ sweep_status sweep_adjoint_dev(sweep_ctx* ctx, const sweep_opts* opts, const dou
                                const double* dl_dGamma, double* grad_kappa_abs, double* grad_emissivity,
                                sweep_stats* stats);
 
+/* Wavefront levels of one direction without any device allocation. The paper has no counterpart:
+ * this serves callers that cannot allocate GPU memory where they need a sweep order (a fixed
+ * device-memory budget such as an arena or pool that hands out no new blocks, or memory nearly
+ * exhausted by another component, where cudaMalloc would fail or stall the device).
+ *   device, cuda_stream    the GPU and stream to run on (NULL stream = legacy default stream)
+ *   face_cells[n_faces][2], normal[n_faces][3], flags[n_faces]
+ *                          DEVICE pointers, the mesh faces as for sweep_set_mesh (not validated)
+ *   omega[3]               HOST pointer, the direction
+ *   level[n_cells]         DEVICE output: level of every cell (as sweep_levels)
+ *   depth                  HOST output: 1 + the largest level
+ * Limit: 1 <= n_cells <= 65536; larger meshes are rejected with SWEEP_ERR_INVALID_ARG before any
+ * GPU work. The working memory is one static device array (65536 counters plus a control block,
+ * 256 KB) that every GPU loading the library holds until exit; every call shares it and clears
+ * what must start at zero, so calls whose GPU work overlaps (other host threads, other streams)
+ * race and give wrong results. The first call on a device looks up the array's device address
+ * (a one-time set-up); make that first call before any stream capture. The call returns after
+ * the result is on the device (it synchronizes the stream). Errors: INVALID_ARG (sizes, null
+ * pointers, device), CYCLE, TIMEOUT (a bounded wait gave up), CUDA. */
+sweep_status sweep_levels_noalloc(int device, void* cuda_stream, int64_t n_cells, int64_t n_faces,
+                                  const int32_t* face_cells, const double* normal, const uint8_t* flags,
+                                  const double* omega, int32_t* level, int32_t* depth);
+
 /* Static description of a status code; sweep_last_error gives the context's last detailed message. */
 const char* sweep_status_string(sweep_status status);
 const char* sweep_last_error(const sweep_ctx* ctx);

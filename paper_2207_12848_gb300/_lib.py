@@ -27,7 +27,8 @@ SCHEDULES = {"auto": 0, "level": 1, "dataflow": 2, "plain": 3}
 # every entry point include/sweep.h declares
 EXPORTS = ("sweep_default_opts", "sweep_create", "sweep_destroy", "sweep_set_mesh", "sweep_set_directions",
            "sweep_set_material", "sweep_set_material_dev", "sweep_solve", "sweep_solve_dev", "sweep_levels",
-           "sweep_intensity", "sweep_adjoint", "sweep_adjoint_dev", "sweep_status_string", "sweep_last_error")
+           "sweep_intensity", "sweep_adjoint", "sweep_adjoint_dev", "sweep_status_string", "sweep_last_error",
+           "sweep_levels_noalloc")
 
 
 class sweep_opts(ctypes.Structure):
@@ -90,6 +91,7 @@ def load(path: str | None = None):
         "sweep_adjoint_dev": (S, [P, OP, P, P, P, P, SP]),
         "sweep_status_string": (ctypes.c_char_p, [S]),
         "sweep_last_error": (ctypes.c_char_p, [P]),
+        "sweep_levels_noalloc": (S, [ctypes.c_int, P, I64, I64, P, P, P, P, P, ctypes.POINTER(I32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -9,7 +9,7 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libsweep.so")
-SOURCES = ["api.cu", "setup.cu", "sweep.cu", "tally.cu"]
+SOURCES = ["api.cu", "setup.cu", "sweep.cu", "tally.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 EXTRA = os.environ.get("SWEEP_NVCC_EXTRA", "").split()  # extra nvcc flags (tuning experiments)
