@@ -329,3 +329,19 @@ def test_periodic_headline_full_size(ctx):
     has_p[c1[per]] = True
     ok = ~has_p & (rhs > 1e-30 * rhs.max())
     assert np.max(np.abs(lhs[ok] - rhs[ok]) / rhs[ok]) <= 1e-5
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_plain32_against_stored_golden(ctx, precision):
+    # stored FP64 oracle values of the 32^3 lattice set-up (tests/golden/oracle_plain32.json)
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_plain32.json")) as f:
+        g = json.load(f)
+    p = configs.plain32()
+    load(ctx, p)
+    J, Gm, st, s = ctx.solve(precision=precision)
+    tol = 1e-12 if precision == 64 else FP32_TOL
+    assert np.max(np.abs(J[g["cells"], 0] - g["J"]) / np.abs(g["J"])) <= tol
+    assert np.max(np.abs(Gm[g["cells"], 0] - g["Gamma"]) / np.abs(g["Gamma"])) <= tol
+    assert [ctx.levels(d)[1] for d in range(p.n_dir)] == g["depths"]

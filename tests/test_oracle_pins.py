@@ -306,3 +306,22 @@ def test_invalid_inputs_rejected():
     from synth.mesh import Mesh
     mb = Mesh(volume=m.volume, face_cells=bad, area=m.area, normal=m.normal, flags=m.flags)
     assert oracle.solve(mb, p.omega, p.weight, p.kappa_abs, p.emissivity)["rc"] == oracle.ERR_ARG
+
+
+def test_oracle_matches_stored_plain32_golden():
+    # tests/golden/oracle_plain32.json was written by tests/golden/make_oracle_golden.py (oracle only);
+    # its depths are also the lattice closed form 3(n-1)+1 for directions with no zero component, and its
+    # absorbed plus escaped rate is the unit source (vacuum conservation)
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_plain32.json")) as f:
+        g = json.load(f)
+    p = configs.plain32()
+    r = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, threads=4)
+    assert np.allclose(r["J"][g["cells"], 0], g["J"], rtol=1e-13, atol=0)
+    assert np.allclose(r["Gamma"][g["cells"], 0], g["Gamma"], rtol=1e-13, atol=0)
+    assert g["Gamma_total"] + g["escaped"] == pytest.approx(1.0, abs=1e-12)
+    assert np.all(np.abs(p.omega) > 0)
+    assert g["depths"] == [3 * 31 + 1] * p.n_dir
+    rc, _, depth = oracle.levels(p.mesh, p.omega)
+    assert rc == 0 and list(depth) == g["depths"]
