@@ -317,7 +317,10 @@ def run_ours(args, dist: Dist):
     alg_bytes = bpu * N * D * G
     peaks = measured_peaks()
     achieved = alg_bytes / avg_launch_s / 1e9
-    roof = {"bound": "hbm", "kernel": "k_sweep<float,%d> (dataflow/level persistent sweep)" % G,
+    from paper_2207_12848_gb300._lib import KERNELS
+    roof = {"bound": "hbm", "kernel": "%s (%s schedule, %d lanes per task)" % (
+                KERNELS.get(last.get("kernel_used", 0), "?"), {1: "level", 2: "dataflow"}.get(last["schedule_used"], "?"),
+                last["lanes_used"]),
             "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
             "peak_source": peaks["source"], "traffic": profiled_traffic(args.workload),
             "bytes_per_update": bpu, "face_sides_per_cell": fbar, "updates_per_launch": N * D * G,

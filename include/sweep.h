@@ -102,7 +102,19 @@ typedef struct {
     int32_t lanes_used;        /* lanes per task of the batched sweep that ran */
     int32_t threads_used;      /* threads per block of the batched sweep that ran */
     int32_t blocks_per_sm_used;/* resident blocks per SM it was launched with (0 = maximum) */
+    int32_t kernel_used;       /* SWEEP_KERNEL_* form of the batched sweep that ran last */
 } sweep_stats;
+
+/* Forms of the batched sweep kernel (sweep_stats.kernel_used). */
+enum {
+    SWEEP_KERNEL_NONE = 0,
+    SWEEP_KERNEL_PLAIN = 1,          /* one launch per (direction, level), FP64 */
+    SWEEP_KERNEL_GEOMETRY = 2,       /* lane groups reading the mesh rows (FP64, and every adjoint sweep) */
+    SWEEP_KERNEL_RECORDS = 3,        /* FP32 forward, lane groups over task records and mesh rows */
+    SWEEP_KERNEL_OPERATOR = 4,       /* FP32 forward over the assembled operator, lane groups */
+    SWEEP_KERNEL_OPERATOR_LEAN = 5,  /* the same, one group and 8 lanes per task, dataflow schedule */
+    SWEEP_KERNEL_OPERATOR_TMA = 6    /* FP32 forward over the assembled operator, one task per thread, bulk copies */
+};
 
 /* Fill *opts with defaults: precision 32, AUTO schedule, tolerances 1e-6, 100 iterations. */
 void sweep_default_opts(sweep_opts* opts);

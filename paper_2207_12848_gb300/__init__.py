@@ -6,5 +6,13 @@ package only loads it and marshals arguments. Build it with ``build.build()``.
 from ._lib import (EXPORTS, SCHEDULES, SWEEP_FACE_BOUNDARY, SWEEP_FACE_PERIODIC, Context, SweepError, default_opts,
                    load, sweep_opts, sweep_stats)
 
-__all__ = ["Context", "SweepError", "default_opts", "load", "sweep_opts", "sweep_stats", "EXPORTS", "SCHEDULES",
+
+
+def transport_solve(*args, **kw):
+    """Differentiable solve (see autograd.transport_solve); imports torch on first use."""
+    from .autograd import transport_solve as f
+    return f(*args, **kw)
+
+
+__all__ = ["transport_solve", "Context", "SweepError", "default_opts", "load", "sweep_opts", "sweep_stats", "EXPORTS", "SCHEDULES",
            "SWEEP_FACE_BOUNDARY", "SWEEP_FACE_PERIODIC"]

@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/sweep.h: context, uploads and validation,
 // the solve loop (periodic iteration of Sec. 2.7 outside, source iteration of Alg. 1 inside,
 // batched sweep innermost), the schedule autotuner and the adjoint with recompute batches.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -36,6 +37,7 @@ struct sweep_ctx {
     double* om64 = nullptr;
     double* w64 = nullptr;
     float4* om32 = nullptr;
+    float4* om32lo = nullptr;  // [D] direction minus its FP32 value
     double wsum = 0.0;
     // material
     bool has_mat = false;
@@ -53,6 +55,7 @@ struct sweep_ctx {
     size_t ng_cap = 0;
     double* partial = nullptr;
     int partial_cap = 0;
+    int last_kernel = SWEEP_KERNEL_NONE;  // form of the last batched sweep launched
     double* red = nullptr;          // [4]
     unsigned long long* dmax = nullptr;
     GridBar* bar = nullptr;
@@ -102,12 +105,12 @@ void dfree(T*& p) {
 
 void free_levels(Levels& L) {
     dfree(L.raw); dfree(L.task); dfree(L.trec); dfree(L.info); dfree(L.level); dfree(L.lvl_cnt); dfree(L.pad_off);
-    dfree(L.lev_chunk); dfree(L.seg_off); dfree(L.op);
+    dfree(L.lev_chunk); dfree(L.seg_off); dfree(L.op); dfree(L.dlev);
     L = Levels();
 }
 
 void free_mesh(DevMesh& m) {
-    dfree(m.rowptr); dfree(m.side); dfree(m.side64); dfree(m.vol); dfree(m.pcells); dfree(m.bcells);
+    dfree(m.rowptr); dfree(m.side); dfree(m.side64); dfree(m.side_lo); dfree(m.vol); dfree(m.pcells); dfree(m.bcells);
     m = DevMesh();
 }
 
@@ -152,6 +155,8 @@ sweep_status alloc_levels(sweep_ctx* c, Levels& L, int d0, int nd) {
     CK(cudaMalloc(&L.lvl_cnt, sizeof(int32_t) * (N + 2)), "alloc level counts");
     CK(cudaMalloc(&L.pad_off, sizeof(uint32_t) * (N + 2)), "alloc level offsets");
     CK(cudaMalloc(&L.lev_chunk, sizeof(int64_t) * (N + 2)), "alloc level chunks");
+    L.dlev_cap = (int)std::min<int64_t>(N + 1, 1 << 16);
+    CK(cudaMalloc(&L.dlev, sizeof(int32_t) * ((int64_t)nd * (2 * L.dlev_cap + 2) + 1)), "alloc level tables");
     // worst case of levels x (nd+1) segment starts is only known after levelisation
     return SWEEP_OK;
 }
@@ -161,7 +166,7 @@ sweep_status run_levelise(sweep_ctx* c, Levels& L, int d0, int nd, long long bud
     if (s != SWEEP_OK) return s;
     CK(cudaMemsetAsync(c->derr, 0, sizeof(int), c->st), "reset error word");
     std::string msg;
-    CK(levelise(c->mesh, L, c->om64, c->om32, c->sms, c->bar, c->derr, budget, c->scratch, c->st, t1, t2, &msg),
+    CK(levelise(c->mesh, L, c->om64, c->om32, c->om32lo, c->sms, c->bar, c->derr, budget, c->scratch, c->st, t1, t2, &msg),
        "levelise");
     c->launches += 3;  // classification, levelisation, per-level direction grouping
     if (!L.valid) {
@@ -238,7 +243,9 @@ SweepArgs make_args(sweep_ctx* c, const Levels& L, int precision, const void* cm
     a.rowptr = c->mesh.rowptr;
     a.side = c->mesh.side;
     a.side64 = c->mesh.side64;
+    a.side_lo = c->mesh.side_lo;
     a.om32 = c->om32 + L.d0;
+    a.om32lo = c->om32lo + L.d0;
     a.om64 = c->om64 + 3 * (int64_t)L.d0;
     a.w64 = c->w64 + L.d0;
     a.cm = cm;
@@ -270,6 +277,7 @@ sweep_status run_sweep(sweep_ctx* c, const Levels& L, int precision, int schedul
     CK(cudaMemsetAsync(c->derr, 0, sizeof(int), c->st), "reset error word");
     cudaEventRecord(e0, c->st);
     if (schedule == SWEEP_SCHED_PLAIN) {
+        c->last_kernel = SWEEP_KERNEL_PLAIN;
         const int nd = L.nd;
         for (int d = 0; d < nd; ++d) {
             for (int li = 0; li < L.n_levels; ++li) {
@@ -283,7 +291,7 @@ sweep_status run_sweep(sweep_ctx* c, const Levels& L, int precision, int schedul
         if (per_sm < 1) return bad(c, "sweep kernel does not fit on an SM");
         if (bpsm > 0 && bpsm < per_sm) per_sm = bpsm;
         a.level_sync = schedule == SWEEP_SCHED_LEVEL ? 1 : 0;
-        CKL(launch_sweep(a, precision, c->sms * per_sm, threads, c->st), "sweep launch");
+        CKL(launch_sweep(a, precision, c->sms * per_sm, threads, c->st, &c->last_kernel), "sweep launch");
     }
     cudaEventRecord(e1, c->st);
     int herr = 0;
@@ -370,7 +378,7 @@ sweep_status sweep_destroy(sweep_ctx* c) {
     free_solution(c);
     free_material(c);
     free_mesh(c->mesh);
-    dfree(c->om64); dfree(c->w64); dfree(c->om32);
+    dfree(c->om64); dfree(c->w64); dfree(c->om32); dfree(c->om32lo);
     dfree(c->cm32); dfree(c->cm64);
     dfree(c->J); dfree(c->Jold); dfree(c->Gam); dfree(c->jn); dfree(c->jn1);
     dfree(c->partial); dfree(c->red); dfree(c->dmax); dfree(c->bar); dfree(c->derr); dfree(c->scratch);
@@ -462,6 +470,7 @@ sweep_status sweep_set_mesh(sweep_ctx* c, int64_t n_cells, const double* volume,
     CKM(cudaMalloc(&m.rowptr, sizeof(uint32_t) * (n_cells + 1)), "alloc rows");
     CKM(cudaMalloc(&m.side, sizeof(int4) * (S > 0 ? S : 1) + 64 * sizeof(int4)), "alloc sides");
     CKM(cudaMalloc(&m.side64, sizeof(d4) * (S > 0 ? S : 1)), "alloc sides");
+    CKM(cudaMalloc(&m.side_lo, sizeof(float4) * (S > 0 ? S : 1)), "alloc sides");
     CKM(launch_build_csr(m, d_fc, d_area, d_normal, d_flags, d_tmp, c->st), "build CSR");
     CKM(cudaStreamSynchronize(c->st), "build CSR");
 #undef CKM
@@ -485,19 +494,25 @@ sweep_status sweep_set_directions(sweep_ctx* c, int32_t n_dir, const double* ome
     }
     if (!(std::fabs(ws - FOURPI) <= 1e-12 * FOURPI)) return bad(c, "direction weights must sum to 4pi");
     cudaStreamSynchronize(c->st);
-    dfree(c->om64); dfree(c->w64); dfree(c->om32);
+    dfree(c->om64); dfree(c->w64); dfree(c->om32); dfree(c->om32lo);
     free_levels(c->lev);
     free_levels(c->adj_lev);
     free_solution(c);
-    std::vector<float4> o32(n_dir);
-    for (int d = 0; d < n_dir; ++d)
-        o32[d] = make_float4((float)omega[3 * d], (float)omega[3 * d + 1], (float)omega[3 * d + 2], (float)weight[d]);
+    std::vector<float4> o32(n_dir), o32lo(n_dir);
+    for (int d = 0; d < n_dir; ++d) {
+        const double* w = omega + 3 * d;
+        o32[d] = make_float4((float)w[0], (float)w[1], (float)w[2], (float)weight[d]);
+        o32lo[d] = make_float4((float)(w[0] - (double)o32[d].x), (float)(w[1] - (double)o32[d].y),
+                               (float)(w[2] - (double)o32[d].z), 0.f);
+    }
     CK(cudaMalloc(&c->om64, sizeof(double) * 3 * n_dir), "alloc directions");
     CK(cudaMalloc(&c->w64, sizeof(double) * n_dir), "alloc directions");
     CK(cudaMalloc(&c->om32, sizeof(float4) * n_dir), "alloc directions");
+    CK(cudaMalloc(&c->om32lo, sizeof(float4) * n_dir), "alloc directions");
     CK(cudaMemcpyAsync(c->om64, omega, sizeof(double) * 3 * n_dir, cudaMemcpyHostToDevice, c->st), "upload");
     CK(cudaMemcpyAsync(c->w64, weight, sizeof(double) * n_dir, cudaMemcpyHostToDevice, c->st), "upload");
     CK(cudaMemcpyAsync(c->om32, o32.data(), sizeof(float4) * n_dir, cudaMemcpyHostToDevice, c->st), "upload");
+    CK(cudaMemcpyAsync(c->om32lo, o32lo.data(), sizeof(float4) * n_dir, cudaMemcpyHostToDevice, c->st), "upload");
     CK(cudaStreamSynchronize(c->st), "upload directions");
     c->D = n_dir;
     c->wsum = ws;
@@ -591,7 +606,7 @@ sweep_status assemble_operator(sweep_ctx* c, Levels& L, float* t_ms) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, c->st);
-    CKL(build_operator(c->mesh, L, c->om64, c->om32, c->st), "assemble operator");
+    CKL(build_operator(c->mesh, L, c->om64, c->om32, c->om32lo, c->st), "assemble operator");
     cudaEventRecord(e1, c->st);
     CK(cudaEventSynchronize(e1), "assemble operator");
     float ms = 0;
@@ -747,9 +762,12 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     if (s != SWEEP_OK) return s;
     s = ensure_solution(c, prec, has_pbc);
     if (s != SWEEP_OK) return s;
-    int nblk = nblocks256(NG > (size_t)c->mesh.n_pcells ? NG : c->mesh.n_pcells);
-    if (c->mesh.n_bcells > nblk) nblk = nblocks256(c->mesh.n_bcells);
-    s = ensure_partial(c, nblk + 1);
+    // partial sums: one pair per 256-thread block of the tallies, one pair per periodic or boundary cell
+    const int nblk = nblocks256(NG);
+    int64_t npart = nblk + 1;
+    if (c->mesh.n_pcells > npart) npart = c->mesh.n_pcells;
+    if (c->mesh.n_bcells > npart) npart = c->mesh.n_bcells;
+    s = ensure_partial(c, (int)npart);
     if (s != SWEEP_OK) return s;
     Bc32 bc32;
     if (prec == 32 && c->bc) {
@@ -820,17 +838,11 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
             b.sign[cur] = parity;
             ++n_sweeps;
             ++it_scat;
+            // without scattering nothing inside the iteration needs J: the final tally below computes it
+            if (!c->has_scat) break;
             cudaEventRecord(u0, c->st);
             CKL(launch_tally(prec, b.I[cur], N, G, D, 0, c->w64, c->wsum, c->mesh.vol, c->ka, c->em, c->J, c->Gam,
                             c->partial, nblk, c->st), "tally");
-            if (!c->has_scat) {
-                cudaEventRecord(u1, c->st);
-                cudaEventSynchronize(u1);
-                float tt = 0;
-                cudaEventElapsedTime(&tt, u0, u1);
-                t_other += tt;
-                break;
-            }
             CK(cudaMemsetAsync(c->dmax, 0, sizeof(unsigned long long), c->st), "init");
             CKL(launch_scat_residual(NG, c->J, c->Jold, c->dmax, c->st), "scattering residual");
             cudaEventRecord(u1, c->st);
@@ -848,8 +860,7 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
         CK(cudaMemsetAsync(c->dmax, 0, sizeof(unsigned long long), c->st), "init");
         CKL(launch_periodic_source(prec, c->mesh, b.I[cur], G, D, c->om64, c->w64, c->jn1, c->jn, c->dmax, c->partial,
                                   nblk, c->st), "periodic source");
-        int npb = nblocks256(c->mesh.n_pcells > 0 ? c->mesh.n_pcells : 1);
-        CKL(launch_reduce_sum(c->partial, npb, c->red + 2, c->st), "reduce");
+        CKL(launch_reduce_sum(c->partial, (int)c->mesh.n_pcells, c->red + 2, c->st), "reduce");
         cudaEventRecord(u1, c->st);
         res_pbc = read_max(c);
         double hred[2] = {0, 0};
@@ -874,7 +885,7 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     if (c->mesh.n_bcells > 0) {
         CKL(launch_boundary_tally(prec, c->mesh, b.I[fin], G, D, 0, c->om64, c->w64, c->bc, c->partial, nblk, c->st),
            "boundary tally");
-        CKL(launch_reduce_sum(c->partial, nblocks256(c->mesh.n_bcells), c->red + 2, c->st), "reduce");
+        CKL(launch_reduce_sum(c->partial, (int)c->mesh.n_bcells, c->red + 2, c->st), "reduce");
     } else {
         CK(cudaMemsetAsync(c->red + 2, 0, 2 * sizeof(double), c->st), "init");
     }
@@ -897,6 +908,7 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     S.it_scat = it_scat_total;
     S.it_pbc = it_pbc;
     S.n_sweeps = n_sweeps;
+    S.kernel_used = c->last_kernel;
     S.res_scat = res_scat;
     S.res_pbc = res_pbc;
     S.res_pbc_mean = res_pbc_mean;
@@ -1043,6 +1055,7 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
     S.updates = (double)N * D * G * 3;  // forward, and the transposed sweep over 2G split groups
     S.updates_per_s = ttot > 0 ? S.updates / (ttot * 1e-3) : 0.0;
     S.schedule_used = plain ? SWEEP_SCHED_PLAIN : sched;
+    S.kernel_used = c->last_kernel;
     S.kernel_launches = (int32_t)(c->launches - launches0);
     if (stats) *stats = S;
     return SWEEP_OK;

@@ -113,13 +113,47 @@ __device__ __forceinline__ float dot32(float ax, float ay, float az, const float
 
 // Classification of one face side for a direction: +1 outflow, -1 inflow, 0 tie (no flux).
 // t32 is the FP32 dot product An.Omega; the FP64 twin decides inside the rounding band.
+static __device__ __noinline__ int exact_sign(const d4* side64, uint32_t s, const double* om64) {
+    const double t = exact_t(side64[s], om64);
+    return t > 0.0 ? 1 : (t < 0.0 ? -1 : 0);
+}
 __device__ __forceinline__ int classify_side(float t32, float ax, float ay, float az, const d4* side64,
                                              uint32_t s, const double* om64) {
-    float band = BAND_REL * (fabsf(ax) + fabsf(ay) + fabsf(az));
+    const float band = BAND_REL * (fabsf(ax) + fabsf(ay) + fabsf(az));
     if (t32 > band) return 1;
     if (t32 < -band) return -1;
-    double t = exact_t(side64[s], om64);
-    return t > 0.0 ? 1 : (t < 0.0 ? -1 : 0);
+    return exact_sign(side64, s, om64);
+}
+
+// FP32 weight |a.Omega| of a face side (a = A n_out, its area vector), accurate to about one
+// rounding for every side, grazing ones included. The area vector and the direction are each
+// carried as an FP32 pair hi + lo (hi in the side record and the FP32 direction, lo beside them);
+// the hi-hi products are formed exactly (product plus its FMA residual) and summed with
+// error-free two-sums, and the residuals and hi-lo cross terms are added as one correction. Every
+// step is symmetric under negation, so the two sides of a face (exactly negated records) get
+// weights of exactly equal magnitude.
+__device__ __forceinline__ float dot_comp(float ax, float ay, float az, const float4& lo, const float4& om,
+                                          const float4& oml) {
+    const float px = __fmul_rn(ax, om.x), py = __fmul_rn(ay, om.y), pz = __fmul_rn(az, om.z);
+    const float ex = fmaf(ax, om.x, -px), ey = fmaf(ay, om.y, -py), ez = fmaf(az, om.z, -pz);
+    const float s1 = __fadd_rn(px, py);
+    const float b1 = __fsub_rn(s1, px);
+    const float r1 = __fadd_rn(__fsub_rn(px, __fsub_rn(s1, b1)), __fsub_rn(py, b1));
+    const float s2 = __fadd_rn(s1, pz);
+    const float b2 = __fsub_rn(s2, s1);
+    const float r2 = __fadd_rn(__fsub_rn(s1, __fsub_rn(s2, b2)), __fsub_rn(pz, b2));
+    float c = __fadd_rn(__fadd_rn(__fadd_rn(ex, ey), ez), __fadd_rn(r1, r2));
+    c = fmaf(ax, oml.x, c);
+    c = fmaf(ay, oml.y, c);
+    c = fmaf(az, oml.z, c);
+    c = fmaf(lo.x, om.x, c);
+    c = fmaf(lo.y, om.y, c);
+    c = fmaf(lo.z, om.z, c);
+    return __fadd_rn(s2, c);
+}
+
+__device__ __forceinline__ float side_weight(const int4& r, const float4& lo, const float4& om, const float4& oml) {
+    return fabsf(dot_comp(__int_as_float(r.y), __int_as_float(r.z), __int_as_float(r.w), lo, om, oml));
 }
 
 // Grid-wide barrier for persistent cooperative kernels, with a bounded wait.
@@ -162,7 +196,8 @@ struct DevMesh {
     int64_t N = 0, F = 0, S = 0, NB = 0;  // cells, faces, face sides, boundary faces
     uint32_t* rowptr = nullptr;            // [N+1]
     int4* side = nullptr;                  // [S]
-    d4* side64 = nullptr;             // [S]
+    d4* side64 = nullptr;                  // [S]
+    float4* side_lo = nullptr;             // [S] area vector minus its FP32 value in the side record
     double* vol = nullptr;                 // [N]
     int32_t* pcells = nullptr;             // cells with periodic sides
     int64_t n_pcells = 0;
@@ -196,6 +231,10 @@ struct Levels {
     std::vector<uint32_t> h_seg_off;
     std::vector<int32_t> depth;  // per direction
     int64_t n_tasks = 0;
+    // direction-parallel levelisation: per direction, the cells per level and the start of each level
+    // in that direction's list, for up to dlev_cap levels; then level-0 sizes, depths, overflow word
+    int32_t* dlev = nullptr;     // [nd][2][dlev_cap] + [nd] + [nd] + [1]
+    int dlev_cap = 0;
 };
 
 // Kernel argument block of the batched sweep.
@@ -213,7 +252,9 @@ struct SweepArgs {
     const uint32_t* rowptr;
     const int4* side;
     const d4* side64;
+    const float4* side_lo;  // [S] low parts of the area vectors
     const float4* om32;   // [nd]
+    const float4* om32lo; // [nd] low parts of the directions
     const double* om64;   // [nd][3]
     const double* w64;    // [nd] weights (adjoint source scaling)
     const void* cm;       // [N][G] {q, dnm} in the sweep precision
@@ -243,13 +284,14 @@ cudaError_t launch_validate_mesh(int64_t N, int64_t F, const double* vol, const 
                                  int* d_bad, cudaStream_t st);
 
 cudaError_t build_operator(const DevMesh& m, const Levels& L, const double* om64_all, const float4* om32_all,
-                           cudaStream_t st);
-cudaError_t levelise(const DevMesh& m, Levels& L, const double* om64_all, const float4* om32_all, int dev_sms,
-                     GridBar* bar, int* err, long long budget, int64_t* d_scratch, cudaStream_t st, float* t_classify,
-                     float* t_levelise, std::string* msg);
+                           const float4* om32lo_all, cudaStream_t st);
+cudaError_t levelise(const DevMesh& m, Levels& L, const double* om64_all, const float4* om32_all,
+                     const float4* om32lo_all, int dev_sms, GridBar* bar, int* err, long long budget,
+                     int64_t* d_scratch, cudaStream_t st, float* t_classify, float* t_levelise, std::string* msg);
 
 int sweep_occupancy(int precision, int G, int threads, int nd, int lanes, int reverse, bool op);
-cudaError_t launch_sweep(const SweepArgs& a, int precision, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_sweep(const SweepArgs& a, int precision, int blocks, int threads, cudaStream_t st,
+                         int* kernel = nullptr);
 cudaError_t launch_plain_level(const SweepArgs& a, uint32_t begin, uint32_t end, cudaStream_t st);
 
 cudaError_t launch_prep_material(int64_t N, int G, const double* vol, const double* ka, const double* ks,

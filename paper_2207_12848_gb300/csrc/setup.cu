@@ -10,6 +10,7 @@
 // for an acyclic graph (Sec. 2.3). K2 is Alg. 2's Kahn queue run one wavefront at a time for
 // all directions at once: the tasks of level L decrement the upwind counters n(c, Omega) of
 // their downwind neighbours; a counter reaching zero puts that task into level L+1.
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -183,7 +184,7 @@ __global__ void k_flag_boundary(int64_t F, const uint8_t* flags, int32_t* isb) {
 
 __global__ void k_fill_sides(int64_t S, const int64_t* key, const int32_t* fc, const double* area,
                              const double* normal, const uint8_t* flags, const int64_t* bidx, int4* side,
-                             d4* side64) {
+                             d4* side64, float4* side_lo) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     int64_t k = key[s];
@@ -199,13 +200,17 @@ __global__ void k_fill_sides(int64_t S, const int64_t* key, const int32_t* fc, c
         int32_t other = sd ? fc[2 * f] : fc[2 * f + 1];
         nbr = (fl & SWEEP_FACE_PERIODIC) ? (other | NBR_PERIODIC) : other;
     }
+    // area vector A n_out in FP64, as an FP32 value plus its (exactly representable) remainder
+    const double ax = A * nx, ay = A * ny, az = A * nz;
+    const float hx = (float)ax, hy = (float)ay, hz = (float)az;
     int4 r;
     r.x = nbr;
-    r.y = __float_as_int((float)(A * nx));
-    r.z = __float_as_int((float)(A * ny));
-    r.w = __float_as_int((float)(A * nz));
+    r.y = __float_as_int(hx);
+    r.z = __float_as_int(hy);
+    r.w = __float_as_int(hz);
     side[s] = r;
     side64[s] = d4{nx, ny, nz, A};
+    side_lo[s] = make_float4((float)(ax - (double)hx), (float)(ay - (double)hy), (float)(az - (double)hz), 0.f);
 }
 
 __global__ void k_cell_kinds(int64_t N, const uint32_t* rowptr, const int4* side, int32_t* isp, int32_t* isb) {
@@ -274,7 +279,8 @@ cudaError_t launch_build_csr(const DevMesh& mc, const int32_t* fc, const double*
         k_flag_boundary<<<nblk(F), 256, 0, st>>>(F, flags, isb);
         TRY(scan_i32(isb, F, bidx, scratch, total, st));
     }
-    if (S > 0) k_fill_sides<<<nblk(S), 256, 0, st>>>(S, key, fc, area, normal, flags, bidx, m.side, m.side64);
+    if (S > 0) k_fill_sides<<<nblk(S), 256, 0, st>>>(S, key, fc, area, normal, flags, bidx, m.side, m.side64,
+                                                     m.side_lo);
     // periodic / boundary cell lists (increasing cell order)
     if (N > 0) {
         k_cell_kinds<<<nblk(N), 256, 0, st>>>(N, m.rowptr, m.side, isp, isb);
@@ -328,8 +334,9 @@ namespace {
 //               bit k: side k (< 32) is an inflow side (any kind),
 //               bit k: side k (< 32) is an outflow side to an interior cell}
 __global__ void k_classify(int64_t N, int nd, const uint32_t* rowptr, const int4* side, const d4* side64,
-                           const float4* om32, const double* om64, int4* info, int32_t* level, uint32_t* raw,
-                           int32_t* lvl_cnt, int cshift) {
+                           const float4* side_lo, const float4* om32, const float4* om32lo, const double* om64,
+                           int4* info, int32_t* level, uint32_t* raw, int32_t* lvl_cnt, int cshift, uint32_t* dlist,
+                           int32_t* n0) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool active = t < N * (int64_t)nd;
     int cnt = 0;
@@ -337,7 +344,7 @@ __global__ void k_classify(int64_t N, int nd, const uint32_t* rowptr, const int4
     if (active) {
         int64_t c = t / nd;
         int dl = (int)(t - c * nd);
-        float4 om = om32[dl];
+        const float4 om = om32[dl], oml = om32lo[dl];
         const double* o64 = om64 + 3 * dl;
         const uint32_t r0 = rowptr[c], r1 = rowptr[c + 1];
         float P = 0.f;
@@ -345,13 +352,12 @@ __global__ void k_classify(int64_t N, int nd, const uint32_t* rowptr, const int4
         for (uint32_t s = r0; s < r1; ++s) {
             int4 r = side[s];
             float ax = __int_as_float(r.y), ay = __int_as_float(r.z), az = __int_as_float(r.w);
-            float t32 = dot32(ax, ay, az, om);
-            int sgn = classify_side(t32, ax, ay, az, side64, s, o64);
+            const int sgn = classify_side(dot32(ax, ay, az, om), ax, ay, az, side64, s, o64);
             if (sgn == 0) continue;
             const uint32_t k = s - r0;
             const bool interior = r.x >= 0 && !(r.x & NBR_PERIODIC);
             if (sgn > 0) {
-                P += fabsf(t32);
+                P += side_weight(r, side_lo[s], om, oml);
                 if (k < 32 && interior) outm |= 1u << k;
             } else {
                 if (k < 32) inm |= 1u << k;
@@ -364,6 +370,14 @@ __global__ void k_classify(int64_t N, int nd, const uint32_t* rowptr, const int4
         entry = ((uint32_t)dl << cshift) | (uint32_t)c;
     }
     bool push = active && cnt == 0;
+    if (dlist) {
+        // per-direction level-0 lists for the direction-parallel levelisation
+        if (push) {
+            const uint32_t dl = entry >> cshift;
+            dlist[(size_t)dl * N + atomicAdd(&n0[dl], 1)] = entry & ~(~0u << cshift);
+        }
+        return;
+    }
     unsigned m = __ballot_sync(0xffffffffu, push);
     if (m) {
         int lane = threadIdx.x & 31;
@@ -540,14 +554,204 @@ __global__ void k_sort_levels(const uint32_t* raw, uint32_t* task, const uint32_
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// K2, direction-parallel form: the dependency graphs of different directions share nothing, so
+// one block levelises one direction at a time (Alg. 2 applied level by level): the cells of level L
+// release their downwind cells, a counter reaching zero puts the cell on level L+1. Levels are
+// separated by __syncthreads only -- no grid barrier and no device-wide queue -- and each level's
+// list is kept in shared memory (spilling to the direction's list in global memory when wide).
+// ---------------------------------------------------------------------------------------------
+constexpr int LD_THREADS = 1024;
+constexpr int LD_KL = 2;     // lanes per task
+constexpr int LD_KU = 8;     // face sides per lane per pass
+constexpr int LD_Q = 4096;   // shared-memory list capacity per level
+
+struct DirLevArgs {
+    int64_t N;
+    int nd;
+    int cap;                 // levels the per-direction tables hold
+    const uint32_t* rowptr;
+    const int4* side;
+    const d4* side64;
+    const float4* om32;
+    const double* om64;
+    int4* info;
+    int32_t* level;
+    uint32_t* dlist;         // [nd][N] cells of each direction in level order; level 0 from the classification
+    const int32_t* n0;       // [nd] level-0 sizes
+    int32_t* dcnt;           // [nd][cap] cells on each level
+    int32_t* dbase;          // [nd][cap] start of each level in dlist
+    int32_t* depth;          // [nd]
+    int32_t* overflow;       // set when a direction has more than cap levels
+};
+
+__global__ void __launch_bounds__(LD_THREADS, 1) k_levelise_dir(DirLevArgs a) {
+    __shared__ uint32_t s_q[2][LD_Q];
+    __shared__ int s_next;
+    const int gl = threadIdx.x % LD_KL;
+    constexpr int TPR = LD_THREADS / LD_KL;  // tasks per round
+    for (int d = blockIdx.x; d < a.nd; d += gridDim.x) {
+        uint32_t* out = a.dlist + (size_t)d * a.N;
+        int32_t* cnt = a.dcnt + (size_t)d * a.cap;
+        int32_t* bas = a.dbase + (size_t)d * a.cap;
+        const float4 om = a.om32[d];
+        const double* o64 = a.om64 + 3 * d;
+        int n = a.n0[d];
+        for (int i = threadIdx.x; i < n && i < LD_Q; i += LD_THREADS) s_q[0][i] = out[i];
+        uint32_t base = 0;
+        int L = 0, cur = 0;
+        while (n > 0) {
+            if (L >= a.cap) {
+                if (threadIdx.x == 0) atomicExch(a.overflow, 1);
+                break;
+            }
+            if (threadIdx.x == 0) {
+                cnt[L] = n;
+                bas[L] = (int32_t)base;
+                s_next = 0;
+            }
+            __syncthreads();
+            const uint32_t nbase = base + (uint32_t)n;
+            for (int i0 = 0; i0 < n; i0 += TPR) {
+                const int i = i0 + threadIdx.x / LD_KL;
+                if (i >= n) continue;
+                const uint32_t c = n <= LD_Q ? s_q[cur][i] : out[base + i];
+                const uint32_t r0 = a.rowptr[c], r1 = a.rowptr[c + 1];
+                const uint32_t outm = (uint32_t)a.info[(int64_t)c * a.nd + d].w;
+                for (uint32_t b = r0; b < r1; b += LD_KL * LD_KU) {
+                    int4 r[LD_KU];
+#pragma unroll
+                    for (int k = 0; k < LD_KU; ++k) {
+                        const uint32_t s = b + gl + k * LD_KL;
+                        const uint32_t idx = s - r0;
+                        const bool need = s < r1 && (idx >= 32u || ((outm >> idx) & 1u));
+                        r[k] = need ? a.side[s] : make_int4(-1, 0, 0, 0);
+                    }
+                    int old[LD_KU];
+#pragma unroll
+                    for (int k = 0; k < LD_KU; ++k) {
+                        old[k] = 0;
+                        const uint32_t s = b + gl + k * LD_KL;
+                        if (r[k].x < 0 || (r[k].x & NBR_PERIODIC)) continue;
+                        if (s - r0 >= 32u) {
+                            const float ax = __int_as_float(r[k].y), ay = __int_as_float(r[k].z),
+                                        az = __int_as_float(r[k].w);
+                            if (classify_side(dot32(ax, ay, az, om), ax, ay, az, a.side64, s, o64) <= 0) continue;
+                        }
+                        old[k] = atomicSub(&a.info[(int64_t)r[k].x * a.nd + d].x, 1);
+                    }
+#pragma unroll
+                    for (int k = 0; k < LD_KU; ++k) {
+                        if (old[k] != 1) continue;
+                        const uint32_t x = (uint32_t)r[k].x;
+                        a.level[(int64_t)x * a.nd + d] = L + 1;
+                        const int p = atomicAdd(&s_next, 1);
+                        if (nbase + (uint32_t)p < (uint32_t)a.N) out[nbase + p] = x;
+                        if (p < LD_Q) s_q[cur ^ 1][p] = x;
+                    }
+                }
+            }
+            __syncthreads();
+            n = s_next;
+            base = nbase;
+            cur ^= 1;
+            ++L;
+            __syncthreads();  // everyone has read s_next before it is reset
+        }
+        if (threadIdx.x == 0) a.depth[d] = L;
+        __syncthreads();
+    }
+}
+
+// Cells on each level over all directions (lvl_cnt[L]) for L < n_levels.
+__global__ void k_level_totals(const int32_t* dcnt, const int32_t* depth, int nd, int cap, int n_levels,
+                               int32_t* lvl_cnt) {
+    const int L = blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= n_levels) return;
+    int s = 0;
+    for (int d = 0; d < nd; ++d)
+        if (L < depth[d]) s += dcnt[(size_t)d * cap + L];
+    lvl_cnt[L] = s;
+}
+
+// Start of every level in the padded task list (each level padded to 32 tasks) and its chunk
+// index, by one block: pad_off[L], lev_chunk[L] for L <= n_levels.
+__global__ void k_level_starts(const int32_t* lvl_cnt, int n_levels, uint32_t* pad_off, int64_t* lev_chunk) {
+    __shared__ uint32_t s_sum[1024];
+    const int per = (n_levels + blockDim.x - 1) / blockDim.x;
+    const int i0 = threadIdx.x * per;
+    uint32_t loc = 0;
+    for (int i = i0; i < i0 + per && i < n_levels; ++i) loc += round32((uint32_t)lvl_cnt[i]);
+    s_sum[threadIdx.x] = loc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int t = 0; t < (int)blockDim.x; ++t) {
+            const uint32_t v = s_sum[t];
+            s_sum[t] = run;
+            run += v;
+        }
+        pad_off[n_levels] = run;
+        lev_chunk[n_levels] = run / 32;
+    }
+    __syncthreads();
+    uint32_t run = s_sum[threadIdx.x];
+    for (int i = i0; i < i0 + per && i < n_levels; ++i) {
+        pad_off[i] = run;
+        lev_chunk[i] = run / 32;
+        run += round32((uint32_t)lvl_cnt[i]);
+    }
+}
+
+// Per-(level, direction) segment starts: seg_off[L][d] = pad_off[L] + cells of directions < d.
+__global__ void k_seg_starts(const int32_t* dcnt, const int32_t* depth, int nd, int cap, int n_levels,
+                             const uint32_t* pad_off, uint32_t* seg_off) {
+    const int L = blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= n_levels) return;
+    uint32_t run = pad_off[L];
+    for (int d = 0; d < nd; ++d) {
+        seg_off[(int64_t)L * (nd + 1) + d] = run;
+        if (L < depth[d]) run += (uint32_t)dcnt[(size_t)d * cap + L];
+    }
+    seg_off[(int64_t)L * (nd + 1) + nd] = run;
+}
+
+// One block per level: copy each direction's cells of that level into its segment of the task list,
+// with the task records, and pad the level to 32 tasks.
+__global__ void k_gather_levels(const uint32_t* dlist, const int32_t* dcnt, const int32_t* dbase,
+                                const int32_t* depth, int64_t N, int nd, int cap, int cshift, const uint32_t* pad_off,
+                                const int32_t* lvl_cnt, const uint32_t* seg_off, const uint32_t* rowptr,
+                                const int4* info, uint32_t* task, int4* trec) {
+    const int L = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int d = warp; d < nd; d += nw) {
+        if (L >= depth[d]) continue;
+        const int n = dcnt[(size_t)d * cap + L];
+        const uint32_t* src = dlist + (size_t)d * N + dbase[(size_t)d * cap + L];
+        const uint32_t dst = seg_off[(int64_t)L * (nd + 1) + d];
+        for (int i = lane; i < n; i += 32) {
+            const uint32_t c = src[i];
+            const uint32_t e = ((uint32_t)d << cshift) | c;
+            const int4 inf = info[(int64_t)c * nd + d];
+            task[dst + i] = e;
+            trec[dst + i] = make_int4((int)e, (int)rowptr[c], inf.y, inf.z);
+        }
+    }
+    const uint32_t b0 = pad_off[L] + (uint32_t)lvl_cnt[L], b1 = pad_off[L + 1];
+    for (uint32_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+        task[i] = TASK_PAD;
+        trec[i] = make_int4((int)TASK_PAD, 0, 0, 0);
+    }
+}
+
 // Assembled transport operator, 128 bytes per task in sweep order, as two arrays:
 //   hdr[t]          int4 {task entry, P_c (FP32 bits), number of inflow sides n (> OP_MAX: entries incomplete), 0}
 //   ent[t][0..13]   int2 {neighbour code, FP32 weight |A_f n_f.Omega|} of each inflow side, in row order
 // This is row c of the lower-triangular system L_Omega I = q (Sec. 2.3), its diagonal P_c plus
 // kappa_t V_c completed from the material at sweep time.
 __global__ void k_build_op(const int4* trec, int64_t n, const uint32_t* rowptr, const int4* side, const d4* side64,
-                           const float4* om32, const double* om64, uint32_t cmask, int cshift, int4* hdr,
-                           int2* ent) {
+                           const float4* side_lo, const float4* om32, const float4* om32lo, const double* om64,
+                           uint32_t cmask, int cshift, int4* hdr, int2* ent) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int4 tr = trec[i];
@@ -557,25 +761,23 @@ __global__ void k_build_op(const int4* trec, int64_t n, const uint32_t* rowptr, 
     }
     const uint32_t c = (uint32_t)tr.x & cmask, dl = (uint32_t)tr.x >> cshift;
     const uint32_t r0 = (uint32_t)tr.y;
-    const float4 om = om32[dl];
+    const float4 om = om32[dl], oml = om32lo[dl];
+    const double* o64 = om64 + 3 * dl;
     int2* E = ent + i * OP_MAX;
     int nin = 0;
     for (uint32_t m = (uint32_t)tr.w; m; m &= m - 1) {
         const uint32_t s = r0 + (uint32_t)(__ffs(m) - 1);
         const int4 r = side[s];
-        const float w = fabsf(dot32(__int_as_float(r.y), __int_as_float(r.z), __int_as_float(r.w), om));
-        if (nin < OP_MAX) E[nin] = make_int2(r.x, __float_as_int(w));
+        if (nin < OP_MAX) E[nin] = make_int2(r.x, __float_as_int(side_weight(r, side_lo[s], om, oml)));
         ++nin;
     }
     if (tr.z < 0) {  // rows longer than 32 sides
         const uint32_t r1 = rowptr[c + 1];
-        const double* o64 = om64 + 3 * dl;
         for (uint32_t s = r0 + 32; s < r1; ++s) {
             const int4 r = side[s];
             const float ax = __int_as_float(r.y), ay = __int_as_float(r.z), az = __int_as_float(r.w);
-            const float t32 = dot32(ax, ay, az, om);
-            if (classify_side(t32, ax, ay, az, side64, s, o64) >= 0) continue;
-            if (nin < OP_MAX) E[nin] = make_int2(r.x, __float_as_int(fabsf(t32)));
+            if (classify_side(dot32(ax, ay, az, om), ax, ay, az, side64, s, o64) >= 0) continue;
+            if (nin < OP_MAX) E[nin] = make_int2(r.x, __float_as_int(side_weight(r, side_lo[s], om, oml)));
             ++nin;
         }
     }
@@ -585,42 +787,101 @@ __global__ void k_build_op(const int4* trec, int64_t n, const uint32_t* rowptr, 
 }  // namespace
 
 cudaError_t build_operator(const DevMesh& m, const Levels& L, const double* om64_all, const float4* om32_all,
-                           cudaStream_t st) {
+                           const float4* om32lo_all, cudaStream_t st) {
     const int64_t n = L.h_lev_chunk.empty() ? 0 : L.h_lev_chunk.back() * 32;
     if (n > 0)
-        k_build_op<<<nblk(n), 256, 0, st>>>(L.trec, n, m.rowptr, m.side, m.side64, om32_all + L.d0,
-                                            om64_all + 3 * (int64_t)L.d0, L.cmask, L.cshift, L.op,
+        k_build_op<<<nblk(n), 256, 0, st>>>(L.trec, n, m.rowptr, m.side, m.side64, m.side_lo, om32_all + L.d0,
+                                            om32lo_all + L.d0, om64_all + 3 * (int64_t)L.d0, L.cmask, L.cshift, L.op,
                                             reinterpret_cast<int2*>(L.op + n));
     return cudaGetLastError();
 }
 
-cudaError_t levelise(const DevMesh& m, Levels& L, const double* om64_all, const float4* om32_all, int dev_sms,
-                     GridBar* bar, int* err, long long budget, int64_t* d_scratch, cudaStream_t st,
-                     float* t_classify, float* t_levelise, std::string* msg) {
-    cudaError_t e;
+namespace {
+
+cudaError_t classify(const DevMesh& m, Levels& L, const float4* om32, const float4* om32lo, const double* om64,
+                     bool per_direction, cudaStream_t st) {
     const int64_t N = m.N;
     const int nd = L.nd;
-    const float4* om32 = om32_all + L.d0;
-    const double* om64 = om64_all + 3 * (int64_t)L.d0;
-    cudaEvent_t ev[3];
-    for (auto& x : ev) cudaEventCreate(&x);
-    cudaEventRecord(ev[0], st);
-    e = cudaMemsetAsync(L.lvl_cnt, 0, sizeof(int32_t) * (N + 2), st);
+    cudaError_t e = cudaMemsetAsync(L.lvl_cnt, 0, sizeof(int32_t) * (N + 2), st);
     if (e != cudaSuccess) return e;
-    int64_t tot = N * (int64_t)nd;
+    int32_t* n0 = L.dlev + (int64_t)nd * 2 * L.dlev_cap;
+    if (per_direction) {
+        e = cudaMemsetAsync(n0, 0, sizeof(int32_t) * (2 * nd + 1), st);  // level-0 sizes, depths, overflow
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t tot = N * (int64_t)nd;
     if (tot > 0)
-        k_classify<<<nblk(tot), 256, 0, st>>>(N, nd, m.rowptr, m.side, m.side64, om32, om64, L.info, L.level, L.raw,
-                                               L.lvl_cnt, L.cshift);
-    e = cudaGetLastError();
+        k_classify<<<nblk(tot), 256, 0, st>>>(N, nd, m.rowptr, m.side, m.side64, m.side_lo, om32, om32lo, om64,
+                                               L.info, L.level, L.raw, L.lvl_cnt, L.cshift,
+                                               per_direction ? L.raw : nullptr, n0);
+    return cudaGetLastError();
+}
+
+cudaError_t ensure_seg(Levels& L, int nlev) {
+    const int nd = L.nd;
+    if ((int64_t)nlev * (nd + 1) <= L.seg_cap) return cudaSuccess;
+    if (L.seg_off) cudaFree(L.seg_off);
+    L.seg_off = nullptr;
+    L.seg_cap = 0;
+    const int64_t want = ((int64_t)nlev + nlev / 4 + 16) * (nd + 1);
+    cudaError_t e = cudaMalloc(&L.seg_off, sizeof(uint32_t) * want);
     if (e != cudaSuccess) return e;
-    cudaEventRecord(ev[1], st);
-    // persistent levelisation: one co-resident grid
+    L.seg_cap = want;
+    return cudaSuccess;
+}
+
+// Direction-parallel levelisation. Sets *nlev_out, or *overflow when a direction is deeper than the
+// per-direction tables (the classification counters are then spent: classify again before retrying).
+cudaError_t levelise_by_direction(const DevMesh& m, Levels& L, const float4* om32, const double* om64, int dev_sms,
+                                  cudaStream_t st, int* nlev_out, bool* overflow) {
+    const int nd = L.nd, cap = L.dlev_cap;
+    int32_t* dcnt = L.dlev;
+    int32_t* dbase = dcnt + (int64_t)nd * cap;
+    int32_t* n0 = dbase + (int64_t)nd * cap;
+    int32_t* depth = n0 + nd;
+    int32_t* ovf = depth + nd;
+    DirLevArgs a;
+    a.N = m.N; a.nd = nd; a.cap = cap; a.rowptr = m.rowptr; a.side = m.side; a.side64 = m.side64; a.om32 = om32;
+    a.om64 = om64; a.info = L.info; a.level = L.level; a.dlist = L.raw; a.n0 = n0; a.dcnt = dcnt; a.dbase = dbase;
+    a.depth = depth; a.overflow = ovf;
+    const int blocks = nd < dev_sms ? nd : dev_sms;
+    k_levelise_dir<<<blocks, LD_THREADS, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    std::vector<int32_t> h(nd + 1);
+    cudaMemcpyAsync(h.data(), depth, sizeof(int32_t) * (nd + 1), cudaMemcpyDeviceToHost, st);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    *overflow = h[nd] != 0;
+    if (*overflow) return cudaSuccess;
+    int nlev = 0;
+    for (int d = 0; d < nd; ++d) nlev = std::max(nlev, h[d]);
+    *nlev_out = nlev;
+    if (nlev == 0) {
+        cudaMemsetAsync(L.pad_off, 0, sizeof(uint32_t), st);
+        return cudaMemsetAsync(L.lev_chunk, 0, sizeof(int64_t), st);
+    }
+    e = ensure_seg(L, nlev);
+    if (e != cudaSuccess) return e;
+    k_level_totals<<<nblk(nlev), 256, 0, st>>>(dcnt, depth, nd, cap, nlev, L.lvl_cnt);
+    k_level_starts<<<1, 1024, 0, st>>>(L.lvl_cnt, nlev, L.pad_off, L.lev_chunk);
+    k_seg_starts<<<nblk(nlev), 256, 0, st>>>(dcnt, depth, nd, cap, nlev, L.pad_off, L.seg_off);
+    k_gather_levels<<<nlev, 256, 0, st>>>(L.raw, dcnt, dbase, depth, m.N, nd, cap, L.cshift, L.pad_off, L.lvl_cnt,
+                                          L.seg_off, m.rowptr, L.info, L.task, L.trec);
+    return cudaGetLastError();
+}
+
+// Level-synchronous levelisation of all directions at once (one cooperative grid, a grid barrier
+// per level), then the per-level grouping by direction. Sets *nlev_out, or *timed_out.
+cudaError_t levelise_all(const DevMesh& m, Levels& L, const float4* om32, const double* om64, int dev_sms,
+                         GridBar* bar, int* err, long long budget, int64_t* d_scratch, cudaStream_t st, int* nlev_out,
+                         bool* timed_out) {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_levelise, 256, 0);
     if (per_sm < 1) per_sm = 1;
-    int blocks = dev_sms * per_sm;
+    const int blocks = dev_sms * per_sm;
     LeveliseArgs a;
-    a.N = N; a.nd = nd; a.cshift = L.cshift; a.cmask = L.cmask; a.rowptr = m.rowptr; a.side = m.side;
+    a.N = m.N; a.nd = L.nd; a.cshift = L.cshift; a.cmask = L.cmask; a.rowptr = m.rowptr; a.side = m.side;
     a.side64 = m.side64; a.om32 = om32; a.om64 = om64; a.info = L.info; a.level = L.level; a.raw = L.raw;
     a.lvl_cnt = L.lvl_cnt; a.pad_off = L.pad_off; a.lev_chunk = L.lev_chunk;
     a.n_levels_out = (int32_t*)d_scratch; a.bar = bar; a.err = err; a.budget = budget;
@@ -635,7 +896,7 @@ cudaError_t levelise(const DevMesh& m, Levels& L, const double* om64_all, const 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_levelise, a);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_levelise, a);
     if (e != cudaSuccess) return e;
     int32_t nlev = 0;
     int herr = 0;
@@ -643,42 +904,61 @@ cudaError_t levelise(const DevMesh& m, Levels& L, const double* om64_all, const 
     cudaMemcpyAsync(&herr, err, sizeof herr, cudaMemcpyDeviceToHost, st);
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
-    if (herr != DEV_OK) {
-        *msg = "levelisation: device wait timed out";
-        L.valid = false;
-        return cudaSuccess;
+    *timed_out = herr != DEV_OK;
+    *nlev_out = nlev;
+    if (*timed_out || nlev == 0) return cudaSuccess;
+    e = ensure_seg(L, nlev);
+    if (e != cudaSuccess) return e;
+    k_sort_levels<<<nlev, 256, 2 * L.nd * sizeof(int), st>>>(L.raw, L.task, L.pad_off, L.lvl_cnt, L.nd, L.cshift,
+                                                              L.seg_off, L.cmask, m.rowptr, L.info, L.trec);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t levelise(const DevMesh& m, Levels& L, const double* om64_all, const float4* om32_all,
+                     const float4* om32lo_all, int dev_sms, GridBar* bar, int* err, long long budget,
+                     int64_t* d_scratch, cudaStream_t st, float* t_classify, float* t_levelise, std::string* msg) {
+    cudaError_t e;
+    const int64_t N = m.N;
+    const int nd = L.nd;
+    const float4* om32 = om32_all + L.d0;
+    const float4* om32lo = om32lo_all + L.d0;
+    const double* om64 = om64_all + 3 * (int64_t)L.d0;
+    cudaEvent_t ev[3];
+    for (auto& x : ev) cudaEventCreate(&x);
+    cudaEventRecord(ev[0], st);
+    const bool by_dir = L.dlev != nullptr && L.dlev_cap > 0;
+    e = classify(m, L, om32, om32lo, om64, by_dir, st);
+    if (e != cudaSuccess) return e;
+    cudaEventRecord(ev[1], st);
+    int nlev = 0;
+    bool done_by_dir = false;
+    if (by_dir) {
+        bool overflow = false;
+        e = levelise_by_direction(m, L, om32, om64, dev_sms, st, &nlev, &overflow);
+        if (e != cudaSuccess) return e;
+        done_by_dir = !overflow;
+        if (overflow) {
+            e = classify(m, L, om32, om32lo, om64, false, st);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    if (!done_by_dir) {
+        bool timed_out = false;
+        e = levelise_all(m, L, om32, om64, dev_sms, bar, err, budget, d_scratch, st, &nlev, &timed_out);
+        if (e != cudaSuccess) return e;
+        if (timed_out) {
+            *msg = "levelisation: device wait timed out";
+            L.valid = false;
+            return cudaSuccess;
+        }
     }
     L.n_levels = nlev;
     std::vector<int32_t> cnt(nlev > 0 ? nlev : 1);
     if (nlev > 0) cudaMemcpyAsync(cnt.data(), L.lvl_cnt, sizeof(int32_t) * nlev, cudaMemcpyDeviceToHost, st);
     L.h_lev_chunk.assign(nlev + 1, 0);
     cudaMemcpyAsync(L.h_lev_chunk.data(), L.lev_chunk, sizeof(int64_t) * (nlev + 1), cudaMemcpyDeviceToHost, st);
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return e;
-    int64_t done = 0;
-    for (int i = 0; i < nlev; ++i) done += cnt[i];
-    L.n_tasks = done;
-    if (done != tot) {
-        *msg = "dependency graph is cyclic: " + std::to_string(tot - done) + " tasks never became ready";
-        L.valid = false;
-        L.n_levels = 0;
-        return cudaSuccess;
-    }
-    if ((int64_t)nlev * (nd + 1) > L.seg_cap) {
-        if (L.seg_off) cudaFree(L.seg_off);
-        L.seg_off = nullptr;
-        L.seg_cap = 0;
-        int64_t want = ((int64_t)nlev + nlev / 4 + 16) * (nd + 1);
-        e = cudaMalloc(&L.seg_off, sizeof(uint32_t) * want);
-        if (e != cudaSuccess) return e;
-        L.seg_cap = want;
-    }
-    if (nlev > 0) {
-        k_sort_levels<<<nlev, 256, 2 * nd * sizeof(int), st>>>(L.raw, L.task, L.pad_off, L.lvl_cnt, nd, L.cshift,
-                                                               L.seg_off, L.cmask, m.rowptr, L.info, L.trec);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
     L.h_seg_off.assign((size_t)nlev * (nd + 1), 0);
     if (nlev > 0)
         cudaMemcpyAsync(L.h_seg_off.data(), L.seg_off, sizeof(uint32_t) * L.h_seg_off.size(), cudaMemcpyDeviceToHost,
@@ -686,6 +966,16 @@ cudaError_t levelise(const DevMesh& m, Levels& L, const double* om64_all, const 
     cudaEventRecord(ev[2], st);
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
+    int64_t done = 0;
+    for (int i = 0; i < nlev; ++i) done += cnt[i];
+    L.n_tasks = done;
+    const int64_t tot = N * (int64_t)nd;
+    if (done != tot) {
+        *msg = "dependency graph is cyclic: " + std::to_string(tot - done) + " tasks never became ready";
+        L.valid = false;
+        L.n_levels = 0;
+        return cudaSuccess;
+    }
     L.depth.assign(nd, 0);
     for (int lv = 0; lv < nlev; ++lv)
         for (int d = 0; d < nd; ++d) {

@@ -40,13 +40,7 @@ __device__ __forceinline__ double fmar(double a, double b, double c) { return __
 __device__ __forceinline__ float divr(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double divr(double a, double b) { return __ddiv_rn(a, b); }
 
-// Rare paths, kept out of line so the common path stays short:
-// exact FP64 classification inside the FP32 rounding band ...
-__device__ __noinline__ int classify_exact(const d4* side64, uint32_t s, const double* om64) {
-    const double t = exact_t(side64[s], om64);
-    return t > 0.0 ? 1 : (t < 0.0 ? -1 : 0);
-}
-
+// Rare path, kept out of line so the common path stays short:
 // Wait (bounded) until *p carries this sweep's parity; returns the magnitude. false on give-up.
 template <typename real>
 __device__ __noinline__ bool wait_value_slow(const real* p, int parity, const SweepArgs& a, real& out);
@@ -117,6 +111,7 @@ __device__ __forceinline__ bool group_task(const SweepArgs& a, uint32_t entry, u
     }
     const double* om64 = a.om64 + 3 * dl;
     const float4 om = s_om[dl];
+    const float4 oml = F64 ? make_float4(0.f, 0.f, 0.f, 0.f) : a.om32lo[dl];
     real* I = reinterpret_cast<real*>(a.I);
     const size_t slab = (size_t)dl * a.N;
     bool fail = false;
@@ -152,11 +147,8 @@ __device__ __forceinline__ bool group_task(const SweepArgs& a, uint32_t entry, u
                 } else {
                     const float ax = __int_as_float(rec[k].y), ay = __int_as_float(rec[k].z),
                                 az = __int_as_float(rec[k].w);
-                    const float t32 = dot32(ax, ay, az, om);
-                    const float band = BAND_REL * ((fabsf(ax) + fabsf(ay)) + fabsf(az));
-                    sgn = t32 > band ? 1 : (t32 < -band ? -1 : 2);
-                    if (sgn == 2) sgn = classify_exact(a.side64, s, om64);
-                    w[k] = (real)fabsf(t32);
+                    sgn = classify_side(dot32(ax, ay, az, om), ax, ay, az, a.side64, s, om64);
+                    if (sgn != 0) w[k] = (real)side_weight(rec[k], a.side_lo[s], om, oml);
                 }
                 if (sgn > 0) P = addr(P, w[k]);
                 const bool inflow = sgn != 0 && (a.reverse ? (sgn > 0) : (sgn < 0));
@@ -355,6 +347,7 @@ __device__ __forceinline__ bool rec_task(const SweepArgs& a, const int4 tr, cons
             if (g < G) q[g] = cm[g];
     }
     const float4 om = s_om[dl];
+    const float4 oml = a.om32lo[valid ? dl : 0u];
     const size_t slab = (size_t)dl * a.N;
     bool fail = false;
     if (stall && gl == 0) {
@@ -390,7 +383,7 @@ __device__ __forceinline__ bool rec_task(const SweepArgs& a, const int4 tr, cons
 #pragma unroll
         for (int k = 0; k < U; ++k) {
             if (!ok[k]) continue;
-            const float w = fabsf(dot32(__int_as_float(rec[k].y), __int_as_float(rec[k].z), __int_as_float(rec[k].w), om));
+            const float w = side_weight(rec[k], __ldg(a.side_lo + r0 + pos[k]), om, oml);
             add_inflow<GC>(a, rec[k].x, w, v[k], slab, G, acc, fail);
         }
     }
@@ -400,9 +393,8 @@ __device__ __forceinline__ bool rec_task(const SweepArgs& a, const int4 tr, cons
         for (uint32_t s = r0 + 32 + gl; s < r1; s += L) {
             const int4 r = a.side[s];
             const float ax = __int_as_float(r.y), ay = __int_as_float(r.z), az = __int_as_float(r.w);
-            const float t32 = dot32(ax, ay, az, om);
-            if (classify_side(t32, ax, ay, az, a.side64, s, om64) < 0)
-                add_inflow<GC>(a, r.x, fabsf(t32), nullptr, slab, G, acc, fail);
+            if (classify_side(dot32(ax, ay, az, om), ax, ay, az, a.side64, s, om64) < 0)
+                add_inflow<GC>(a, r.x, side_weight(r, a.side_lo[s], om, oml), nullptr, slab, G, acc, fail);
         }
     }
 #pragma unroll
@@ -1136,7 +1128,7 @@ int occupancy_rec_lanes(int G, int threads, size_t smem) {
 }
 
 template <typename real>
-cudaError_t launch_typed(const SweepArgs& a, int blocks, int threads, cudaStream_t st) {
+cudaError_t launch_typed(const SweepArgs& a, int blocks, int threads, cudaStream_t st, int* kid) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(blocks);
     cfg.blockDim = dim3(threads);
@@ -1148,6 +1140,7 @@ cudaError_t launch_typed(const SweepArgs& a, int blocks, int threads, cudaStream
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (sizeof(real) == 4 && !a.reverse && a.op && a.lanes == 1) {  // thread per task, TMA-staged rows
+        *kid = SWEEP_KERNEL_OPERATOR_TMA;
         cudaLaunchConfig_t c2 = cfg;
         c2.blockDim = dim3(TMA_WARPS * 32);
         c2.dynamicSmemBytes = tma_smem_bytes(a.nd);
@@ -1159,16 +1152,19 @@ cudaError_t launch_typed(const SweepArgs& a, int blocks, int threads, cudaStream
         }
     }
     if (sizeof(real) == 4 && !a.reverse && a.op) {  // FP32 forward over the assembled operator
+        *kid = a.lanes >= 8 && a.G == 1 && !a.level_sync ? SWEEP_KERNEL_OPERATOR_LEAN : SWEEP_KERNEL_OPERATOR;
         if (a.lanes <= 2) return launch_op_lanes<2>(a, cfg);
         if (a.lanes == 4) return launch_op_lanes<4>(a, cfg);
         return launch_op_lanes<8>(a, cfg);
     }
     if (sizeof(real) == 4 && !a.reverse) {  // FP32 forward: the record kernel
+        *kid = SWEEP_KERNEL_RECORDS;
         if (a.lanes == 1) return launch_rec_lanes<1>(a, cfg);
         if (a.lanes == 2) return launch_rec_lanes<2>(a, cfg);
         if (a.lanes == 4) return launch_rec_lanes<4>(a, cfg);
         return launch_rec_lanes<8>(a, cfg);
     }
+    *kid = SWEEP_KERNEL_GEOMETRY;
     if (a.lanes == 16) return launch_lanes<real, 16>(a, cfg);
     if (a.lanes == 2) return launch_lanes<real, 2>(a, cfg);
     if (a.lanes == 1) return launch_lanes<real, 1>(a, cfg);
@@ -1223,8 +1219,12 @@ int sweep_occupancy(int precision, int G, int threads, int nd, int lanes, int re
     return lanes == 8 ? occupancy_lanes<float, 8>(G, threads, smem) : occupancy_lanes<float, 4>(G, threads, smem);
 }
 
-cudaError_t launch_sweep(const SweepArgs& a, int precision, int blocks, int threads, cudaStream_t st) {
-    return precision == 64 ? launch_typed<double>(a, blocks, threads, st) : launch_typed<float>(a, blocks, threads, st);
+cudaError_t launch_sweep(const SweepArgs& a, int precision, int blocks, int threads, cudaStream_t st, int* kernel) {
+    int kid = 0;
+    cudaError_t e = precision == 64 ? launch_typed<double>(a, blocks, threads, st, &kid)
+                                    : launch_typed<float>(a, blocks, threads, st, &kid);
+    if (kernel) *kernel = kid;
+    return e;
 }
 
 cudaError_t launch_plain_level(const SweepArgs& a, uint32_t begin, uint32_t end, cudaStream_t st) {

@@ -97,30 +97,103 @@ __global__ void k_tally(const real* I, int64_t N, int G, int nd, const double* w
     block_sum2(absorbed, emitted, partial);
 }
 
+// Sums over the rows of a few cells (boundary or periodic cells) for every direction: one block per
+// cell, its threads over directions, so the FP64 classification and the strided intensity reads of
+// the D directions run in parallel; the block's partial sums are then combined in a fixed order
+// (warp shuffles, then the warps in index order), so results do not depend on timing.
+constexpr int ROW_THREADS = 128;
+
+__device__ __forceinline__ double block_sum_fixed(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();  // sh may still be read from the previous call
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < ROW_THREADS / 32; ++w) t += sh[w];
+    return t;
+}
+
+// Escaped (outflow through vacuum faces) and injected (boundary inflow) photon rates of one boundary
+// cell, into partial[2k], partial[2k+1].
 template <typename real>
-__global__ void k_boundary_tally(const int32_t* bcells, int64_t nb, const uint32_t* rowptr, const int4* side,
-                                 const d4* side64, const real* I, int64_t N, int G, int nd, const double* om64,
-                                 const double* w64, const double* bc, double* partial) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(ROW_THREADS) k_boundary_tally(const int32_t* bcells, const uint32_t* rowptr,
+                                                                const int4* side, const d4* side64, const real* I,
+                                                                int64_t N, int G, int nd, const double* om64,
+                                                                const double* w64, const double* bc,
+                                                                double* partial) {
+    __shared__ double sh[ROW_THREADS / 32];
+    const int64_t k = blockIdx.x;
+    const int32_t c = bcells[k];
+    const uint32_t r0 = rowptr[c], r1 = rowptr[c + 1];
     double esc = 0.0, inj = 0.0;
-    if (k < nb) {
-        int32_t c = bcells[k];
-        for (int d = 0; d < nd; ++d) {
-            for (uint32_t s = rowptr[c]; s < rowptr[c + 1]; ++s) {
-                int32_t nbr = side[s].x;
-                if (nbr >= 0) continue;
-                d4 n = side64[s];
-                double t = exact_t(n, om64 + 3 * d);
-                double a = dmul(n.w, fabs(t));
-                double wa = dmul(w64[d], a);
-                for (int g = 0; g < G; ++g) {
-                    if (t > 0.0) esc = dadd(esc, dmul(wa, mag(I + ((size_t)d * N + c) * G + g)));
-                    else if (t < 0.0 && bc) inj = dadd(inj, dmul(wa, bc[(size_t)(-1 - nbr) * G + g]));
-                }
+    for (int d = threadIdx.x; d < nd; d += ROW_THREADS) {
+        const double w = w64[d];
+        for (uint32_t s = r0; s < r1; ++s) {
+            const int32_t nbr = side[s].x;
+            if (nbr >= 0) continue;
+            const d4 n = side64[s];
+            const double t = exact_t(n, om64 + 3 * d);
+            const double wa = dmul(w, dmul(n.w, fabs(t)));
+            for (int g = 0; g < G; ++g) {
+                if (t > 0.0) esc = dadd(esc, dmul(wa, mag(I + ((size_t)d * N + c) * G + g)));
+                else if (t < 0.0 && bc) inj = dadd(inj, dmul(wa, bc[(size_t)(-1 - nbr) * G + g]));
             }
         }
     }
-    block_sum2(esc, inj, partial);
+    esc = block_sum_fixed(esc, sh);
+    inj = block_sum_fixed(inj, sh);
+    if (threadIdx.x == 0) {
+        partial[2 * k] = esc;
+        partial[2 * k + 1] = inj;
+    }
+}
+
+// Periodic iteration (Sec. 2.7): the inflow j^n of one periodic cell and group, summed over the
+// directions and its periodic sides of the partner cells' intensities, and the relative change
+// E = |j^n - j^(n-1)| / (j^n + j^(n-1)) (Eq. relativeErrorPbc). Writes jn1, raises *dmax to the
+// cell's largest E, and puts the sum of its E over groups into partial[2k].
+template <typename real>
+__global__ void __launch_bounds__(ROW_THREADS) k_periodic_source(const int32_t* pcells, const uint32_t* rowptr,
+                                                                 const int4* side, const d4* side64, const real* I,
+                                                                 int64_t N, int G, int nd, const double* om64,
+                                                                 const double* w64, double* jn1, const double* jn,
+                                                                 unsigned long long* dmax, double* partial) {
+    __shared__ double sh[ROW_THREADS / 32];
+    const int64_t k = blockIdx.x;
+    const int32_t c = pcells[k];
+    const uint32_t r0 = rowptr[c], r1 = rowptr[c + 1];
+    double j[8];
+    for (int g = 0; g < 8; ++g) j[g] = 0.0;
+    for (int d = threadIdx.x; d < nd; d += ROW_THREADS) {
+        const double w = w64[d];
+        for (uint32_t s = r0; s < r1; ++s) {
+            const int32_t nbr = side[s].x;
+            if (nbr < 0 || !(nbr & NBR_PERIODIC)) continue;
+            const d4 n = side64[s];
+            const double t = exact_t(n, om64 + 3 * d);
+            if (!(t < 0.0)) continue;
+            const double wa = dmul(w, dmul(n.w, fabs(t)));
+            const size_t base = ((size_t)d * N + (uint32_t)(nbr & NBR_MASK)) * G;
+            for (int g = 0; g < G; ++g) j[g] = dadd(j[g], dmul(wa, mag(I + base + g)));
+        }
+    }
+    double esum = 0.0, emax = 0.0;
+    for (int g = 0; g < G; ++g) {
+        const double jt = block_sum_fixed(j[g], sh);
+        if (threadIdx.x == 0) {
+            const size_t i = (size_t)c * G + g;
+            const double s = jt + jn[i];
+            const double e = s > 0.0 ? fabs(jt - jn[i]) / s : 0.0;
+            jn1[i] = jt;
+            esum += e;
+            if (e > emax) emax = e;
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (emax > 0.0) atomicMax(dmax, (unsigned long long)__double_as_longlong(emax));
+        partial[2 * k] = esum;
+        partial[2 * k + 1] = 0.0;
+    }
 }
 
 __global__ void k_scat_residual(int64_t NG, const double* J, double* Jold, unsigned long long* dmax) {
@@ -133,43 +206,6 @@ __global__ void k_scat_residual(int64_t NG, const double* J, double* Jold, unsig
     else e = INFINITY;
     Jold[i] = J[i];
     if (e > 0.0) atomicMax(dmax, (unsigned long long)__double_as_longlong(e));
-}
-
-template <typename real>
-__global__ void k_periodic_source(const int32_t* pcells, int64_t np, const uint32_t* rowptr, const int4* side,
-                                  const d4* side64, const real* I, int64_t N, int G, int nd, const double* om64,
-                                  const double* w64, double* jn1, const double* jn, unsigned long long* dmax,
-                                  double* partial) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double esum = 0.0;
-    if (k < np) {
-        int32_t c = pcells[k];
-        double j[8];
-        for (int g = 0; g < G; ++g) j[g] = 0.0;
-        for (int d = 0; d < nd; ++d) {
-            for (uint32_t s = rowptr[c]; s < rowptr[c + 1]; ++s) {
-                int32_t nbr = side[s].x;
-                if (nbr < 0 || !(nbr & NBR_PERIODIC)) continue;
-                d4 n = side64[s];
-                double t = exact_t(n, om64 + 3 * d);
-                if (!(t < 0.0)) continue;
-                double wa = dmul(w64[d], dmul(n.w, fabs(t)));
-                int32_t up = nbr & NBR_MASK;
-                for (int g = 0; g < G; ++g) j[g] = dadd(j[g], dmul(wa, mag(I + ((size_t)d * N + up) * G + g)));
-            }
-        }
-        double emax = 0.0;
-        for (int g = 0; g < G; ++g) {
-            size_t i = (size_t)c * G + g;
-            double s = j[g] + jn[i];
-            double e = s > 0.0 ? fabs(j[g] - jn[i]) / s : 0.0;
-            jn1[i] = j[g];
-            esum += e;
-            if (e > emax) emax = e;
-        }
-        if (emax > 0.0) atomicMax(dmax, (unsigned long long)__double_as_longlong(emax));
-    }
-    block_sum2(esum, 0.0, partial);
 }
 
 __global__ void k_reduce_sum(const double* partial, int n, double* out) {
@@ -262,14 +298,14 @@ cudaError_t launch_boundary_tally(int precision, const DevMesh& m, const void* I
                                   const double* om64, const double* w64, const double* bc, double* partial, int nblk_,
                                   cudaStream_t st) {
     (void)nblk_;
-    unsigned b = nb(m.n_bcells > 0 ? m.n_bcells : 1);
+    if (m.n_bcells <= 0) return cudaSuccess;
+    const unsigned b = (unsigned)m.n_bcells;
     if (precision == 64)
-        k_boundary_tally<double><<<b, 256, 0, st>>>(m.bcells, m.n_bcells, m.rowptr, m.side, m.side64,
-                                                    (const double*)I, m.N, G, nd, om64 + 3 * d0, w64 + d0, bc,
-                                                    partial);
+        k_boundary_tally<double><<<b, ROW_THREADS, 0, st>>>(m.bcells, m.rowptr, m.side, m.side64, (const double*)I,
+                                                            m.N, G, nd, om64 + 3 * d0, w64 + d0, bc, partial);
     else
-        k_boundary_tally<float><<<b, 256, 0, st>>>(m.bcells, m.n_bcells, m.rowptr, m.side, m.side64,
-                                                   (const float*)I, m.N, G, nd, om64 + 3 * d0, w64 + d0, bc, partial);
+        k_boundary_tally<float><<<b, ROW_THREADS, 0, st>>>(m.bcells, m.rowptr, m.side, m.side64, (const float*)I,
+                                                           m.N, G, nd, om64 + 3 * d0, w64 + d0, bc, partial);
     return cudaGetLastError();
 }
 
@@ -283,14 +319,14 @@ cudaError_t launch_periodic_source(int precision, const DevMesh& m, const void* 
                                    const double* w64, double* jn1, const double* jn, unsigned long long* d_max,
                                    double* partial, int nblk_, cudaStream_t st) {
     (void)nblk_;
-    unsigned b = nb(m.n_pcells > 0 ? m.n_pcells : 1);
+    if (m.n_pcells <= 0) return cudaSuccess;
+    const unsigned b = (unsigned)m.n_pcells;
     if (precision == 64)
-        k_periodic_source<double><<<b, 256, 0, st>>>(m.pcells, m.n_pcells, m.rowptr, m.side, m.side64,
-                                                     (const double*)I, m.N, G, nd, om64, w64, jn1, jn, d_max,
-                                                     partial);
+        k_periodic_source<double><<<b, ROW_THREADS, 0, st>>>(m.pcells, m.rowptr, m.side, m.side64, (const double*)I,
+                                                             m.N, G, nd, om64, w64, jn1, jn, d_max, partial);
     else
-        k_periodic_source<float><<<b, 256, 0, st>>>(m.pcells, m.n_pcells, m.rowptr, m.side, m.side64,
-                                                    (const float*)I, m.N, G, nd, om64, w64, jn1, jn, d_max, partial);
+        k_periodic_source<float><<<b, ROW_THREADS, 0, st>>>(m.pcells, m.rowptr, m.side, m.side64, (const float*)I,
+                                                            m.N, G, nd, om64, w64, jn1, jn, d_max, partial);
     return cudaGetLastError();
 }
 

@@ -135,6 +135,22 @@ def test_column_closed_form(ctx, precision, reverse):
     assert np.max(np.abs(I - exact) / exact) <= (1e-13 if precision == 64 else 2e-5)
 
 
+def test_column_deeper_than_the_level_tables(ctx):
+    # 70000 levels of one cell: more than the direction-parallel levelisation's 65536-level tables, so the
+    # level-synchronous form takes over; levels and the closed form must come out the same
+    n, kap = 70000, 3.2
+    h = 1.0 / n
+    p = configs.column(n, kappa=kap, h=h)
+    load(ctx, p)
+    lev, depth = ctx.levels(0)
+    assert depth == n and np.array_equal(lev, np.arange(n))
+    ctx.solve(precision=64, schedule="dataflow")
+    I = ctx.intensity(0)[:, 0]
+    k = np.arange(n)
+    exact = np.exp(-(k + 1.0) * np.log1p(kap * h))
+    assert np.max(np.abs(I - exact) / exact) <= 1e-11
+
+
 # ---- iterations: scattering (Alg. 1) and periodic boundaries (Sec. 2.7) -------------------------------
 @pytest.mark.parametrize("precision", [32, 64])
 def test_scattering_iteration(ctx, precision):
