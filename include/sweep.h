@@ -78,7 +78,7 @@ typedef struct {
     int64_t spin_budget;  /* bound on each device-side wait, in polls (0 = default, about 1 s) */
     int32_t debug_stall;  /* TEST ONLY: 1 makes the first sweep task wait on a word nothing writes */
     int32_t lanes_per_task; /* lanes cooperating on one task in the batched sweep: 1..16, a power of 2 (0 = autotuned);
-                               with the assembled operator, 1 = one task per thread with TMA-staged rows */
+                               over the assembled operator 2, 4 or 8 (1 runs as 2, 16 as 8) */
     int32_t geometry_only;  /* 1: the FP32 sweep reads the mesh every sweep instead of the assembled operator */
     int32_t blocks_per_sm;  /* resident blocks per SM of the batched sweep (0 = autotuned / maximum) */
 } sweep_opts;
@@ -112,8 +112,7 @@ enum {
     SWEEP_KERNEL_GEOMETRY = 2,       /* lane groups reading the mesh rows (FP64, and every adjoint sweep) */
     SWEEP_KERNEL_RECORDS = 3,        /* FP32 forward, lane groups over task records and mesh rows */
     SWEEP_KERNEL_OPERATOR = 4,       /* FP32 forward over the assembled operator, lane groups */
-    SWEEP_KERNEL_OPERATOR_LEAN = 5,  /* the same, one group and 8 lanes per task, dataflow schedule */
-    SWEEP_KERNEL_OPERATOR_TMA = 6    /* FP32 forward over the assembled operator, one task per thread, bulk copies */
+    SWEEP_KERNEL_OPERATOR_LEAN = 5   /* the same, one group and 8 lanes per task, dataflow schedule */
 };
 
 /* Fill *opts with defaults: precision 32, AUTO schedule, tolerances 1e-6, 100 iterations. */

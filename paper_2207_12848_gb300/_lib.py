@@ -24,7 +24,7 @@ SWEEP_FACE_PERIODIC = 2
 SWEEP_SCHED_AUTO, SWEEP_SCHED_LEVEL, SWEEP_SCHED_DATAFLOW, SWEEP_SCHED_PLAIN = 0, 1, 2, 3
 SCHEDULES = {"auto": 0, "level": 1, "dataflow": 2, "plain": 3}
 # forms of the batched sweep kernel (sweep_stats.kernel_used)
-KERNELS = {0: "none", 1: "k_plain", 2: "k_sweep", 3: "k_sweep_rec", 4: "k_sweep_op", 5: "k_sweep_op1", 6: "k_sweep_tma"}
+KERNELS = {0: "none", 1: "k_plain", 2: "k_sweep", 3: "k_sweep_rec", 4: "k_sweep_op", 5: "k_sweep_op1"}
 
 # every entry point include/sweep.h declares
 EXPORTS = ("sweep_default_opts", "sweep_create", "sweep_destroy", "sweep_set_mesh", "sweep_set_directions",

@@ -242,7 +242,6 @@ struct SweepArgs {
     const uint32_t* task;
     const int4* trec;     // task records (FP32 forward sweep)
     const int4* op;       // assembled operator headers (one int4 per task), or null (FP32 forward sweep)
-    const int2* op_ent;   // assembled operator entries (OP_MAX int2 per task)
     int64_t n_chunks;
     const int64_t* lev_chunk;
     int n_levels;

@@ -744,32 +744,57 @@ __global__ void k_gather_levels(const uint32_t* dlist, const int32_t* dcnt, cons
     }
 }
 
-// Assembled transport operator, 128 bytes per task in sweep order, as two arrays:
-//   hdr[t]          int4 {task entry, P_c (FP32 bits), number of inflow sides n (> OP_MAX: entries incomplete), 0}
-//   ent[t][0..13]   int2 {neighbour code, FP32 weight |A_f n_f.Omega|} of each inflow side, in row order
-// This is row c of the lower-triangular system L_Omega I = q (Sec. 2.3), its diagonal P_c plus
-// kappa_t V_c completed from the material at sweep time.
+// Assembled transport operator: one 128-byte line per task, in sweep order (row t of the
+// lower-triangular system L_Omega I = q of Sec. 2.3, its diagonal P_c plus kappa_t V_c completed
+// from the material at sweep time):
+//   int4 header  {task entry, P_c (FP32 bits), n_in | boundary-entry mask << 16, destination}
+//                n_in = inflow sides (capped at 255; > OP_MAX: the line is incomplete and the task
+//                takes the geometry path); destination = element index dl*N + c of the intensity
+//   int2 entry[OP_MAX] {source index, FP32 weight |A_f n_f.Omega|}, inflow sides in row order:
+//                interior upwind cell: index dl*N + nb into this sweep's intensities, weight >= +0;
+//                periodic partner: index dl*N + partner into the previous iteration's intensities,
+//                weight with its sign bit set; boundary face b: index b into the boundary inflow,
+//                weight with its sign bit set and the entry's bit set in the boundary mask.
+//                Unused entries are {0, 0}.
 __global__ void k_build_op(const int4* trec, int64_t n, const uint32_t* rowptr, const int4* side, const d4* side64,
                            const float4* side_lo, const float4* om32, const float4* om32lo, const double* om64,
-                           uint32_t cmask, int cshift, int4* hdr, int2* ent) {
+                           uint32_t cmask, int cshift, uint32_t N, int4* op) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int4 tr = trec[i];
+    int4* line = op + i * 8;
+    int2* E = reinterpret_cast<int2*>(line + 1);
     if ((uint32_t)tr.x == TASK_PAD) {
-        hdr[i] = make_int4((int)TASK_PAD, 0, 0, 0);
+        line[0] = make_int4((int)TASK_PAD, 0, 0, 0);
+        for (int j = 0; j < OP_MAX; ++j) E[j] = make_int2(0, 0);
         return;
     }
     const uint32_t c = (uint32_t)tr.x & cmask, dl = (uint32_t)tr.x >> cshift;
+    const uint32_t slab = dl * N;
     const uint32_t r0 = (uint32_t)tr.y;
     const float4 om = om32[dl], oml = om32lo[dl];
     const double* o64 = om64 + 3 * dl;
-    int2* E = ent + i * OP_MAX;
     int nin = 0;
+    uint32_t bmask = 0;
+    auto put = [&](const int4& r, uint32_t s) {
+        if (nin < OP_MAX) {
+            const float w = side_weight(r, side_lo[s], om, oml);
+            int2 v;
+            if (r.x >= 0 && !(r.x & NBR_PERIODIC)) {
+                v = make_int2((int)(slab + (uint32_t)r.x), __float_as_int(w));
+            } else if (r.x >= 0) {
+                v = make_int2((int)(slab + (uint32_t)(r.x & NBR_MASK)), __float_as_int(-w));
+            } else {
+                v = make_int2(-1 - r.x, __float_as_int(-w));
+                bmask |= 1u << nin;
+            }
+            E[nin] = v;
+        }
+        ++nin;
+    };
     for (uint32_t m = (uint32_t)tr.w; m; m &= m - 1) {
         const uint32_t s = r0 + (uint32_t)(__ffs(m) - 1);
-        const int4 r = side[s];
-        if (nin < OP_MAX) E[nin] = make_int2(r.x, __float_as_int(side_weight(r, side_lo[s], om, oml)));
-        ++nin;
+        put(side[s], s);
     }
     if (tr.z < 0) {  // rows longer than 32 sides
         const uint32_t r1 = rowptr[c + 1];
@@ -777,11 +802,11 @@ __global__ void k_build_op(const int4* trec, int64_t n, const uint32_t* rowptr, 
             const int4 r = side[s];
             const float ax = __int_as_float(r.y), ay = __int_as_float(r.z), az = __int_as_float(r.w);
             if (classify_side(dot32(ax, ay, az, om), ax, ay, az, side64, s, o64) >= 0) continue;
-            if (nin < OP_MAX) E[nin] = make_int2(r.x, __float_as_int(side_weight(r, side_lo[s], om, oml)));
-            ++nin;
+            put(r, s);
         }
     }
-    hdr[i] = make_int4(tr.x, tr.z & 0x7fffffff, nin, 0);  // nin > OP_MAX: entries incomplete
+    for (int j = nin; j < OP_MAX; ++j) E[j] = make_int2(0, 0);
+    line[0] = make_int4(tr.x, tr.z & 0x7fffffff, (nin < 255 ? nin : 255) | (int)(bmask << 16), (int)(slab + c));
 }
 
 }  // namespace
@@ -791,8 +816,8 @@ cudaError_t build_operator(const DevMesh& m, const Levels& L, const double* om64
     const int64_t n = L.h_lev_chunk.empty() ? 0 : L.h_lev_chunk.back() * 32;
     if (n > 0)
         k_build_op<<<nblk(n), 256, 0, st>>>(L.trec, n, m.rowptr, m.side, m.side64, m.side_lo, om32_all + L.d0,
-                                            om32lo_all + L.d0, om64_all + 3 * (int64_t)L.d0, L.cmask, L.cshift, L.op,
-                                            reinterpret_cast<int2*>(L.op + n));
+                                            om32lo_all + L.d0, om64_all + 3 * (int64_t)L.d0, L.cmask, L.cshift,
+                                            (uint32_t)m.N, L.op);
     return cudaGetLastError();
 }
 

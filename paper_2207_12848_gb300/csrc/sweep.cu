@@ -523,10 +523,11 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// FP32 forward sweep over the assembled operator. LP lanes share a task's 128-byte line: lane j
-// loads pieces [j*PL, (j+1)*PL) (PL = 8/LP pieces of 16 bytes; piece 0 is the header, piece p >= 1
-// holds inflow entries 2p-2 and 2p-1). One coalesced load brings the whole row of L_Omega; the
-// upwind values are gathered, reduced over the LP lanes, and lane 0 solves the cell.
+// FP32 forward sweep over the assembled operator (one 128-byte line per task, see k_build_op). LP
+// lanes share a task's line: lane j holds pieces [j*PL, (j+1)*PL) (PL = 8/LP pieces of 16 bytes;
+// piece 0 is the header, piece p >= 1 holds entries 2p-2 and 2p-1), so one coalesced load brings
+// the whole row of L_Omega; the upwind values are gathered, reduced over the LP lanes, and lane 0
+// solves the cell.
 // ---------------------------------------------------------------------------------------------
 template <int LP>
 struct OpPieces {
@@ -539,6 +540,37 @@ __device__ __noinline__ bool op_overflow(const SweepArgs& a, int4 tr, const floa
     return rec_task<GC, LP>(a, tr, s_om, gl, false, policy_evict_first());
 }
 
+// an upwind value not yet written by this sweep: bounded wait (out of line, rare)
+__device__ __noinline__ float op_wait(const SweepArgs& a, const float* p, bool& fail) {
+    float x = 0.f;
+    if (fail || !wait_value_slow(p, a.parity, a, x)) {
+        fail = true;
+        return 0.f;
+    }
+    return x;
+}
+
+// inflow through a periodic face (previous iteration's partner intensity) or a boundary face
+template <int GC>
+__device__ __forceinline__ void op_external(const SweepArgs& a, uint32_t idx, float w, bool boundary, int G,
+                                            float* acc) {
+    constexpr int GM = GC > 0 ? GC : 8;
+    const float aw = -w;  // external entries carry the weight with its sign bit set
+    if (boundary) {
+        if (a.bc) {
+            const float* b = reinterpret_cast<const float*>(a.bc) + (size_t)idx * G;
+#pragma unroll
+            for (int g = 0; g < GM; ++g)
+                if (g < G) acc[g] = fmaf(aw, b[g], acc[g]);
+        }
+    } else if (a.Iprev) {
+        const float* src = reinterpret_cast<const float*>(a.Iprev) + (size_t)idx * G;
+#pragma unroll
+        for (int g = 0; g < GM; ++g)
+            if (g < G) acc[g] = fmaf(aw, fabsf(src[g]), acc[g]);
+    }
+}
+
 template <int GC, int LP>
 __device__ __forceinline__ bool op_task(const SweepArgs& a, const OpPieces<LP>& mine, int gl, bool stall,
                                         bool& overflow) {
@@ -549,11 +581,13 @@ __device__ __forceinline__ bool op_task(const SweepArgs& a, const OpPieces<LP>& 
     const int4 h = mine.p[0];
     const uint32_t e = (uint32_t)__shfl_sync(0xffffffffu, h.x, lead);
     const float P = __int_as_float(__shfl_sync(0xffffffffu, h.y, lead));
-    const int nin = __shfl_sync(0xffffffffu, h.z, lead);
+    const int nz = __shfl_sync(0xffffffffu, h.z, lead);
+    const uint32_t dst = (uint32_t)__shfl_sync(0xffffffffu, h.w, lead);
+    const int nin = nz & 0xff;
     const bool valid = e != TASK_PAD;
     overflow = valid && nin > OP_MAX;
     const uint32_t c = valid ? (e & a.cmask) : 0u;
-    const uint32_t dl = valid ? (e >> a.cshift) : 0u;
+    const uint32_t par = a.parity ? 0x80000000u : 0u;
     float2 q[GM];
     if (valid && gl == 0 && !overflow) {
         const float2* cm = reinterpret_cast<const float2*>(a.cm) + (size_t)c * G;
@@ -561,7 +595,6 @@ __device__ __forceinline__ bool op_task(const SweepArgs& a, const OpPieces<LP>& 
         for (int g = 0; g < GM; ++g)
             if (g < G) q[g] = cm[g];
     }
-    const size_t slab = (size_t)dl * a.N;
     bool fail = false;
     if (stall && gl == 0) {
         float dummy;
@@ -572,34 +605,50 @@ __device__ __forceinline__ bool op_task(const SweepArgs& a, const OpPieces<LP>& 
     for (int g = 0; g < GM; ++g) acc[g] = 0.f;
     if (valid && !overflow) {
         constexpr int NE = 2 * PL;  // entry slots this lane holds
-        int32_t nb[NE];
+        uint32_t idx[NE];
         float w[NE];
         bool has[NE];
+        int j[NE];
 #pragma unroll
         for (int k = 0; k < PL; ++k) {
             const int piece = gl * PL + k;
             const int4 q4 = mine.p[k];
-            const int i0 = 2 * piece - 2;
-            has[2 * k] = piece > 0 && i0 < nin;
-            has[2 * k + 1] = piece > 0 && i0 + 1 < nin;
-            nb[2 * k] = q4.x;
+            j[2 * k] = 2 * piece - 2;
+            j[2 * k + 1] = 2 * piece - 1;
+            has[2 * k] = piece > 0 && j[2 * k] < nin;
+            has[2 * k + 1] = piece > 0 && j[2 * k + 1] < nin;
+            idx[2 * k] = (uint32_t)q4.x;
             w[2 * k] = __int_as_float(q4.y);
-            nb[2 * k + 1] = q4.z;
+            idx[2 * k + 1] = (uint32_t)q4.z;
             w[2 * k + 1] = __int_as_float(q4.w);
         }
         float v[NE][GM];
         const float* I = reinterpret_cast<const float*>(a.I);
 #pragma unroll
         for (int k = 0; k < NE; ++k) {  // issue every upwind read before using any
-            if (has[k] && nb[k] >= 0 && !(nb[k] & NBR_PERIODIC)) {
+            if (has[k] && !sign_bit(w[k])) {
 #pragma unroll
                 for (int g = 0; g < GM; ++g)
-                    if (g < G) v[k][g] = ld_relaxed(I + (slab + (uint32_t)nb[k]) * G + g);
+                    if (g < G) v[k][g] = ld_relaxed(I + (size_t)idx[k] * G + g);
             }
         }
 #pragma unroll
-        for (int k = 0; k < NE; ++k)
-            if (has[k]) add_inflow<GC>(a, nb[k], w[k], v[k], slab, G, acc, fail);
+        for (int k = 0; k < NE; ++k) {
+            if (!has[k]) continue;
+            if (sign_bit(w[k])) {
+                op_external<GC>(a, idx[k], w[k], (nz >> (16 + j[k])) & 1, G, acc);
+                continue;
+            }
+#pragma unroll
+            for (int g = 0; g < GM; ++g) {
+                if (g < G) {
+                    const uint32_t u = __float_as_uint(v[k][g]);
+                    const float x = (u & 0x80000000u) == par ? __uint_as_float(u ^ par)
+                                                             : op_wait(a, I + (size_t)idx[k] * G + g, fail);
+                    acc[g] = fmaf(w[k], x, acc[g]);
+                }
+            }
+        }
     }
 #pragma unroll
     for (int off = LP / 2; off > 0; off >>= 1) {
@@ -608,12 +657,12 @@ __device__ __forceinline__ bool op_task(const SweepArgs& a, const OpPieces<LP>& 
             if (g < G) acc[g] += __shfl_xor_sync(0xffffffffu, acc[g], off);
     }
     if (valid && !overflow && gl == 0 && !fail) {
-        float* dst = reinterpret_cast<float*>(a.I) + (slab + c) * G;
+        float* out = reinterpret_cast<float*>(a.I) + (size_t)dst * G;
 #pragma unroll
         for (int g = 0; g < GM; ++g) {
             if (g < G) {
                 const float val = __fdividef(q[g].x + acc[g], P + q[g].y);
-                st_relaxed(dst + g, a.parity ? -val : val);
+                st_relaxed(out + g, __uint_as_float(__float_as_uint(val) ^ par));
             }
         }
     }
@@ -630,23 +679,15 @@ __device__ __forceinline__ bool run_chunks_op(const SweepArgs& a, ChunkFn chunk,
     auto pieces_of = [&](int64_t i) {
         OpPieces<LP> r;
         const int64_t k = chunk(i);
-        const int64_t t = k * CS + grp;
+        const int4* src = a.op + (k * CS + grp) * 8 + gl * PL;
 #pragma unroll
-        for (int j = 0; j < PL; ++j) {
-            const int piece = gl * PL + j;
-            const int4* src = piece == 0 ? a.op + t : reinterpret_cast<const int4*>(a.op_ent + t * OP_MAX) + (piece - 1);
-            r.p[j] = k >= 0 ? ld_stream_int4(src, pol) : make_int4((int)TASK_PAD, 0, 0, 0);
-        }
+        for (int j = 0; j < PL; ++j) r.p[j] = k >= 0 ? ld_stream_int4(src + j, pol) : make_int4((int)TASK_PAD, 0, 0, 0);
         return r;
     };
     auto prefetch_chunk = [&](int64_t i) {
         const int64_t k = chunk(i);
         if (k >= 0 && (threadIdx.x & 31) == 0)
-        {
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.op + k * CS), "r"(CS * 16u));
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.op_ent + k * CS * OP_MAX),
-                         "r"(CS * OP_MAX * 8u));
-        }
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.op + k * CS * 8), "r"(CS * 128u));
     };
     OpPieces<LP> T[PF];
 #pragma unroll
@@ -705,24 +746,13 @@ __global__ void __launch_bounds__(256, SWEEP_REC_MINB) k_sweep_op(SweepArgs a) {
     }
 }
 
-// Lean form for one frequency group and 8 lanes per task (dataflow schedule): the common case of
-// an interior upwind value already written by this sweep stays inline; waits, periodic and
-// boundary inflow go through one out-of-line helper.
-__device__ __noinline__ float op1_slow(const SweepArgs& a, int32_t nb, float w, const float* islab, size_t slab,
-                                       bool& fail) {
-    if (nb >= 0 && !(nb & NBR_PERIODIC)) {
-        float x;
-        if (fail || !wait_value_slow(islab + (uint32_t)nb, a.parity, a, x)) {
-            fail = true;
-            return 0.f;
-        }
-        return w * x;
-    }
-    if (nb >= 0)
-        return a.Iprev ? w * fabsf(reinterpret_cast<const float*>(a.Iprev)[slab + (uint32_t)(nb & NBR_MASK)]) : 0.f;
-    return a.bc ? w * reinterpret_cast<const float*>(a.bc)[-1 - nb] : 0.f;
-}
-
+// Lean form for one frequency group and 8 lanes per task (dataflow schedule). A warp takes 4 tasks
+// (512 contiguous bytes of operator lines) per step, the lines of the next two steps in flight in
+// registers and those of the three after in L2 (bulk prefetch). Lane 0 of a task holds its header,
+// lanes 1..7 two entries each. The common case -- an interior upwind value already written by this
+// sweep -- is a load, a sign test and an FMA; periodic and boundary inflow stay inline; only a wait
+// for a value not yet written goes out of line. A failed wait sets the device error word, which the
+// loop checks every 16 steps.
 __global__ void __launch_bounds__(256, SWEEP_REC_MINB) k_sweep_op1(SweepArgs a) {
     extern __shared__ float4 s_om[];
     for (int i = threadIdx.x; i < a.nd; i += blockDim.x) s_om[i] = a.om32[i];
@@ -731,285 +761,78 @@ __global__ void __launch_bounds__(256, SWEEP_REC_MINB) k_sweep_op1(SweepArgs a) 
     const int grp = lane >> 3, gl = lane & 7, lead = lane & ~7;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t nchunks = a.n_chunks * 8;  // chunks of 4 tasks
+    const int64_t nchunks = a.n_chunks * 8;  // steps of 4 tasks
     const uint64_t pol = policy_evict_first();
     const float* I = reinterpret_cast<const float*>(a.I);
     const float2* cm = reinterpret_cast<const float2*>(a.cm);
     const uint32_t par = a.parity ? 0x80000000u : 0u;
     const int4 pad = make_int4((int)TASK_PAD, 0, 0, 0);
-    // this lane's piece of task grp of chunk 0: the header (lane 0 of the group) or two entries
-    const int4* mine = gl == 0 ? a.op + grp : reinterpret_cast<const int4*>(a.op_ent + grp * OP_MAX) + (gl - 1);
-    const int64_t stride = gl == 0 ? 4 : 4 * OP_MAX / 2;  // int4 per chunk of 4 tasks
-    auto piece = [&](int64_t k) { return k < nchunks ? ld_stream_int4(mine + k * stride, pol) : pad; };
+    const int4* src = a.op + warp * 32 + lane;  // this lane's 16 bytes of step k: src + (k - warp) * 32
+    const int64_t stride = nwarps * 32;
     int64_t k = warp;
-    int4 cur = piece(k), nxt = piece(k + nwarps);
-    if (lane == 0) {
+    int4 cur = k < nchunks ? ld_stream_int4(src, pol) : pad;
+    int4 nxt = k + nwarps < nchunks ? ld_stream_int4(src + stride, pol) : pad;
+    if (lane == 0)
         for (int j = 2; j <= 4; ++j)
             if (k + j * nwarps < nchunks)
-            {
-                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.op + (k + j * nwarps) * 4), "r"(64u));
-                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.op_ent + (k + j * nwarps) * 4 * OP_MAX),
-                             "r"(4u * OP_MAX * 8u));
-            }
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.op + (k + j * nwarps) * 32),
+                             "r"(512u));
+    if (a.debug_stall && warp == 0 && lane == 0) {  // test hook: a wait on a word that nothing writes
+        float dummy;
+        wait_value(reinterpret_cast<const float*>(a.stall_word), 1, a, dummy);
     }
     for (int64_t i = 0; k < nchunks; ++i, k += nwarps) {
         if ((i & 15) == 0 && __any_sync(0xffffffffu, ld_volatile_i32(a.err) != DEV_OK)) return;
-        const int4 nn = piece(k + 2 * nwarps);
+        src += stride;
+        const int4 nn = k + 2 * nwarps < nchunks ? ld_stream_int4(src + stride, pol) : pad;
         if (lane == 0 && k + 5 * nwarps < nchunks)
-        {
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.op + (k + 5 * nwarps) * 4), "r"(64u));
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.op_ent + (k + 5 * nwarps) * 4 * OP_MAX),
-                         "r"(4u * OP_MAX * 8u));
-        }
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.op + (k + 5 * nwarps) * 32), "r"(512u));
         const uint32_t e = (uint32_t)__shfl_sync(0xffffffffu, cur.x, lead);
-        const float P = __int_as_float(__shfl_sync(0xffffffffu, cur.y, lead));
-        const int nin = __shfl_sync(0xffffffffu, cur.z, lead);
+        const int nz = __shfl_sync(0xffffffffu, cur.z, lead);
+        const int nin = nz & 0xff;
         const bool valid = e != TASK_PAD;
         const bool over = valid && nin > OP_MAX;
-        const uint32_t c = e & a.cmask, dl = e >> a.cshift;
-        const size_t slab = (size_t)dl * a.N;
-        const float* islab = I + slab;
-        float2 q = make_float2(0.f, 1.f);
-        if (valid && !over && gl == 0) q = cm[c];
+        const bool work = valid && !over;
         bool fail = false;
-        if (a.debug_stall && i == 0 && warp == 0 && lane == 0) {
-            float dummy;
-            if (!wait_value(reinterpret_cast<const float*>(a.stall_word), 1, a, dummy)) fail = true;
-        }
         float acc = 0.f;
-        if (valid && !over && gl > 0) {
-            const int i0 = 2 * gl - 2;
-            const bool h0 = i0 < nin, h1 = i0 + 1 < nin;
-            const bool in0 = h0 && cur.x >= 0 && !(cur.x & NBR_PERIODIC);
-            const bool in1 = h1 && cur.z >= 0 && !(cur.z & NBR_PERIODIC);
-            const float x0 = in0 ? ld_relaxed(islab + (uint32_t)cur.x) : 0.f;
-            const float x1 = in1 ? ld_relaxed(islab + (uint32_t)cur.z) : 0.f;
+        float2 q = make_float2(0.f, 1.f);
+        if (gl == 0) {
+            if (work) q = cm[e & a.cmask];
+        } else if (work) {
+            const int j0 = 2 * gl - 2;
+            const bool h0 = j0 < nin, h1 = j0 + 1 < nin;
+            const bool in0 = h0 && cur.y >= 0, in1 = h1 && cur.w >= 0;  // sign bit clear: interior entry
+            const float x0 = in0 ? ld_relaxed(I + (uint32_t)cur.x) : 0.f;
+            const float x1 = in1 ? ld_relaxed(I + (uint32_t)cur.z) : 0.f;
             const float w0 = __int_as_float(cur.y), w1 = __int_as_float(cur.w);
-            if (in0 && (__float_as_uint(x0) & 0x80000000u) == par) acc = w0 * __uint_as_float(__float_as_uint(x0) ^ par);
-            else if (h0) acc = op1_slow(a, cur.x, w0, islab, slab, fail);
-            if (in1 && (__float_as_uint(x1) & 0x80000000u) == par)
-                acc = fmaf(w1, __uint_as_float(__float_as_uint(x1) ^ par), acc);
-            else if (h1) acc += op1_slow(a, cur.z, w1, islab, slab, fail);
+            if (in0) {
+                const uint32_t u = __float_as_uint(x0);
+                acc = w0 * ((u & 0x80000000u) == par ? __uint_as_float(u ^ par) : op_wait(a, I + (uint32_t)cur.x, fail));
+            } else if (h0) {
+                op_external<1>(a, (uint32_t)cur.x, w0, (nz >> (16 + j0)) & 1, 1, &acc);
+            }
+            if (in1) {
+                const uint32_t u = __float_as_uint(x1);
+                acc = fmaf(w1, (u & 0x80000000u) == par ? __uint_as_float(u ^ par) : op_wait(a, I + (uint32_t)cur.z, fail),
+                           acc);
+            } else if (h1) {
+                op_external<1>(a, (uint32_t)cur.z, w1, (nz >> (17 + j0)) & 1, 1, &acc);
+            }
         }
         acc += __shfl_xor_sync(0xffffffffu, acc, 4);
         acc += __shfl_xor_sync(0xffffffffu, acc, 2);
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-        if (valid && !over && gl == 0 && !fail) {
-            const float val = __fdividef(q.x + acc, P + q.y);
-            st_relaxed(reinterpret_cast<float*>(a.I) + slab + c, __uint_as_float(__float_as_uint(val) ^ par));
+        if (gl == 0 && work && !fail) {
+            const float val = __fdividef(q.x + acc, __int_as_float(cur.y) + q.y);
+            st_relaxed(reinterpret_cast<float*>(a.I) + (uint32_t)cur.w, __uint_as_float(__float_as_uint(val) ^ par));
         }
-        bool good = !fail;
         if (__any_sync(0xffffffffu, over)) {
             const int4 tr = over ? __ldg(a.trec + k * 4 + grp) : pad;
-            good = op_overflow<1, 8>(a, tr, s_om, gl) && good;
+            op_overflow<1, 8>(a, tr, s_om, gl);  // a failed wait inside sets the error word
         }
-        if (__any_sync(0xffffffffu, !good)) return;
         cur = nxt;
         nxt = nn;
     }
-}
-
-// ---------------------------------------------------------------------------------------------
-// FP32 forward sweep over the assembled operator, one task per thread. Each warp owns a ring of
-// TMA_STAGES shared-memory stages; its lane 0 brings a whole 32-task chunk (headers and entries,
-// contiguous in sweep order) with two bulk copies (cp.async.bulk) completing on an mbarrier, so
-// the rows of the coming chunks are on chip before the warp reaches them and take no registers.
-// ---------------------------------------------------------------------------------------------
-constexpr int TMA_STAGES = 3;
-constexpr int TMA_WARPS = 4;  // warps per block
-
-struct TmaStage {
-    int4 hdr[32];
-    int4 ent[32 * OP_MAX / 2];
-};
-static_assert(sizeof(TmaStage) == 512 + 32 * OP_MAX * 8, "stage layout");
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t phase) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(phase)
-        : "memory");
-    return done != 0;
-}
-
-// bounded wait for a stage; false if the wait gave up (the error word is set)
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, const SweepArgs& a) {
-    if (mbar_test(bar, phase)) return true;
-    for (long long n = 0;; ++n) {
-        if (n > a.spin_budget) {
-            atomicCAS(a.err, DEV_OK, DEV_TIMEOUT);
-            return false;
-        }
-        __nanosleep(32);
-        if (mbar_test(bar, phase)) return true;
-    }
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-template <int GC>
-__device__ __noinline__ bool tma_overflow(const SweepArgs& a, int4 tr, const float4* s_om) {
-    return rec_task<GC, 1>(a, tr, s_om, 0, false, policy_evict_first());
-}
-
-template <int GC>
-__device__ __noinline__ void tma_slow(const SweepArgs& a, int32_t nb, float w, size_t slab, int G, float* acc,
-                                      bool& fail) {
-    add_inflow<GC>(a, nb, w, nullptr, slab, G, acc, fail);
-}
-
-template <int GC>
-__global__ void __launch_bounds__(TMA_WARPS * 32) k_sweep_tma(SweepArgs a) {
-    constexpr int GM = GC > 0 ? GC : 8;
-    const int G = GC > 0 ? GC : a.G;
-    extern __shared__ __align__(128) unsigned char smem[];
-    TmaStage* stages = reinterpret_cast<TmaStage*>(smem);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + sizeof(TmaStage) * TMA_WARPS * TMA_STAGES);
-    float4* s_om = reinterpret_cast<float4*>(bars + TMA_WARPS * TMA_STAGES + 2);
-    for (int i = threadIdx.x; i < a.nd; i += blockDim.x) s_om[i] = a.om32[i];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    TmaStage* st = stages + wib * TMA_STAGES;
-    uint64_t* bar = bars + wib * TMA_STAGES;
-    if (lane == 0) {
-        for (int s = 0; s < TMA_STAGES; ++s) mbar_init(bar + s, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    const int64_t warp = (int64_t)blockIdx.x * TMA_WARPS + wib;
-    const int64_t nwarps = (int64_t)gridDim.x * TMA_WARPS;
-    const int64_t nchunks = a.n_chunks;  // 32-task chunks
-    const float2* cm = reinterpret_cast<const float2*>(a.cm);
-    const uint32_t par = a.parity ? 0x80000000u : 0u;
-    auto issue = [&](int64_t i) {  // lane 0: chunk i of this warp into stage i % TMA_STAGES
-        const int64_t k = warp + i * nwarps;
-        if (k >= nchunks) return;
-        const int s = (int)(i % TMA_STAGES);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive_tx(bar + s, (uint32_t)sizeof(TmaStage));
-        bulk_g2s(st[s].hdr, a.op + k * 32, 512u, bar + s);
-        bulk_g2s(st[s].ent, a.op_ent + k * 32 * OP_MAX, 32u * OP_MAX * 8u, bar + s);
-    };
-    if (lane == 0)
-        for (int i = 0; i < TMA_STAGES; ++i) issue(i);
-    int64_t i = 0;
-    bool ok = true;
-    for (; warp + i * nwarps < nchunks; ++i) {
-        const int s = (int)(i % TMA_STAGES);
-        const uint32_t ph = (uint32_t)((i / TMA_STAGES) & 1);
-        if (!mbar_wait(bar + s, ph, a)) { ok = false; break; }
-        const int4 h = st[s].hdr[lane];
-        const uint32_t e = (uint32_t)h.x;
-        const bool valid = e != TASK_PAD;
-        const int nin = valid ? h.z : 0;
-        const bool over = nin > OP_MAX;
-        const int ne = over ? 0 : nin;
-        int4 pc[OP_MAX / 2];
-#pragma unroll
-        for (int j = 0; j < OP_MAX / 2; ++j)
-            pc[j] = (2 * j < ne) ? st[s].ent[lane * (OP_MAX / 2) + j] : make_int4(0, 0, 0, 0);  // 112-byte stride:
-                                                                                       // no bank conflicts
-        __syncwarp();
-        if (lane == 0) issue(i + TMA_STAGES);  // the stage is free again
-        const uint32_t c = e & a.cmask, dl = e >> a.cshift;
-        const size_t slab = (size_t)dl * a.N;
-        const float* islab = reinterpret_cast<const float*>(a.I) + slab * G;
-        float2 q[GM];
-        if (valid && !over) {
-#pragma unroll
-            for (int g = 0; g < GM; ++g)
-                if (g < G) q[g] = cm[(size_t)c * G + g];
-        }
-        bool fail = false;
-        if (a.debug_stall && i == 0 && warp == 0 && lane == 0) {
-            float dummy;
-            if (!wait_value(reinterpret_cast<const float*>(a.stall_word), 1, a, dummy)) fail = true;
-        }
-        float v[OP_MAX][GM];
-        int32_t nbv[OP_MAX];
-        float wv[OP_MAX];
-#pragma unroll
-        for (int j = 0; j < OP_MAX; ++j) {
-            const int4 pp = pc[j / 2];
-            nbv[j] = (j & 1) ? pp.z : pp.x;
-            wv[j] = __int_as_float((j & 1) ? pp.w : pp.y);
-            const bool in = j < ne && nbv[j] >= 0 && !(nbv[j] & NBR_PERIODIC);
-#pragma unroll
-            for (int g = 0; g < GM; ++g)
-                if (g < G) v[j][g] = in ? ld_relaxed(islab + (uint32_t)nbv[j] * G + g) : 0.f;
-        }
-        float acc[GM];
-#pragma unroll
-        for (int g = 0; g < GM; ++g) acc[g] = 0.f;
-#pragma unroll
-        for (int j = 0; j < OP_MAX; ++j) {
-            if (j >= ne) continue;
-            const int32_t nb = nbv[j];
-            bool fast = nb >= 0 && !(nb & NBR_PERIODIC);
-#pragma unroll
-            for (int g = 0; g < GM; ++g)
-                if (g < G) fast = fast && (__float_as_uint(v[j][g]) & 0x80000000u) == par;
-            if (fast) {
-#pragma unroll
-                for (int g = 0; g < GM; ++g)
-                    if (g < G) acc[g] = fmaf(wv[j], __uint_as_float(__float_as_uint(v[j][g]) ^ par), acc[g]);
-            } else {
-                tma_slow<GC>(a, nb, wv[j], slab, G, acc, fail);
-            }
-        }
-        if (valid && !over && !fail) {
-            float* dst = reinterpret_cast<float*>(a.I) + (slab + c) * G;
-            const float P = __int_as_float(h.y);
-#pragma unroll
-            for (int g = 0; g < GM; ++g) {
-                if (g < G) {
-                    const float val = __fdividef(q[g].x + acc[g], P + q[g].y);
-                    st_relaxed(dst + g, __uint_as_float(__float_as_uint(val) ^ par));
-                }
-            }
-        }
-        if (over) fail = !tma_overflow<GC>(a, __ldg(a.trec + (warp + i * nwarps) * 32 + lane), s_om) || fail;
-        if (__any_sync(0xffffffffu, fail)) { ok = false; break; }
-        if ((i & 15) == 15 && __any_sync(0xffffffffu, ld_volatile_i32(a.err) != DEV_OK)) { ok = false; break; }
-    }
-    if (!ok && lane == 0) {
-        // copies already issued for later chunks must land before the block's shared memory goes away
-        for (int64_t j = i + 1; j < i + TMA_STAGES && warp + j * nwarps < nchunks; ++j)
-            mbar_wait(bar + (j % TMA_STAGES), (uint32_t)((j / TMA_STAGES) & 1), a);
-    }
-}
-
-size_t tma_smem_bytes(int nd) {
-    return sizeof(TmaStage) * TMA_WARPS * TMA_STAGES + sizeof(uint64_t) * (TMA_WARPS * TMA_STAGES + 2) +
-           sizeof(float4) * (size_t)nd;
-}
-
-template <int GC>
-int occupancy_tma(int nd) {
-    static bool attr_set = false;
-    const size_t smem = tma_smem_bytes(nd);
-    cudaFuncSetAttribute(k_sweep_tma<GC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    (void)attr_set;
-    int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma<GC>, TMA_WARPS * 32, smem);
-    return n;
 }
 
 template <int LP>
@@ -1139,18 +962,6 @@ cudaError_t launch_typed(const SweepArgs& a, int blocks, int threads, cudaStream
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (sizeof(real) == 4 && !a.reverse && a.op && a.lanes == 1) {  // thread per task, TMA-staged rows
-        *kid = SWEEP_KERNEL_OPERATOR_TMA;
-        cudaLaunchConfig_t c2 = cfg;
-        c2.blockDim = dim3(TMA_WARPS * 32);
-        c2.dynamicSmemBytes = tma_smem_bytes(a.nd);
-        switch (a.G) {
-            case 1: return cudaLaunchKernelEx(&c2, k_sweep_tma<1>, a);
-            case 2: return cudaLaunchKernelEx(&c2, k_sweep_tma<2>, a);
-            case 4: return cudaLaunchKernelEx(&c2, k_sweep_tma<4>, a);
-            default: return cudaLaunchKernelEx(&c2, k_sweep_tma<0>, a);
-        }
-    }
     if (sizeof(real) == 4 && !a.reverse && a.op) {  // FP32 forward over the assembled operator
         *kid = a.lanes >= 8 && a.G == 1 && !a.level_sync ? SWEEP_KERNEL_OPERATOR_LEAN : SWEEP_KERNEL_OPERATOR;
         if (a.lanes <= 2) return launch_op_lanes<2>(a, cfg);
@@ -1188,14 +999,6 @@ int occupancy_lanes(int G, int threads, size_t smem) {
 
 int sweep_occupancy(int precision, int G, int threads, int nd, int lanes, int reverse, bool op) {
     size_t smem = sizeof(float4) * (size_t)nd;
-    if (precision == 32 && !reverse && op && lanes == 1) {
-        switch (G) {
-            case 1: return occupancy_tma<1>(nd);
-            case 2: return occupancy_tma<2>(nd);
-            case 4: return occupancy_tma<4>(nd);
-            default: return occupancy_tma<0>(nd);
-        }
-    }
     if (precision == 32 && !reverse && op) {
         if (lanes <= 2) return occupancy_op<2>(G, threads, smem);
         if (lanes == 4) return occupancy_op<4>(G, threads, smem);
