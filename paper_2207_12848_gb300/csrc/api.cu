@@ -110,7 +110,7 @@ void free_levels(Levels& L) {
 }
 
 void free_mesh(DevMesh& m) {
-    dfree(m.rowptr); dfree(m.side); dfree(m.side64); dfree(m.side_lo); dfree(m.vol); dfree(m.pcells); dfree(m.bcells);
+    dfree(m.rowptr); dfree(m.side); dfree(m.side64); dfree(m.side_lo); dfree(m.nbr_rows); dfree(m.vol); dfree(m.pcells); dfree(m.bcells);
     m = DevMesh();
 }
 
@@ -469,6 +469,7 @@ sweep_status sweep_set_mesh(sweep_ctx* c, int64_t n_cells, const double* volume,
     CKM(cudaMalloc(&m.side, sizeof(int4) * (S > 0 ? S : 1) + 64 * sizeof(int4)), "alloc sides");
     CKM(cudaMalloc(&m.side64, sizeof(d4) * (S > 0 ? S : 1)), "alloc sides");
     CKM(cudaMalloc(&m.side_lo, sizeof(float4) * (S > 0 ? S : 1)), "alloc sides");
+    CKM(cudaMalloc(&m.nbr_rows, sizeof(int2) * (S > 0 ? S : 1)), "alloc sides");
     CKM(launch_build_csr(m, d_fc, d_area, d_normal, d_flags, d_tmp, c->st), "build CSR");
     CKM(cudaStreamSynchronize(c->st), "build CSR");
 #undef CKM
@@ -1090,8 +1091,8 @@ sweep_status sweep_levels(sweep_ctx* c, int32_t dir, int32_t* level, int32_t* de
     sweep_status s = ensure_levels(c, nullptr, nullptr, nullptr);
     if (s != SWEEP_OK) return s;
     if (level)
-        CK(cudaMemcpy2DAsync(level, sizeof(int32_t), c->lev.level + dir, sizeof(int32_t) * c->lev.nd,
-                             sizeof(int32_t), c->mesh.N, cudaMemcpyDeviceToHost, c->st), "copy levels");
+        CK(cudaMemcpyAsync(level, c->lev.level + (size_t)dir * c->mesh.N, sizeof(int32_t) * c->mesh.N,
+                           cudaMemcpyDeviceToHost, c->st), "copy levels");
     CK(cudaStreamSynchronize(c->st), "copy levels");
     if (depth) *depth = c->lev.depth[dir];
     return SWEEP_OK;

@@ -198,6 +198,7 @@ struct DevMesh {
     int4* side = nullptr;                  // [S]
     d4* side64 = nullptr;                  // [S]
     float4* side_lo = nullptr;             // [S] area vector minus its FP32 value in the side record
+    int2* nbr_rows = nullptr;              // [S] row bounds of the side's interior neighbour ({0, 0} otherwise)
     double* vol = nullptr;                 // [N]
     int32_t* pcells = nullptr;             // cells with periodic sides
     int64_t n_pcells = 0;
@@ -221,7 +222,7 @@ struct Levels {
     int4* op = nullptr;          // assembled operator: headers then entries (see build_operator), or null
     size_t op_bytes = 0;
     bool op_valid = false;
-    int32_t* level = nullptr;    // [N][nd]
+    int32_t* level = nullptr;    // [nd][N] (during levelisation: minus the upwind cells still unsolved)
     int32_t* lvl_cnt = nullptr;  // [N+2]
     uint32_t* pad_off = nullptr; // [N+2] start of each level in the padded list
     int64_t* lev_chunk = nullptr;  // device [n_levels+1] chunk (32-task) offsets

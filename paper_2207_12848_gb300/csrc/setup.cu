@@ -183,8 +183,8 @@ __global__ void k_flag_boundary(int64_t F, const uint8_t* flags, int32_t* isb) {
 }
 
 __global__ void k_fill_sides(int64_t S, const int64_t* key, const int32_t* fc, const double* area,
-                             const double* normal, const uint8_t* flags, const int64_t* bidx, int4* side,
-                             d4* side64, float4* side_lo) {
+                             const double* normal, const uint8_t* flags, const int64_t* bidx,
+                             const uint32_t* rowptr, int4* side, d4* side64, float4* side_lo, int2* nbr_rows) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     int64_t k = key[s];
@@ -211,6 +211,7 @@ __global__ void k_fill_sides(int64_t S, const int64_t* key, const int32_t* fc, c
     side[s] = r;
     side64[s] = d4{nx, ny, nz, A};
     side_lo[s] = make_float4((float)(ax - (double)hx), (float)(ay - (double)hy), (float)(az - (double)hz), 0.f);
+    nbr_rows[s] = nbr >= 0 && !(nbr & NBR_PERIODIC) ? make_int2((int)rowptr[nbr], (int)rowptr[nbr + 1]) : make_int2(0, 0);
 }
 
 __global__ void k_cell_kinds(int64_t N, const uint32_t* rowptr, const int4* side, int32_t* isp, int32_t* isb) {
@@ -279,8 +280,8 @@ cudaError_t launch_build_csr(const DevMesh& mc, const int32_t* fc, const double*
         k_flag_boundary<<<nblk(F), 256, 0, st>>>(F, flags, isb);
         TRY(scan_i32(isb, F, bidx, scratch, total, st));
     }
-    if (S > 0) k_fill_sides<<<nblk(S), 256, 0, st>>>(S, key, fc, area, normal, flags, bidx, m.side, m.side64,
-                                                     m.side_lo);
+    if (S > 0) k_fill_sides<<<nblk(S), 256, 0, st>>>(S, key, fc, area, normal, flags, bidx, m.rowptr, m.side,
+                                                     m.side64, m.side_lo, m.nbr_rows);
     // periodic / boundary cell lists (increasing cell order)
     if (N > 0) {
         k_cell_kinds<<<nblk(N), 256, 0, st>>>(N, m.rowptr, m.side, isp, isb);
@@ -366,7 +367,7 @@ __global__ void k_classify(int64_t N, int nd, const uint32_t* rowptr, const int4
         }
         int pbits = __float_as_int(P) | ((r1 - r0 > 32u) ? (int)0x80000000 : 0);
         info[t] = make_int4(cnt, pbits, (int)inm, (int)outm);
-        level[t] = cnt == 0 ? 0 : -1;
+        level[(size_t)dl * N + c] = -cnt;  // 0: level 0; the levelisation counts up to 0, then stores the level
         entry = ((uint32_t)dl << cshift) | (uint32_t)c;
     }
     bool push = active && cnt == 0;
@@ -482,8 +483,7 @@ __global__ void __launch_bounds__(256) k_levelise(LeveliseArgs a) {
 #pragma unroll
                     for (int k = 0; k < KU; ++k) {
                         if (old[k] != 1) continue;
-                        const int64_t kk = (int64_t)r[k].x * a.nd + dl;
-                        a.level[kk] = L + 1;
+                        a.level[(size_t)dl * a.N + (uint32_t)r[k].x] = L + 1;
                         const uint32_t ne = (dl << a.cshift) | (uint32_t)r[k].x;
                         const int p = atomicAdd(&s_n, 1);
                         if (p < LQ_CAP) s_q[p] = ne;
@@ -564,7 +564,8 @@ __global__ void k_sort_levels(const uint32_t* raw, uint32_t* task, const uint32_
 constexpr int LD_THREADS = 1024;
 constexpr int LD_KL = 2;     // lanes per task
 constexpr int LD_KU = 8;     // face sides per lane per pass
-constexpr int LD_Q = 4096;   // shared-memory list capacity per level
+constexpr int LD_Q = 4096;   // level-list entries {cell, row start, row end} held in shared memory
+constexpr size_t LD_SMEM = sizeof(uint32_t) * 3 * 2 * LD_Q;
 
 struct DirLevArgs {
     int64_t N;
@@ -573,10 +574,10 @@ struct DirLevArgs {
     const uint32_t* rowptr;
     const int4* side;
     const d4* side64;
+    const int2* nbr_rows;    // [S] row bounds of each side's interior neighbour
     const float4* om32;
     const double* om64;
-    int4* info;
-    int32_t* level;
+    int32_t* level;          // [nd][N]: minus the unsolved upwind cells, then the level
     uint32_t* dlist;         // [nd][N] cells of each direction in level order; level 0 from the classification
     const int32_t* n0;       // [nd] level-0 sizes
     int32_t* dcnt;           // [nd][cap] cells on each level
@@ -585,19 +586,29 @@ struct DirLevArgs {
     int32_t* overflow;       // set when a direction has more than cap levels
 };
 
+// Per level and task: the side records of the cell's row (classified in registers: sign of n.Omega
+// as in the classification) and, for each downwind interior neighbour, one atomic on its counter
+// together with a load of that neighbour's row bounds, so a cell released here enters the next
+// level's list with its row already known: two dependent memory round trips per level.
 __global__ void __launch_bounds__(LD_THREADS, 1) k_levelise_dir(DirLevArgs a) {
-    __shared__ uint32_t s_q[2][LD_Q];
+    extern __shared__ uint32_t s_lists[];  // [2][LD_Q][3]
     __shared__ int s_next;
     const int gl = threadIdx.x % LD_KL;
     constexpr int TPR = LD_THREADS / LD_KL;  // tasks per round
     for (int d = blockIdx.x; d < a.nd; d += gridDim.x) {
         uint32_t* out = a.dlist + (size_t)d * a.N;
+        int32_t* lv = a.level + (size_t)d * a.N;
         int32_t* cnt = a.dcnt + (size_t)d * a.cap;
         int32_t* bas = a.dbase + (size_t)d * a.cap;
         const float4 om = a.om32[d];
         const double* o64 = a.om64 + 3 * d;
         int n = a.n0[d];
-        for (int i = threadIdx.x; i < n && i < LD_Q; i += LD_THREADS) s_q[0][i] = out[i];
+        for (int i = threadIdx.x; i < n && i < LD_Q; i += LD_THREADS) {
+            const uint32_t c = out[i];
+            s_lists[3 * i] = c;
+            s_lists[3 * i + 1] = a.rowptr[c];
+            s_lists[3 * i + 2] = a.rowptr[c + 1];
+        }
         uint32_t base = 0;
         int L = 0, cur = 0;
         while (n > 0) {
@@ -612,42 +623,53 @@ __global__ void __launch_bounds__(LD_THREADS, 1) k_levelise_dir(DirLevArgs a) {
             }
             __syncthreads();
             const uint32_t nbase = base + (uint32_t)n;
+            const uint32_t* q = s_lists + cur * 3 * LD_Q;
+            uint32_t* qn = s_lists + (cur ^ 1) * 3 * LD_Q;
             for (int i0 = 0; i0 < n; i0 += TPR) {
                 const int i = i0 + threadIdx.x / LD_KL;
                 if (i >= n) continue;
-                const uint32_t c = n <= LD_Q ? s_q[cur][i] : out[base + i];
-                const uint32_t r0 = a.rowptr[c], r1 = a.rowptr[c + 1];
-                const uint32_t outm = (uint32_t)a.info[(int64_t)c * a.nd + d].w;
+                uint32_t r0, r1;
+                if (i < LD_Q) {
+                    r0 = q[3 * i + 1];
+                    r1 = q[3 * i + 2];
+                } else {  // a level wider than the shared list: cells from the global list
+                    const uint32_t c = out[base + i];
+                    r0 = a.rowptr[c];
+                    r1 = a.rowptr[c + 1];
+                }
                 for (uint32_t b = r0; b < r1; b += LD_KL * LD_KU) {
                     int4 r[LD_KU];
 #pragma unroll
                     for (int k = 0; k < LD_KU; ++k) {
                         const uint32_t s = b + gl + k * LD_KL;
-                        const uint32_t idx = s - r0;
-                        const bool need = s < r1 && (idx >= 32u || ((outm >> idx) & 1u));
-                        r[k] = need ? a.side[s] : make_int4(-1, 0, 0, 0);
+                        r[k] = s < r1 ? a.side[s] : make_int4(-1, 0, 0, 0);
                     }
                     int old[LD_KU];
+                    int2 nr[LD_KU];
 #pragma unroll
                     for (int k = 0; k < LD_KU; ++k) {
                         old[k] = 0;
-                        const uint32_t s = b + gl + k * LD_KL;
+                        nr[k] = make_int2(0, 0);
                         if (r[k].x < 0 || (r[k].x & NBR_PERIODIC)) continue;
-                        if (s - r0 >= 32u) {
-                            const float ax = __int_as_float(r[k].y), ay = __int_as_float(r[k].z),
-                                        az = __int_as_float(r[k].w);
-                            if (classify_side(dot32(ax, ay, az, om), ax, ay, az, a.side64, s, o64) <= 0) continue;
-                        }
-                        old[k] = atomicSub(&a.info[(int64_t)r[k].x * a.nd + d].x, 1);
+                        const uint32_t s = b + gl + k * LD_KL;
+                        const float ax = __int_as_float(r[k].y), ay = __int_as_float(r[k].z),
+                                    az = __int_as_float(r[k].w);
+                        if (classify_side(dot32(ax, ay, az, om), ax, ay, az, a.side64, s, o64) <= 0) continue;
+                        old[k] = atomicAdd(&lv[r[k].x], 1);
+                        nr[k] = a.nbr_rows[s];
                     }
 #pragma unroll
                     for (int k = 0; k < LD_KU; ++k) {
-                        if (old[k] != 1) continue;
+                        if (old[k] != -1) continue;  // this side solved the neighbour's last upwind cell
                         const uint32_t x = (uint32_t)r[k].x;
-                        a.level[(int64_t)x * a.nd + d] = L + 1;
+                        lv[x] = L + 1;
                         const int p = atomicAdd(&s_next, 1);
                         if (nbase + (uint32_t)p < (uint32_t)a.N) out[nbase + p] = x;
-                        if (p < LD_Q) s_q[cur ^ 1][p] = x;
+                        if (p < LD_Q) {
+                            qn[3 * p] = x;
+                            qn[3 * p + 1] = (uint32_t)nr[k].x;
+                            qn[3 * p + 2] = (uint32_t)nr[k].y;
+                        }
                     }
                 }
             }
@@ -866,11 +888,13 @@ cudaError_t levelise_by_direction(const DevMesh& m, Levels& L, const float4* om3
     int32_t* depth = n0 + nd;
     int32_t* ovf = depth + nd;
     DirLevArgs a;
-    a.N = m.N; a.nd = nd; a.cap = cap; a.rowptr = m.rowptr; a.side = m.side; a.side64 = m.side64; a.om32 = om32;
-    a.om64 = om64; a.info = L.info; a.level = L.level; a.dlist = L.raw; a.n0 = n0; a.dcnt = dcnt; a.dbase = dbase;
+    a.N = m.N; a.nd = nd; a.cap = cap; a.rowptr = m.rowptr; a.side = m.side; a.side64 = m.side64;
+    a.nbr_rows = m.nbr_rows; a.om32 = om32; a.om64 = om64; a.level = L.level; a.dlist = L.raw; a.n0 = n0;
+    a.dcnt = dcnt; a.dbase = dbase;
     a.depth = depth; a.overflow = ovf;
     const int blocks = nd < dev_sms ? nd : dev_sms;
-    k_levelise_dir<<<blocks, LD_THREADS, 0, st>>>(a);
+    cudaFuncSetAttribute(k_levelise_dir, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LD_SMEM);
+    k_levelise_dir<<<blocks, LD_THREADS, LD_SMEM, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     std::vector<int32_t> h(nd + 1);
