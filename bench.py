@@ -400,7 +400,8 @@ def run_ours(args, dist: Dist):
                          "sweep_ms_per_launch": avg_launch_s * 1e3,
                          "schedule": {1: "level", 2: "dataflow"}.get(last["schedule_used"], last["schedule_used"]),
                          "lanes_per_task": last["lanes_used"], "threads_per_block": last["threads_used"],
-                         "blocks_per_sm": last["blocks_per_sm_used"]}}
+                         "blocks_per_sm": last["blocks_per_sm_used"],
+                         "iterations_as_cuda_graphs": bool(last["graph_used"])}}
         out.update(extra)
         print(json.dumps(out))
 

@@ -74,11 +74,14 @@ typedef struct {
     int32_t dir_batch;    /* adjoint: directions per recompute batch (0 = all directions at once) */
     int32_t relevel;      /* 1: redo classification and levelisation even if cached for this mesh+directions */
     int32_t block_threads;/* threads per block of the batched sweep (0 = autotuned) */
-    int32_t use_graph;    /* 1: capture one iteration in a CUDA graph and replay it */
+    int32_t use_graph;    /* 1 (default): run the periodic iteration or the source iteration as CUDA graphs, each
+                             distinct iteration captured once per solve and replayed (not with both loops on,
+                             the plain schedule or debug_stall, or when capture is refused: host loop) */
     int64_t spin_budget;  /* bound on each device-side wait, in polls (0 = default, about 1 s) */
     int32_t debug_stall;  /* TEST ONLY: 1 makes the first sweep task wait on a word nothing writes */
     int32_t lanes_per_task; /* lanes cooperating on one task in the batched sweep: 1..16, a power of 2 (0 = autotuned);
-                               over the assembled operator 2, 4 or 8 (1 runs as 2, 16 as 8) */
+                               over the assembled operator 2, 4 or 8 (1 runs as 2), and 16 = 8 lanes per task
+                               with two tasks per lane group (one group, dataflow schedule; else as 8) */
     int32_t geometry_only;  /* 1: the FP32 sweep reads the mesh every sweep instead of the assembled operator */
     int32_t blocks_per_sm;  /* resident blocks per SM of the batched sweep (0 = autotuned / maximum) */
 } sweep_opts;
@@ -103,6 +106,7 @@ typedef struct {
     int32_t threads_used;      /* threads per block of the batched sweep that ran */
     int32_t blocks_per_sm_used;/* resident blocks per SM it was launched with (0 = maximum) */
     int32_t kernel_used;       /* SWEEP_KERNEL_* form of the batched sweep that ran last */
+    int32_t graph_used;        /* 1: the iterations ran as CUDA graphs */
 } sweep_stats;
 
 /* Forms of the batched sweep kernel (sweep_stats.kernel_used). */
@@ -112,7 +116,8 @@ enum {
     SWEEP_KERNEL_GEOMETRY = 2,       /* lane groups reading the mesh rows (FP64, and every adjoint sweep) */
     SWEEP_KERNEL_RECORDS = 3,        /* FP32 forward, lane groups over task records and mesh rows */
     SWEEP_KERNEL_OPERATOR = 4,       /* FP32 forward over the assembled operator, lane groups */
-    SWEEP_KERNEL_OPERATOR_LEAN = 5   /* the same, one group and 8 lanes per task, dataflow schedule */
+    SWEEP_KERNEL_OPERATOR_LEAN = 5,  /* the same, one group and 8 lanes per task, dataflow schedule */
+    SWEEP_KERNEL_OPERATOR_PAIR = 6   /* the same with two tasks per 8-lane group per step */
 };
 
 /* Fill *opts with defaults: precision 32, AUTO schedule, tolerances 1e-6, 100 iterations. */

@@ -24,7 +24,7 @@ SWEEP_FACE_PERIODIC = 2
 SWEEP_SCHED_AUTO, SWEEP_SCHED_LEVEL, SWEEP_SCHED_DATAFLOW, SWEEP_SCHED_PLAIN = 0, 1, 2, 3
 SCHEDULES = {"auto": 0, "level": 1, "dataflow": 2, "plain": 3}
 # forms of the batched sweep kernel (sweep_stats.kernel_used)
-KERNELS = {0: "none", 1: "k_plain", 2: "k_sweep", 3: "k_sweep_rec", 4: "k_sweep_op", 5: "k_sweep_op1"}
+KERNELS = {0: "none", 1: "k_plain", 2: "k_sweep", 3: "k_sweep_rec", 4: "k_sweep_op", 5: "k_sweep_op1", 6: "k_sweep_op2"}
 
 # every entry point include/sweep.h declares
 EXPORTS = ("sweep_default_opts", "sweep_create", "sweep_destroy", "sweep_set_mesh", "sweep_set_directions",
@@ -52,7 +52,8 @@ class sweep_stats(ctypes.Structure):
                 ("updates_per_s", ctypes.c_double), ("sweep_launches", ctypes.c_int32),
                 ("schedule_used", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
                 ("lanes_used", ctypes.c_int32), ("threads_used", ctypes.c_int32),
-                ("blocks_per_sm_used", ctypes.c_int32), ("kernel_used", ctypes.c_int32)]
+                ("blocks_per_sm_used", ctypes.c_int32), ("kernel_used", ctypes.c_int32),
+                ("graph_used", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "t_ms"}

@@ -69,6 +69,8 @@ struct sweep_ctx {
     // autotuner: schedule and block size per (precision, G)
     int tuned[2][9][2][4] = {};  // [precision][groups][operator mode] -> schedule, threads, lanes, blocks/SM
     int64_t launches = 0;  // kernels launched by this context
+    cudaStream_t gst = nullptr;  // capture/replay stream of the iteration graphs
+    void* hpin = nullptr;        // pinned host words the iteration graphs write
 };
 
 namespace {
@@ -307,6 +309,199 @@ sweep_status run_sweep(sweep_ctx* c, const Levels& L, int precision, int schedul
     return SWEEP_OK;
 }
 
+// ---------------------------------------------------------------------------------------------
+// The periodic iteration (Sec. 2.7) or the source iteration (Alg. 1) as CUDA graphs. The iterations
+// of a solve repeat with a short period: which intensity buffer is swept, the sign parity it is
+// written with, and which periodic-inflow array is read change in a cycle of 4 (periodic) or 2
+// (scattering). Each distinct iteration is captured once per solve on the context's capture stream
+// and replayed; an iteration is then one graph launch and one synchronisation, after which the
+// host reads the convergence residual, the error word and the sweep's event times from pinned
+// memory written by the graph itself.
+// ---------------------------------------------------------------------------------------------
+struct IterHost {
+    int err;
+    int pad;
+    unsigned long long dmax;
+    double red[2];
+};
+
+struct GraphSet {
+    cudaGraphExec_t ex[4] = {};
+    cudaEvent_t ev[4][3] = {};
+    ~GraphSet() {
+        for (int t = 0; t < 4; ++t) {
+            if (ex[t]) cudaGraphExecDestroy(ex[t]);
+            for (auto& e : ev[t])
+                if (e) cudaEventDestroy(e);
+        }
+    }
+};
+
+// Captures whatever `enqueue` issues on stream gs into an executable graph; false (nothing run) if
+// capture or instantiation is refused.
+template <typename Fn>
+bool capture(cudaStream_t gs, Fn enqueue, cudaGraphExec_t* ex) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const cudaError_t e1 = enqueue();
+    const cudaError_t e2 = cudaStreamEndCapture(gs, &g);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return false;
+    }
+    const cudaError_t e3 = cudaGraphInstantiate(ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) {
+        cudaGetLastError();
+        *ex = nullptr;
+        return false;
+    }
+    return true;
+}
+
+sweep_status ensure_graph_stream(sweep_ctx* c) {
+    if (!c->gst) CK(cudaStreamCreateWithFlags(&c->gst, cudaStreamNonBlocking), "create capture stream");
+    if (!c->hpin) CK(cudaHostAlloc(&c->hpin, sizeof(IterHost), cudaHostAllocDefault), "alloc pinned");
+    return SWEEP_OK;
+}
+
+struct LoopState {
+    int cur = 0, prev = -1;
+    int it_pbc = 0, it_scat_total = 0, n_sweeps = 0;
+    bool conv_pbc = false, conv_scat = false;
+    double res_pbc = 0.0, res_pbc_mean = 0.0, res_scat = 0.0;
+    float t_sweep = 0.f, t_other = 0.f;
+};
+
+// Runs the iterations of a solve with exactly one of the two loops (periodic without scattering, or
+// scattering without periodic faces) as graphs. *done = false (nothing run) when the graphs cannot
+// be captured; the caller then runs the host loop from the same state.
+sweep_status graph_loop(sweep_ctx* c, const sweep_opts& o, int prec, const void* cm, const float* bc32, int sched,
+                        int threads, int lanes, int bpsm, int nblk, LoopState& st, bool* done) {
+    *done = false;
+    const bool pbc = c->mesh.n_pcells > 0;
+    SolveBuf& b = c->sb;
+    const int64_t N = c->mesh.N;
+    const int G = c->G, D = c->D;
+    const size_t NG = (size_t)N * G;
+    sweep_status s = ensure_graph_stream(c);
+    if (s != SWEEP_OK) return s;
+    cudaStream_t gs = c->gst;
+    IterHost* hp = reinterpret_cast<IterHost*>(c->hpin);
+    int per_sm = sweep_occupancy(prec, G, threads, c->lev.nd, lanes, 0, prec == 32 && c->lev.op_valid && !o.geometry_only);
+    if (per_sm < 1) return bad(c, "sweep kernel does not fit on an SM");
+    if (bpsm > 0 && bpsm < per_sm) per_sm = bpsm;
+    const int period = pbc ? 4 : 2;
+    const int cur0 = st.cur;
+    const int sgn[2] = {b.sign[0], b.sign[1]};
+    double* jA = c->jn;
+    double* jB = c->jn1;
+    int kid = 0;
+    // iteration type t: buffer, parity (the buffer's (t/2)-th or t-th write since the start), j arrays
+    auto cur_of = [&](int t) { return pbc ? ((t & 1) ? 1 - cur0 : cur0) : cur0; };
+    auto parity_of = [&](int t) {
+        const int k = pbc ? t / 2 : t;  // writes of this buffer before iteration t, modulo 2
+        return (k & 1) ? sgn[cur_of(t)] : !sgn[cur_of(t)];
+    };
+    auto enqueue = [&](int t, cudaEvent_t* ev) -> cudaError_t {
+        cudaError_t e;
+        const int cur = cur_of(t);
+        if (!pbc) {  // scattering source from the previous J (Alg. 1)
+            if ((e = launch_prep_material(N, G, c->mesh.vol, c->ka, c->ks, c->em, c->Jold,
+                                          prec == 32 ? c->cm32 : nullptr, prec == 64 ? c->cm64 : nullptr, gs)))
+                return e;
+        }
+        if ((e = cudaMemsetAsync(c->bar, 0, sizeof(GridBar), gs))) return e;
+        if ((e = cudaMemsetAsync(c->derr, 0, sizeof(int), gs))) return e;
+        if ((e = cudaEventRecordWithFlags(ev[0], gs, cudaEventRecordExternal))) return e;
+        SweepArgs a = make_args(c, c->lev, prec, cm, b.I[cur], pbc ? b.I[1 - cur] : nullptr, G, parity_of(t), 0,
+                                sched == SWEEP_SCHED_LEVEL ? 1 : 0, &o);
+        a.debug_stall = 0;
+        if (prec == 32) a.bc = bc32;
+        a.lanes = lanes;
+        if ((e = launch_sweep(a, prec, c->sms * per_sm, threads, gs, &kid))) return e;
+        if ((e = cudaEventRecordWithFlags(ev[1], gs, cudaEventRecordExternal))) return e;
+        if (pbc) {
+            double* jr = (t & 1) ? jB : jA;  // j of the previous iteration
+            double* jw = (t & 1) ? jA : jB;
+            if ((e = cudaMemsetAsync(c->dmax, 0, sizeof(unsigned long long), gs))) return e;
+            if ((e = launch_periodic_source(prec, c->mesh, b.I[cur], G, D, c->om64, c->w64, jw, jr, c->dmax,
+                                            c->partial, nblk, gs)))
+                return e;
+            if ((e = launch_reduce_sum(c->partial, (int)c->mesh.n_pcells, c->red + 2, gs))) return e;
+            if ((e = cudaMemcpyAsync(hp->red, c->red + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, gs))) return e;
+        } else {
+            if ((e = launch_tally(prec, b.I[cur], N, G, D, 0, c->w64, c->wsum, c->mesh.vol, c->ka, c->em, c->J,
+                                  c->Gam, c->partial, nblk, gs)))
+                return e;
+            if ((e = cudaMemsetAsync(c->dmax, 0, sizeof(unsigned long long), gs))) return e;
+            if ((e = launch_scat_residual(NG, c->J, c->Jold, c->dmax, gs))) return e;
+        }
+        if ((e = cudaEventRecordWithFlags(ev[2], gs, cudaEventRecordExternal))) return e;
+        if ((e = cudaMemcpyAsync(&hp->err, c->derr, sizeof(int), cudaMemcpyDeviceToHost, gs))) return e;
+        return cudaMemcpyAsync(&hp->dmax, c->dmax, sizeof(unsigned long long), cudaMemcpyDeviceToHost, gs);
+    };
+    const int max_it = pbc ? o.max_it_pbc : o.max_it_scat;
+    const int ntypes = std::min(period, std::max(max_it, 1));
+    GraphSet gset;
+    for (int t = 0; t < ntypes; ++t) {
+        for (auto& e : gset.ev[t]) CK(cudaEventCreate(&e), "create event");
+        if (!capture(gs, [&] { return enqueue(t, gset.ev[t]); }, &gset.ex[t])) return SWEEP_OK;  // host loop instead
+    }
+    // the graphs run on the capture stream, after everything queued so far on the context's stream
+    cudaEvent_t fork;
+    CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "create event");
+    cudaEventRecord(fork, c->st);
+    cudaStreamWaitEvent(gs, fork, 0);
+    cudaEventDestroy(fork);
+    *done = true;
+    const int per_iter = pbc ? 3 : 4;  // kernels per iteration
+    for (int it = 0;; ++it) {
+        const int t = it % period;
+        CK(cudaGraphLaunch(gset.ex[t], gs), "graph launch");
+        CK(cudaStreamSynchronize(gs), "iteration");
+        c->launches += per_iter;
+        c->last_kernel = kid;
+        float ts = 0, to = 0;
+        cudaEventElapsedTime(&ts, gset.ev[t][0], gset.ev[t][1]);
+        cudaEventElapsedTime(&to, gset.ev[t][1], gset.ev[t][2]);
+        st.t_sweep += ts;
+        st.t_other += to;
+        if (hp->err != DEV_OK) {
+            c->err = "sweep: a bounded device wait gave up";
+            return SWEEP_ERR_TIMEOUT;
+        }
+        const int cur = cur_of(t);
+        b.sign[cur] = parity_of(t);
+        ++st.n_sweeps;
+        double r;
+        memcpy(&r, &hp->dmax, sizeof r);
+        if (pbc) {
+            ++st.it_scat_total;
+            ++st.it_pbc;
+            st.res_pbc = r;
+            st.res_pbc_mean = NG > 0 ? hp->red[0] / (double)NG : 0.0;
+            std::swap(c->jn, c->jn1);
+            st.prev = cur;
+            st.cur = 1 - cur;
+            if (st.res_pbc < o.tol_pbc) { st.conv_pbc = true; break; }
+            if (st.it_pbc >= o.max_it_pbc) { st.conv_pbc = false; break; }
+        } else {
+            ++st.it_scat_total;
+            st.res_scat = r;
+            if (st.res_scat <= o.tol_scat) { st.conv_scat = true; break; }
+            if (st.it_scat_total >= o.max_it_scat) { st.conv_scat = false; break; }
+        }
+    }
+    if (!pbc) st.it_pbc = 1;
+    return SWEEP_OK;
+}
+
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
@@ -322,6 +517,7 @@ void sweep_default_opts(sweep_opts* o) {
     o->tol_scat = 1e-6;
     o->max_it_pbc = 100;
     o->tol_pbc = 1e-6;
+    o->use_graph = 1;
 }
 
 const char* sweep_status_string(sweep_status s) {
@@ -381,6 +577,8 @@ sweep_status sweep_destroy(sweep_ctx* c) {
     dfree(c->J); dfree(c->Jold); dfree(c->Gam); dfree(c->jn); dfree(c->jn1);
     dfree(c->partial); dfree(c->red); dfree(c->dmax); dfree(c->bar); dfree(c->derr); dfree(c->scratch);
     dfree(c->stall_word);
+    if (c->gst) cudaStreamDestroy(c->gst);
+    if (c->hpin) cudaFreeHost(c->hpin);
     delete c;
     return SWEEP_OK;
 }
@@ -674,6 +872,7 @@ sweep_status autotune(sweep_ctx* c, int prec, const void* cm, const float* bc32,
     if (op) {
         // 8 lanes per task (4 tasks per warp step) and 4 lanes per task (8 tasks per step)
         cand.push_back({SWEEP_SCHED_DATAFLOW, 256, 8, 0});
+        cand.push_back({SWEEP_SCHED_DATAFLOW, 256, 16, 0});
         cand.push_back({SWEEP_SCHED_DATAFLOW, 256, 4, 0});
         cand.push_back({SWEEP_SCHED_LEVEL, 256, 8, 0});
     } else {
@@ -833,7 +1032,38 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     cudaEventCreate(&u0);
     cudaEventCreate(&u1);
     float t_other = 0.f;
-    for (;;) {
+    bool graphed = false;
+    if (o.use_graph && !plain && !o.debug_stall && has_pbc != c->has_scat) {
+        // what stays fixed over the iterations: the source without scattering, J_old before Alg. 1
+        if (has_pbc)
+            CKL(launch_prep_material(N, G, c->mesh.vol, c->ka, c->ks, c->em, nullptr, prec == 32 ? c->cm32 : nullptr,
+                                    prec == 64 ? c->cm64 : nullptr, c->st), "prep");
+        else
+            CK(cudaMemsetAsync(c->Jold, 0, sizeof(double) * NG, c->st), "init");
+        LoopState ls;
+        ls.cur = cur;
+        ls.prev = prev;
+        ls.conv_pbc = conv_pbc;
+        ls.conv_scat = conv_scat;
+        s = graph_loop(c, o, prec, cm, bc32.p, sched, threads, lanes, bpsm, nblk, ls, &graphed);
+        if (s != SWEEP_OK) return s;
+        if (graphed) {
+            cur = ls.cur;
+            prev = ls.prev;
+            it_pbc = ls.it_pbc;
+            it_scat_total = ls.it_scat_total;
+            n_sweeps = ls.n_sweeps;
+            conv_pbc = ls.conv_pbc;
+            conv_scat = ls.conv_scat;
+            res_pbc = ls.res_pbc;
+            res_pbc_mean = ls.res_pbc_mean;
+            res_scat = ls.res_scat;
+            t_sweep = ls.t_sweep;
+            t_other = ls.t_other;
+        }
+    }
+    S.graph_used = graphed ? 1 : 0;
+    for (; !graphed;) {
         CK(cudaMemsetAsync(c->Jold, 0, sizeof(double) * NG, c->st), "init");
         int it_scat = 0;
         for (;;) {

@@ -835,6 +835,109 @@ __global__ void __launch_bounds__(256, SWEEP_REC_MINB) k_sweep_op1(SweepArgs a) 
     }
 }
 
+// Two tasks per lane group per step: a warp takes 8 tasks (1 KB of operator lines) per loop
+// iteration, lanes gl of group grp holding piece gl of tasks 8k+grp and 8k+4+grp. The fixed cost
+// of an iteration (line loads, prefetch, header shuffles, loop control, the overflow vote) is shared
+// by twice as many tasks as in k_sweep_op1, and each lane has up to four upwind reads in flight.
+// The 8 tasks of a step lie in one level (levels are padded to 32 tasks), so they are independent.
+__global__ void __launch_bounds__(256, SWEEP_REC_MINB) k_sweep_op2(SweepArgs a) {
+    extern __shared__ float4 s_om[];
+    for (int i = threadIdx.x; i < a.nd; i += blockDim.x) s_om[i] = a.om32[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int grp = lane >> 3, gl = lane & 7, lead = lane & ~7;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nsteps = a.n_chunks * 4;  // steps of 8 tasks
+    const uint64_t pol = policy_evict_first();
+    const float* I = reinterpret_cast<const float*>(a.I);
+    const float2* cm = reinterpret_cast<const float2*>(a.cm);
+    const uint32_t par = a.parity ? 0x80000000u : 0u;
+    const int4 pad = make_int4((int)TASK_PAD, 0, 0, 0);
+    const int4* src = a.op + warp * 64 + lane;  // step k: tasks A at src + (k-warp)*64, B 32 int4 further
+    const int64_t stride = nwarps * 64;
+    int64_t k = warp;
+    int4 ca = k < nsteps ? ld_stream_int4(src, pol) : pad;
+    int4 cb = k < nsteps ? ld_stream_int4(src + 32, pol) : pad;
+    if (lane == 0)
+        for (int j = 1; j <= 2; ++j)
+            if (k + j * nwarps < nsteps)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.op + (k + j * nwarps) * 64),
+                             "r"(1024u));
+    if (a.debug_stall && warp == 0 && lane == 0) {  // test hook: a wait on a word that nothing writes
+        float dummy;
+        wait_value(reinterpret_cast<const float*>(a.stall_word), 1, a, dummy);
+    }
+    for (int64_t i = 0; k < nsteps; ++i, k += nwarps) {
+        if ((i & 15) == 0 && __any_sync(0xffffffffu, ld_volatile_i32(a.err) != DEV_OK)) return;
+        src += stride;
+        const bool more = k + nwarps < nsteps;
+        const int4 na = more ? ld_stream_int4(src, pol) : pad;
+        const int4 nb = more ? ld_stream_int4(src + 32, pol) : pad;
+        if (lane == 0 && k + 3 * nwarps < nsteps)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.op + (k + 3 * nwarps) * 64), "r"(1024u));
+        const uint32_t ea = (uint32_t)__shfl_sync(0xffffffffu, ca.x, lead);
+        const uint32_t eb = (uint32_t)__shfl_sync(0xffffffffu, cb.x, lead);
+        const int za = __shfl_sync(0xffffffffu, ca.z, lead);
+        const int zb = __shfl_sync(0xffffffffu, cb.z, lead);
+        const int nina = za & 0xff, ninb = zb & 0xff;
+        const bool overa = ea != TASK_PAD && nina > OP_MAX, overb = eb != TASK_PAD && ninb > OP_MAX;
+        const bool worka = ea != TASK_PAD && !overa, workb = eb != TASK_PAD && !overb;
+        bool fail = false;
+        float acca = 0.f, accb = 0.f;
+        float2 qa = make_float2(0.f, 1.f), qb = make_float2(0.f, 1.f);
+        if (gl == 0) {
+            if (worka) qa = cm[ea & a.cmask];
+            if (workb) qb = cm[eb & a.cmask];
+        } else {
+            const int j0 = 2 * gl - 2;
+            const bool ha0 = worka && j0 < nina, ha1 = worka && j0 + 1 < nina;
+            const bool hb0 = workb && j0 < ninb, hb1 = workb && j0 + 1 < ninb;
+            const bool ia0 = ha0 && ca.y >= 0, ia1 = ha1 && ca.w >= 0;  // sign bit clear: interior entry
+            const bool ib0 = hb0 && cb.y >= 0, ib1 = hb1 && cb.w >= 0;
+            const float xa0 = ia0 ? ld_relaxed(I + (uint32_t)ca.x) : 0.f;
+            const float xa1 = ia1 ? ld_relaxed(I + (uint32_t)ca.z) : 0.f;
+            const float xb0 = ib0 ? ld_relaxed(I + (uint32_t)cb.x) : 0.f;
+            const float xb1 = ib1 ? ld_relaxed(I + (uint32_t)cb.z) : 0.f;
+            auto term = [&](bool in, bool has, float x, uint32_t idx, int wbits, int bit, int z) -> float {
+                const float w = __int_as_float(wbits);
+                if (in) {
+                    const uint32_t u = __float_as_uint(x);
+                    return w * ((u & 0x80000000u) == par ? __uint_as_float(u ^ par) : op_wait(a, I + idx, fail));
+                }
+                float t = 0.f;
+                if (has) op_external<1>(a, idx, w, (z >> (16 + bit)) & 1, 1, &t);
+                return t;
+            };
+            acca = term(ia0, ha0, xa0, (uint32_t)ca.x, ca.y, j0, za) + term(ia1, ha1, xa1, (uint32_t)ca.z, ca.w, j0 + 1, za);
+            accb = term(ib0, hb0, xb0, (uint32_t)cb.x, cb.y, j0, zb) + term(ib1, hb1, xb1, (uint32_t)cb.z, cb.w, j0 + 1, zb);
+        }
+        acca += __shfl_xor_sync(0xffffffffu, acca, 4);
+        accb += __shfl_xor_sync(0xffffffffu, accb, 4);
+        acca += __shfl_xor_sync(0xffffffffu, acca, 2);
+        accb += __shfl_xor_sync(0xffffffffu, accb, 2);
+        acca += __shfl_xor_sync(0xffffffffu, acca, 1);
+        accb += __shfl_xor_sync(0xffffffffu, accb, 1);
+        if (gl == 0 && !fail) {
+            float* out = reinterpret_cast<float*>(a.I);
+            if (worka) {
+                const float v = __fdividef(qa.x + acca, __int_as_float(ca.y) + qa.y);
+                st_relaxed(out + (uint32_t)ca.w, __uint_as_float(__float_as_uint(v) ^ par));
+            }
+            if (workb) {
+                const float v = __fdividef(qb.x + accb, __int_as_float(cb.y) + qb.y);
+                st_relaxed(out + (uint32_t)cb.w, __uint_as_float(__float_as_uint(v) ^ par));
+            }
+        }
+        if (__any_sync(0xffffffffu, overa || overb)) {  // a failed wait inside sets the error word
+            if (__any_sync(0xffffffffu, overa)) op_overflow<1, 8>(a, overa ? __ldg(a.trec + k * 8 + grp) : pad, s_om, gl);
+            if (__any_sync(0xffffffffu, overb)) op_overflow<1, 8>(a, overb ? __ldg(a.trec + k * 8 + 4 + grp) : pad, s_om, gl);
+        }
+        ca = na;
+        cb = nb;
+    }
+}
+
 template <int LP>
 cudaError_t launch_op_lanes(const SweepArgs& a, const cudaLaunchConfig_t& cfg) {
     if (LP == 8 && a.G == 1 && !a.level_sync) return cudaLaunchKernelEx(&cfg, k_sweep_op1, a);
@@ -963,6 +1066,10 @@ cudaError_t launch_typed(const SweepArgs& a, int blocks, int threads, cudaStream
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (sizeof(real) == 4 && !a.reverse && a.op) {  // FP32 forward over the assembled operator
+        if (a.lanes == 16 && a.G == 1 && !a.level_sync) {
+            *kid = SWEEP_KERNEL_OPERATOR_PAIR;
+            return cudaLaunchKernelEx(&cfg, k_sweep_op2, a);
+        }
         *kid = a.lanes >= 8 && a.G == 1 && !a.level_sync ? SWEEP_KERNEL_OPERATOR_LEAN : SWEEP_KERNEL_OPERATOR;
         if (a.lanes <= 2) return launch_op_lanes<2>(a, cfg);
         if (a.lanes == 4) return launch_op_lanes<4>(a, cfg);
@@ -1000,6 +1107,11 @@ int occupancy_lanes(int G, int threads, size_t smem) {
 int sweep_occupancy(int precision, int G, int threads, int nd, int lanes, int reverse, bool op) {
     size_t smem = sizeof(float4) * (size_t)nd;
     if (precision == 32 && !reverse && op) {
+        if (lanes == 16 && G == 1) {
+            int n = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_op2, threads, smem);
+            return n;
+        }
         if (lanes <= 2) return occupancy_op<2>(G, threads, smem);
         if (lanes == 4) return occupancy_op<4>(G, threads, smem);
         return occupancy_op<8>(G, threads, smem);

@@ -107,7 +107,7 @@ def test_voronoi_fp32(ctx, schedule, G, geometry_only):
     assert st["absorbed"] == pytest.approx(r["stats"]["absorbed"], rel=FP32_TOL)
 
 
-@pytest.mark.parametrize("lanes,bpsm", [(1, 1), (1, 0), (2, 0), (4, 0), (8, 0)])
+@pytest.mark.parametrize("lanes,bpsm", [(1, 1), (1, 0), (2, 0), (4, 0), (8, 0), (16, 0)])
 @pytest.mark.parametrize("G", [1, 3])
 def test_operator_kernels(ctx, lanes, bpsm, G):
     # every form of the FP32 forward sweep over the assembled operator (and the periodic inflow path)
@@ -116,6 +116,8 @@ def test_operator_kernels(ctx, lanes, bpsm, G):
     J, Gm, st, s = ctx.solve(precision=32, schedule="dataflow", lanes_per_task=lanes, blocks_per_sm=bpsm,
                              tol_pbc=0.0, max_it_pbc=4)
     assert st["lanes_used"] == lanes
+    if G == 1 and lanes in (8, 16):
+        assert st["kernel_used"] == {8: 5, 16: 6}[lanes]  # the lean forms
     r = run_oracle(p, tol_pbc=0.0, max_it_pbc=4)
     assert fp32_err(J, r["J"]) <= FP32_TOL
 
@@ -238,8 +240,8 @@ def test_adjoint_rejects_scattering(ctx):
 
 
 # ---- edge cases -------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("geometry_only", [0, 1])
-def test_high_degree_cell(ctx, geometry_only):
+@pytest.mark.parametrize("geometry_only,lanes", [(0, 0), (1, 0), (0, 16)])
+def test_high_degree_cell(ctx, geometry_only, lanes):
     # a generator at the centre of a sphere of 60 others: its cell has ~60 faces (rows longer than
     # 32 sides) and ~30 inflow sides per direction (more than an operator line holds)
     rng = np.random.default_rng(61)
@@ -260,7 +262,8 @@ def test_high_degree_cell(ctx, geometry_only):
     ctx.set_mesh(m)
     ctx.set_directions(om, w)
     ctx.set_material(ka, eps)
-    J, G, st, s = ctx.solve(precision=32, geometry_only=geometry_only)
+    J, G, st, s = ctx.solve(precision=32, geometry_only=geometry_only, lanes_per_task=lanes,
+                            schedule="dataflow" if lanes else "auto")
     r = oracle.solve(m, om, w, ka, eps, threads=8)
     assert fp32_err(J, r["J"]) <= FP32_TOL
     J64, _, _, _ = ctx.solve(precision=64)
@@ -361,3 +364,22 @@ def test_plain32_against_stored_golden(ctx, precision):
     assert np.max(np.abs(J[g["cells"], 0] - g["J"]) / np.abs(g["J"])) <= tol
     assert np.max(np.abs(Gm[g["cells"], 0] - g["Gamma"]) / np.abs(g["Gamma"])) <= tol
     assert [ctx.levels(d)[1] for d in range(p.n_dir)] == g["depths"]
+
+
+@pytest.mark.parametrize("kind", ["periodic", "scattering"])
+def test_iteration_graphs_match_the_host_loop(ctx, kind):
+    # the iterations replayed as CUDA graphs run the same kernels in the same order as the host loop,
+    # and every reduction has a fixed order: the answers are bit-identical
+    if kind == "periodic":
+        p = configs.voronoi_small(4000, periodic_box=True, n_dir=12, n_groups=2, seed=91, n_src=8)
+    else:
+        p = configs.voronoi_small(4000, n_dir=12, n_groups=2, seed=92, scatter_albedo=0.5, n_src=8)
+    load(ctx, p)
+    Jg, Gg, sg, _ = ctx.solve(precision=32, schedule="dataflow", use_graph=1)
+    Jh, Gh, sh, _ = ctx.solve(precision=32, schedule="dataflow", use_graph=0)
+    assert sg["graph_used"] == 1 and sh["graph_used"] == 0
+    assert sg["n_sweeps"] == sh["n_sweeps"] and sg["it_pbc"] == sh["it_pbc"] and sg["it_scat"] == sh["it_scat"]
+    assert np.array_equal(Jg, Jh) and np.array_equal(Gg, Gh)
+    assert sg["t_sweep_ms"] > 0  # sweep time from the event nodes inside the graphs
+    r = run_oracle(p)
+    assert fp32_err(Jg, r["J"]) <= FP32_TOL
