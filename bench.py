@@ -32,6 +32,8 @@ WORKLOADS = {
                 "log-uniform sources, absorption only, 128 directions, 1 group, periodic iteration to E<1e-6",
     "batched": "64 Poisson-Voronoi meshes of log-uniform size (2^12..2^17, 2^22 cells), lognormal kappa, "
                "8 sources/mesh, 128 directions, 2 groups, one persistent launch",
+    "scatter": "Voronoi mesh of 2^20 cells sampled ~rho (lognormal, P(k)~k^-3), albedo 0.5, 64 sources, "
+               "96 directions, 4 groups, source iteration to relative change of J < 1e-6",
 }
 
 
@@ -180,6 +182,8 @@ def make_problem(workload: str, rank: int, threads: int | None, cells: int | Non
         return configs.periodic(n_cells=cells or 1 << 22, seed=4 + 100 * rank, threads=threads)
     if workload == "batched":
         return configs.batched(total=cells or 1 << 22, seed=1 + 100 * rank, threads=threads)
+    if workload == "scatter":
+        return configs.scatter(n_cells=cells or 1 << 20, seed=3 + 100 * rank, threads=threads)
     raise ValueError(workload)
 
 
@@ -275,10 +279,11 @@ def run_ours(args, dist: Dist):
     ctx.set_directions(p.omega, p.weight)
     ka = torch.from_numpy(p.kappa_abs).cuda()
     em = torch.from_numpy(p.emissivity).cuda()
-    ctx.set_material(ka, em)
+    ks = None if p.kappa_scat is None else torch.from_numpy(p.kappa_scat).cuda()
+    ctx.set_material(ka, em, kappa_scat=ks)
     J = torch.empty((N, G), dtype=torch.float64, device="cuda")
     Gm = torch.empty_like(J)
-    opts = default_opts(precision=32, relevel=1, tol_pbc=1e-6, max_it_pbc=200)
+    opts = default_opts(precision=32, relevel=1, tol_pbc=1e-6, max_it_pbc=200, tol_scat=1e-6, max_it_scat=200)
     for _ in range(args.warmup):
         ctx.solve_dev(J, Gm, opts)
     torch.cuda.synchronize()
@@ -291,7 +296,7 @@ def run_ours(args, dist: Dist):
     dist.barrier()
     ev0.record(stream)
     agg = {"updates": 0.0, "sweep_ms": 0.0, "sweeps": 0, "launches": 0, "classify_ms": 0.0, "levelise_ms": 0.0,
-           "it_pbc": [], "defect": [], "res_pbc": []}
+           "it_pbc": [], "it_scat": [], "defect": [], "res_pbc": []}
     for _ in range(args.steps):
         st, s = ctx.solve_dev(J, Gm, opts)
         agg["updates"] += st["updates"]
@@ -301,6 +306,7 @@ def run_ours(args, dist: Dist):
         agg["classify_ms"] += st["t_classify_ms"]
         agg["levelise_ms"] += st["t_levelise_ms"]
         agg["it_pbc"].append(st["it_pbc"])
+        agg["it_scat"].append(st["it_scat"])
         agg["defect"].append(st["defect"])
         agg["res_pbc"].append(st["res_pbc"])
         last = st
@@ -350,15 +356,16 @@ def run_ours(args, dist: Dist):
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
         hv, hfc, har, hnr, hfl = pin(m.volume), pin(m.face_cells), pin(m.area), pin(m.normal), pin(m.flags)
         hom, hw, hka, hem = pin(p.omega), pin(p.weight), pin(p.kappa_abs), pin(p.emissivity)
-        h2d = sum(a.nbytes for a in (hv, hfc, har, hnr, hfl, hom, hw, hka, hem))
+        hks = None if p.kappa_scat is None else pin(p.kappa_scat)
+        h2d = sum(a.nbytes for a in (hv, hfc, har, hnr, hfl, hom, hw, hka, hem) + (() if hks is None else (hks,)))
         d2h = 2 * N * G * 8
         ctx2 = Context(dist.local, stream.cuda_stream)
-        o = default_opts(precision=32, tol_pbc=1e-6, max_it_pbc=200)
+        o = default_opts(precision=32, tol_pbc=1e-6, max_it_pbc=200, tol_scat=1e-6, max_it_scat=200)
 
         def e2e_step():
             ctx2.set_mesh(volume=hv, face_cells=hfc, area=har, normal=hnr, flags=hfl)
             ctx2.set_directions(hom, hw)
-            ctx2.set_material(hka, hem)
+            ctx2.set_material(hka, hem, kappa_scat=hks)
             return ctx2.solve(o)
 
         e2e_step()
@@ -393,7 +400,7 @@ def run_ours(args, dist: Dist):
                           "parallelism": "one independent box per GPU" if dist.world > 1 else "1 GPU"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": agg["launches"],
                "clocks": clk,
-               "solve": {"it_pbc": agg["it_pbc"], "defect_max": max(abs(x) for x in agg["defect"]),
+               "solve": {"it_pbc": agg["it_pbc"], "it_scat": agg["it_scat"], "defect_max": max(abs(x) for x in agg["defect"]),
                          "res_pbc": max(agg["res_pbc"]), "depth_max": last["depth_max"],
                          "depth_mean": last["depth_mean"], "classify_ms": agg["classify_ms"] / args.steps,
                          "levelise_ms": agg["levelise_ms"] / args.steps,
