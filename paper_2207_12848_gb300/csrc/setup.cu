@@ -562,9 +562,9 @@ __global__ void k_sort_levels(const uint32_t* raw, uint32_t* task, const uint32_
 // list is kept in shared memory (spilling to the direction's list in global memory when wide).
 // ---------------------------------------------------------------------------------------------
 constexpr int LD_THREADS = 1024;
-constexpr int LD_KL = 2;     // lanes per task
+constexpr int LD_KL = 4;     // lanes per task: one pass covers 32 face sides, so nearly every row takes one
 constexpr int LD_KU = 8;     // face sides per lane per pass
-constexpr int LD_Q = 4096;   // level-list entries {cell, row start, row end} held in shared memory
+constexpr int LD_Q = 8192;   // level-list entries {cell, row start, row end} held in shared memory (2 x 96 KB)
 constexpr size_t LD_SMEM = sizeof(uint32_t) * 3 * 2 * LD_Q;
 
 struct DirLevArgs {
