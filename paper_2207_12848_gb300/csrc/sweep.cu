@@ -627,9 +627,18 @@ __device__ __forceinline__ bool op_task(const SweepArgs& a, const OpPieces<LP>& 
 #pragma unroll
         for (int k = 0; k < NE; ++k) {  // issue every upwind read before using any
             if (has[k] && !sign_bit(w[k])) {
+                const float* src = I + (size_t)idx[k] * G;
+                if constexpr (GC == 4) {
+                    const float4 q4 = ld_relaxed_v4(src);
+                    v[k][0] = q4.x; v[k][1] = q4.y; v[k][2] = q4.z; v[k][3] = q4.w;
+                } else if constexpr (GC == 2) {
+                    const float2 q2 = ld_relaxed_v2(src);
+                    v[k][0] = q2.x; v[k][1] = q2.y;
+                } else {
 #pragma unroll
-                for (int g = 0; g < GM; ++g)
-                    if (g < G) v[k][g] = ld_relaxed(I + (size_t)idx[k] * G + g);
+                    for (int g = 0; g < GM; ++g)
+                        if (g < G) v[k][g] = ld_relaxed(src + g);
+                }
             }
         }
 #pragma unroll
@@ -658,12 +667,18 @@ __device__ __forceinline__ bool op_task(const SweepArgs& a, const OpPieces<LP>& 
     }
     if (valid && !overflow && gl == 0 && !fail) {
         float* out = reinterpret_cast<float*>(a.I) + (size_t)dst * G;
+        float val[GM];
 #pragma unroll
-        for (int g = 0; g < GM; ++g) {
-            if (g < G) {
-                const float val = __fdividef(q[g].x + acc[g], P + q[g].y);
-                st_relaxed(out + g, __uint_as_float(__float_as_uint(val) ^ par));
-            }
+        for (int g = 0; g < GM; ++g)
+            if (g < G) val[g] = __uint_as_float(__float_as_uint(__fdividef(q[g].x + acc[g], P + q[g].y)) ^ par);
+        if constexpr (GC == 4) {
+            st_relaxed_v4(out, make_float4(val[0], val[1], val[2], val[3]));
+        } else if constexpr (GC == 2) {
+            st_relaxed_v2(out, make_float2(val[0], val[1]));
+        } else {
+#pragma unroll
+            for (int g = 0; g < GM; ++g)
+                if (g < G) st_relaxed(out + g, val[g]);
         }
     }
     return !fail;
