@@ -268,7 +268,8 @@ def test_adjoint_dense_transpose():
 
 
 def test_adjoint_finite_differences():
-    p = configs.voronoi_small(256, n_dir=8, n_groups=2, seed=35)
+    # the 2^12-cell differentiation sub-mesh
+    p = configs.voronoi_small(4096, n_dir=8, n_groups=2, seed=35)
     rng = np.random.default_rng(4)
     T = rng.random(p.kappa_abs.shape) * 1e-3
 
