@@ -34,6 +34,9 @@ WORKLOADS = {
                "8 sources/mesh, 128 directions, 2 groups, one persistent launch",
     "scatter": "Voronoi mesh of 2^20 cells sampled ~rho (lognormal, P(k)~k^-3), albedo 0.5, 64 sources, "
                "96 directions, 4 groups, source iteration to relative change of J < 1e-6",
+    "adjoint": "Poisson-Voronoi mesh of 2^18 cells, lognormal kappa, 32 sources, 64 directions, 2 groups; "
+               "gradient of sum (Gamma - T)^2 in kappa and emissivity by the transposed sweep, forward "
+               "intensities recomputed",
 }
 
 
@@ -184,6 +187,8 @@ def make_problem(workload: str, rank: int, threads: int | None, cells: int | Non
         return configs.batched(total=cells or 1 << 22, seed=1 + 100 * rank, threads=threads)
     if workload == "scatter":
         return configs.scatter(n_cells=cells or 1 << 20, seed=3 + 100 * rank, threads=threads)
+    if workload == "adjoint":
+        return configs.adjoint(n_cells=cells or 1 << 18, seed=5 + 100 * rank, threads=threads)
     raise ValueError(workload)
 
 
@@ -413,6 +418,75 @@ def run_ours(args, dist: Dist):
         print(json.dumps(out))
 
 
+def run_adjoint(args, dist: Dist):
+    """The differentiation workload: each step is one adjoint call (forward intensities recomputed, then
+    the transposed sweep), timed with CUDA events; inputs resident on the device."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_2207_12848_gb300 import Context, default_opts
+
+    torch.cuda.set_device(dist.local)
+    __graft_entry__.build()
+    p = make_problem("adjoint", dist.rank, args.threads, args.cells)
+    stream = torch.cuda.current_stream()
+    N, D, G = p.mesh.n_cells, p.n_dir, p.n_groups
+    ctx = Context(dist.local, stream.cuda_stream)
+    ctx.set_mesh(p.mesh)
+    ctx.set_directions(p.omega, p.weight)
+    rng = np.random.default_rng(5)
+    ka_t = p.kappa_abs * (1.0 + 0.1 * rng.standard_normal(p.kappa_abs.shape)).clip(0.5, 1.5)
+    ctx.set_material(ka_t, p.emissivity)
+    _, T, _, _ = ctx.solve(precision=32)  # target: absorbed rate of the perturbed kappa
+    ka = torch.from_numpy(p.kappa_abs).cuda()
+    ctx.set_material(ka, torch.from_numpy(p.emissivity).cuda())
+    J = torch.empty((N, G), dtype=torch.float64, device="cuda")
+    Gm = torch.empty_like(J)
+    ctx.solve_dev(J, Gm, default_opts(precision=32))
+    dg = 2.0 * (Gm - torch.from_numpy(T).cuda())
+    gk, ge = torch.empty_like(J), torch.empty_like(J)
+    opts = default_opts(precision=32)
+    for _ in range(args.warmup):
+        ctx.adjoint_dev(gk, ge, None, dg, opts)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = Clocks(dist.local)
+    clocks.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    upd, sweep_ms, sweeps, launches = 0.0, 0.0, 0, 0
+    for _ in range(args.steps):
+        st = ctx.adjoint_dev(gk, ge, None, dg, opts)
+        upd += st["updates"]
+        sweep_ms += st["t_sweep_ms"]
+        sweeps += st["n_sweeps"]
+        launches += st["kernel_launches"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    clk = clocks.stop()
+    value, tmax = aggregate(dist, elapsed, upd)
+    if dist.rank != 0:
+        return
+    bpu, fbar = bytes_per_update(p)
+    peaks = measured_peaks()
+    avg = sweep_ms / max(1, sweeps) / 1e3
+    achieved = bpu * N * D * G / avg / 1e9
+    print(json.dumps({"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": dist.world, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": WORKLOADS["adjoint"], "n_cells": N, "n_dir": D, "n_groups": G,
+                                 "step": "one adjoint call: forward recompute + transposed sweep + FP64 gradients"},
+                      "roofline": {"bound": "hbm", "kernel": "k_sweep (reverse, lane groups)", "achieved": achieved,
+                                   "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                                   "peak_source": peaks["source"], "traffic": None, "bytes_per_update": bpu,
+                                   "avg_launch_ms": avg * 1e3},
+                      "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clk}))
+
+
 def run_profile_case(args):
     """Small fixed case for ncu captures: one solve with two sweeps, no autotuning, no extras."""
     import torch
@@ -461,6 +535,8 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, dist)
+        elif args.workload == "adjoint":
+            run_adjoint(args, dist)
         else:
             run_ours(args, dist)
     finally:

@@ -383,3 +383,37 @@ def test_iteration_graphs_match_the_host_loop(ctx, kind):
     assert sg["t_sweep_ms"] > 0  # sweep time from the event nodes inside the graphs
     r = run_oracle(p)
     assert fp32_err(Jg, r["J"]) <= FP32_TOL
+
+
+def test_adjoint_against_central_differences(ctx):
+    # the GPU's FP64 adjoint against FP64 central differences of the GPU's own solve, on the 2^12-cell
+    # differentiation sub-mesh, loss sum (Gamma - T)^2
+    p = configs.voronoi_small(4096, n_dir=8, n_groups=2, seed=36, n_src=6)
+    load(ctx, p)
+    T = np.random.default_rng(37).random(p.kappa_abs.shape) * 1e-3
+
+    def loss(ka, em):
+        ctx.set_material(ka, em)
+        _, Gm, _, _ = ctx.solve(precision=64)
+        return math.fsum(((Gm - T) ** 2).ravel()), Gm
+
+    L0, G0 = loss(p.kappa_abs, p.emissivity)
+    gk, ge, _ = ctx.adjoint(dl_dGamma=2 * (G0 - T), precision=64)
+    rng = np.random.default_rng(38)
+    big = np.argsort(np.abs(gk[:, 0]))[-40:]
+    for c in rng.choice(big, 4, replace=False):
+        for g in range(2):
+            h = 1e-4 * p.kappa_abs[c, g]
+            kp, km = p.kappa_abs.copy(), p.kappa_abs.copy()
+            kp[c, g] += h
+            km[c, g] -= h
+            fd = (loss(kp, p.emissivity)[0] - loss(km, p.emissivity)[0]) / (2 * h)
+            assert gk[c, g] == pytest.approx(fd, rel=1e-6, abs=1e-7 * np.abs(gk).max())
+            # emissivity must stay >= 0 (most cells have none): the loss is quadratic in it (Gamma is
+            # linear), so the one-sided three-point difference is exact up to rounding
+            he = 1e-4 * max(p.emissivity[c, g], 1.0)
+            e1, e2 = p.emissivity.copy(), p.emissivity.copy()
+            e1[c, g] += he
+            e2[c, g] += 2 * he
+            fde = (-3 * L0 + 4 * loss(p.kappa_abs, e1)[0] - loss(p.kappa_abs, e2)[0]) / (2 * he)
+            assert ge[c, g] == pytest.approx(fde, rel=1e-6, abs=1e-7 * np.abs(ge).max())
