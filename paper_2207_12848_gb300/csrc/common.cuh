@@ -75,6 +75,20 @@ __device__ __forceinline__ void st_relaxed_v2(float* p, float2 v) {
 __device__ __forceinline__ void st_relaxed_v4(float* p, float4 v) {
     asm volatile("st.relaxed.gpu.global.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w));
 }
+// relaxed accesses with an L2 eviction-priority hint (createpolicy), for values read again soon
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ float ld_relaxed_hint(const float* p, uint64_t pol) {
+    float v;
+    asm volatile("ld.relaxed.gpu.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_hint(float* p, float v, uint64_t pol) {
+    asm volatile("st.relaxed.gpu.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol));
+}
 __device__ __forceinline__ void st_relaxed(float* p, float v) {
     asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v));
 }

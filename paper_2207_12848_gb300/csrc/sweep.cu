@@ -855,6 +855,7 @@ __global__ void __launch_bounds__(256, SWEEP_REC_MINB) k_sweep_op1(SweepArgs a) 
 // of an iteration (line loads, prefetch, header shuffles, loop control, the overflow vote) is shared
 // by twice as many tasks as in k_sweep_op1, and each lane has up to four upwind reads in flight.
 // The 8 tasks of a step lie in one level (levels are padded to 32 tasks), so they are independent.
+// Operator lines stream through L2 marked evict-first, intensities are read and written evict-last.
 __global__ void __launch_bounds__(256, SWEEP_REC_MINB) k_sweep_op2(SweepArgs a) {
     extern __shared__ float4 s_om[];
     for (int i = threadIdx.x; i < a.nd; i += blockDim.x) s_om[i] = a.om32[i];
@@ -865,6 +866,7 @@ __global__ void __launch_bounds__(256, SWEEP_REC_MINB) k_sweep_op2(SweepArgs a) 
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nsteps = a.n_chunks * 4;  // steps of 8 tasks
     const uint64_t pol = policy_evict_first();
+    const uint64_t keep = policy_evict_last();  // intensities: each is read again by ~8 downwind tasks
     const float* I = reinterpret_cast<const float*>(a.I);
     const float2* cm = reinterpret_cast<const float2*>(a.cm);
     const uint32_t par = a.parity ? 0x80000000u : 0u;
@@ -910,10 +912,10 @@ __global__ void __launch_bounds__(256, SWEEP_REC_MINB) k_sweep_op2(SweepArgs a) 
             const bool hb0 = workb && j0 < ninb, hb1 = workb && j0 + 1 < ninb;
             const bool ia0 = ha0 && ca.y >= 0, ia1 = ha1 && ca.w >= 0;  // sign bit clear: interior entry
             const bool ib0 = hb0 && cb.y >= 0, ib1 = hb1 && cb.w >= 0;
-            const float xa0 = ia0 ? ld_relaxed(I + (uint32_t)ca.x) : 0.f;
-            const float xa1 = ia1 ? ld_relaxed(I + (uint32_t)ca.z) : 0.f;
-            const float xb0 = ib0 ? ld_relaxed(I + (uint32_t)cb.x) : 0.f;
-            const float xb1 = ib1 ? ld_relaxed(I + (uint32_t)cb.z) : 0.f;
+            const float xa0 = ia0 ? ld_relaxed_hint(I + (uint32_t)ca.x, keep) : 0.f;
+            const float xa1 = ia1 ? ld_relaxed_hint(I + (uint32_t)ca.z, keep) : 0.f;
+            const float xb0 = ib0 ? ld_relaxed_hint(I + (uint32_t)cb.x, keep) : 0.f;
+            const float xb1 = ib1 ? ld_relaxed_hint(I + (uint32_t)cb.z, keep) : 0.f;
             auto term = [&](bool in, bool has, float x, uint32_t idx, int wbits, int bit, int z) -> float {
                 const float w = __int_as_float(wbits);
                 if (in) {
@@ -937,11 +939,11 @@ __global__ void __launch_bounds__(256, SWEEP_REC_MINB) k_sweep_op2(SweepArgs a) 
             float* out = reinterpret_cast<float*>(a.I);
             if (worka) {
                 const float v = __fdividef(qa.x + acca, __int_as_float(ca.y) + qa.y);
-                st_relaxed(out + (uint32_t)ca.w, __uint_as_float(__float_as_uint(v) ^ par));
+                st_relaxed_hint(out + (uint32_t)ca.w, __uint_as_float(__float_as_uint(v) ^ par), keep);
             }
             if (workb) {
                 const float v = __fdividef(qb.x + accb, __int_as_float(cb.y) + qb.y);
-                st_relaxed(out + (uint32_t)cb.w, __uint_as_float(__float_as_uint(v) ^ par));
+                st_relaxed_hint(out + (uint32_t)cb.w, __uint_as_float(__float_as_uint(v) ^ par), keep);
             }
         }
         if (__any_sync(0xffffffffu, overa || overb)) {  // a failed wait inside sets the error word
