@@ -778,19 +778,12 @@ __global__ void k_gather_levels(const uint32_t* dlist, const int32_t* dcnt, cons
 //                weight with its sign bit set; boundary face b: index b into the boundary inflow,
 //                weight with its sign bit set and the entry's bit set in the boundary mask.
 //                Unused entries are {0, 0}.
-__global__ void k_build_op(const int4* trec, int64_t n, const uint32_t* rowptr, const int4* side, const d4* side64,
-                           const float4* side_lo, const float4* om32, const float4* om32lo, const double* om64,
-                           uint32_t cmask, int cshift, uint32_t N, int4* op) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int4 tr = trec[i];
-    int4* line = op + i * 8;
+// One task's line built by one thread: rows longer than 32 sides (inflow mask plus classification of
+// the sides past 32), and the reference form of the assembly.
+__device__ void build_line_serial(const int4 tr, int4* line, const uint32_t* rowptr, const int4* side, const d4* side64,
+                                  const float4* side_lo, const float4* om32, const float4* om32lo, const double* om64,
+                                  uint32_t cmask, int cshift, uint32_t N) {
     int2* E = reinterpret_cast<int2*>(line + 1);
-    if ((uint32_t)tr.x == TASK_PAD) {
-        line[0] = make_int4((int)TASK_PAD, 0, 0, 0);
-        for (int j = 0; j < OP_MAX; ++j) E[j] = make_int2(0, 0);
-        return;
-    }
     const uint32_t c = (uint32_t)tr.x & cmask, dl = (uint32_t)tr.x >> cshift;
     const uint32_t slab = dl * N;
     const uint32_t r0 = (uint32_t)tr.y;
@@ -831,13 +824,69 @@ __global__ void k_build_op(const int4* trec, int64_t n, const uint32_t* rowptr, 
     line[0] = make_int4(tr.x, tr.z & 0x7fffffff, (nin < 255 ? nin : 255) | (int)(bmask << 16), (int)(slab + c));
 }
 
+// 8 lanes per task: lane 0 writes the header, lane g >= 1 the entries 2g-2 and 2g-1 (the (2g-2)-th and
+// (2g-1)-th inflow sides of the row in row order), so the side loads of a row run in parallel and the
+// 128-byte line is one coalesced store of the group. Rows longer than 32 sides take the serial form.
+__global__ void __launch_bounds__(256) k_build_op(const int4* trec, int64_t n, const uint32_t* rowptr, const int4* side,
+                                                  const d4* side64, const float4* side_lo, const float4* om32,
+                                                  const float4* om32lo, const double* om64, uint32_t cmask, int cshift,
+                                                  uint32_t N, int4* op) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;  // task
+    const int gl = threadIdx.x & 7;
+    const unsigned gmask = 0xffu << (threadIdx.x & 24);  // the 8 lanes of this task
+    if (i >= n) return;  // a whole group at a time
+    const int4 tr = trec[i];
+    int4* line = op + i * 8;
+    if ((uint32_t)tr.x == TASK_PAD) {
+        line[gl] = gl == 0 ? make_int4((int)TASK_PAD, 0, 0, 0) : make_int4(0, 0, 0, 0);
+        return;
+    }
+    if (tr.z < 0) {
+        if (gl == 0) build_line_serial(tr, line, rowptr, side, side64, side_lo, om32, om32lo, om64, cmask, cshift, N);
+        return;
+    }
+    const uint32_t c = (uint32_t)tr.x & cmask, dl = (uint32_t)tr.x >> cshift;
+    const uint32_t slab = dl * N;
+    const uint32_t r0 = (uint32_t)tr.y;
+    const uint32_t inm = (uint32_t)tr.w;
+    const int nin = __popc(inm);
+    int2 ent[2] = {make_int2(0, 0), make_int2(0, 0)};
+    uint32_t bm = 0;
+    if (gl > 0) {
+        const float4 om = om32[dl], oml = om32lo[dl];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int j = 2 * gl - 2 + k;
+            if (j >= nin || j >= OP_MAX) continue;
+            uint32_t m = inm;
+            for (int q = 0; q < j; ++q) m &= m - 1;  // the j-th inflow side
+            const uint32_t s = r0 + (uint32_t)(__ffs(m) - 1);
+            const int4 r = side[s];
+            const float w = side_weight(r, side_lo[s], om, oml);
+            if (r.x >= 0 && !(r.x & NBR_PERIODIC)) {
+                ent[k] = make_int2((int)(slab + (uint32_t)r.x), __float_as_int(w));
+            } else if (r.x >= 0) {
+                ent[k] = make_int2((int)(slab + (uint32_t)(r.x & NBR_MASK)), __float_as_int(-w));
+            } else {
+                ent[k] = make_int2(-1 - r.x, __float_as_int(-w));
+                bm |= 1u << j;
+            }
+        }
+    }
+    bm |= __shfl_xor_sync(gmask, bm, 1);
+    bm |= __shfl_xor_sync(gmask, bm, 2);
+    bm |= __shfl_xor_sync(gmask, bm, 4);
+    line[gl] = gl == 0 ? make_int4(tr.x, tr.z & 0x7fffffff, nin | (int)(bm << 16), (int)(slab + c))
+                       : make_int4(ent[0].x, ent[0].y, ent[1].x, ent[1].y);
+}
+
 }  // namespace
 
 cudaError_t build_operator(const DevMesh& m, const Levels& L, const double* om64_all, const float4* om32_all,
                            const float4* om32lo_all, cudaStream_t st) {
     const int64_t n = L.h_lev_chunk.empty() ? 0 : L.h_lev_chunk.back() * 32;
     if (n > 0)
-        k_build_op<<<nblk(n), 256, 0, st>>>(L.trec, n, m.rowptr, m.side, m.side64, m.side_lo, om32_all + L.d0,
+        k_build_op<<<nblk(n * 8), 256, 0, st>>>(L.trec, n, m.rowptr, m.side, m.side64, m.side_lo, om32_all + L.d0,
                                             om32lo_all + L.d0, om64_all + 3 * (int64_t)L.d0, L.cmask, L.cshift,
                                             (uint32_t)m.N, L.op);
     return cudaGetLastError();
