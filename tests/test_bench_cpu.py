@@ -1,0 +1,46 @@
+"""Host logic of bench.py that needs no GPU: the algorithmic bytes per update of the roofline, and the
+rule that a recorded DRAM-traffic figure is only used while the kernel sources it was measured on are
+unchanged."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from synth import configs  # noqa: E402
+from synth.mesh import lattice_mesh  # noqa: E402
+
+
+@pytest.mark.parametrize("periodic,G", [(True, 1), (True, 4), (False, 2)])
+def test_bytes_per_update_on_a_lattice(periodic, G):
+    # an n^3 lattice has 6 face sides per cell either way: periodic faces have two sides, and with
+    # vacuum walls each of the 6n^2 boundary faces has one side and the interior faces two
+    n = 6
+    m = lattice_mesh(n, periodic=periodic)
+    p = configs.Problem("lattice", m, np.zeros((1, 3)), np.ones(1), np.ones((m.n_cells, G)),
+                        np.zeros((m.n_cells, G)))
+    bpu, fbar = bench.bytes_per_update(p)
+    sides = 6 * n ** 3
+    assert fbar == pytest.approx(sides / n ** 3)
+    assert bpu == pytest.approx((8.0 + 16.0 * fbar) / G + 12.0)
+
+
+def test_traffic_figure_follows_the_kernel_sources(tmp_path, monkeypatch):
+    summary = tmp_path / "traffic.txt"
+    summary.write_text("kernel_sha: %s\ntraffic_bytes_per_launch: 12345\n" % bench.kernel_sha())
+    monkeypatch.setattr(bench, "PROFILE_SUMMARY", str(summary))
+    assert bench.profiled_traffic("periodic") == 12345.0
+    assert bench.profiled_traffic("batched") is None  # measured on the periodic box only
+    summary.write_text("kernel_sha: 0000000000000000\ntraffic_bytes_per_launch: 12345\n")
+    assert bench.profiled_traffic("periodic") is None  # sources changed since the capture
+
+
+def test_single_rank_aggregate():
+    d = bench.Dist()
+    assert d.world == 1
+    v, t = bench.aggregate(d, 2.0, 10.0)
+    assert (v, t) == (5.0, 2.0)
