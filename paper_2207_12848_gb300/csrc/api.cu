@@ -69,6 +69,7 @@ struct sweep_ctx {
     // autotuner: schedule and block size per (precision, G)
     int tuned[2][9][2][4] = {};  // [precision][groups][operator mode] -> schedule, threads, lanes, blocks/SM
     int64_t launches = 0;  // kernels launched by this context
+    PeriodicTable ptab;          // periodic-inflow weights, rebuilt at the start of each periodic solve
     cudaStream_t gst = nullptr;  // capture/replay stream of the iteration graphs
     void* hpin = nullptr;        // pinned host words the iteration graphs write
 };
@@ -430,7 +431,7 @@ sweep_status graph_loop(sweep_ctx* c, const sweep_opts& o, int prec, const void*
             double* jw = (t & 1) ? jA : jB;
             if ((e = cudaMemsetAsync(c->dmax, 0, sizeof(unsigned long long), gs))) return e;
             if ((e = launch_periodic_source(prec, c->mesh, b.I[cur], G, D, c->om64, c->w64, jw, jr, c->dmax,
-                                            c->partial, nblk, gs)))
+                                            c->partial, nblk, gs, &c->ptab)))
                 return e;
             if ((e = launch_reduce_sum(c->partial, (int)c->mesh.n_pcells, c->red + 2, gs))) return e;
             if ((e = cudaMemcpyAsync(hp->red, c->red + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, gs))) return e;
@@ -577,6 +578,7 @@ sweep_status sweep_destroy(sweep_ctx* c) {
     dfree(c->J); dfree(c->Jold); dfree(c->Gam); dfree(c->jn); dfree(c->jn1);
     dfree(c->partial); dfree(c->red); dfree(c->dmax); dfree(c->bar); dfree(c->derr); dfree(c->scratch);
     dfree(c->stall_word);
+    dfree(c->ptab.off); dfree(c->ptab.wa);
     if (c->gst) cudaStreamDestroy(c->gst);
     if (c->hpin) cudaFreeHost(c->hpin);
     delete c;
@@ -1005,6 +1007,9 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     // the periodic inflow of the first sweep: the previous solve's intensities or zeros
     int prev = -1;
     if (has_pbc) {
+        c->ptab.ready = false;
+        CK(build_periodic_table(c->mesh, D, c->om64, c->w64, &c->ptab, c->st), "periodic weights");
+        c->launches += 3;
         if (o.warm_start && b.last >= 0) prev = b.last;
         else {
             prev = b.last >= 0 ? b.last : 1;
@@ -1015,7 +1020,7 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
         if (o.warm_start && b.last >= 0) {
             CK(cudaMemsetAsync(c->dmax, 0, sizeof(unsigned long long), c->st), "init");
             CKL(launch_periodic_source(prec, c->mesh, b.I[prev], G, D, c->om64, c->w64, c->jn1, c->jn, c->dmax,
-                                      c->partial, nblk, c->st), "periodic source");
+                                      c->partial, nblk, c->st, &c->ptab), "periodic source");
             std::swap(c->jn, c->jn1);
         }
     }
@@ -1099,7 +1104,7 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
         cudaEventRecord(u0, c->st);
         CK(cudaMemsetAsync(c->dmax, 0, sizeof(unsigned long long), c->st), "init");
         CKL(launch_periodic_source(prec, c->mesh, b.I[cur], G, D, c->om64, c->w64, c->jn1, c->jn, c->dmax, c->partial,
-                                  nblk, c->st), "periodic source");
+                                  nblk, c->st, &c->ptab), "periodic source");
         CKL(launch_reduce_sum(c->partial, (int)c->mesh.n_pcells, c->red + 2, c->st), "reduce");
         cudaEventRecord(u1, c->st);
         res_pbc = read_max(c);

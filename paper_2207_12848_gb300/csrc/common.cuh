@@ -340,9 +340,20 @@ cudaError_t launch_boundary_tally(int precision, const DevMesh& m, const void* I
                                   int nblk, cudaStream_t st);
 cudaError_t launch_scat_residual(int64_t NG, const double* J, double* Jold, unsigned long long* d_max,
                                  cudaStream_t st);
+// FP64 periodic-inflow weights of a solve (periodic sides of the periodic cells x directions)
+struct PeriodicTable {
+    int32_t* off = nullptr;   // [n_pcells+1] first periodic side of each periodic cell, then scratch counts
+    size_t off_cap = 0;
+    double* wa = nullptr;     // [periodic sides][nd] w_d A |n.Omega| on inflow sides, else 0
+    size_t wa_cap = 0;
+    bool ready = false;
+};
+cudaError_t build_periodic_table(const DevMesh& m, int nd, const double* om64, const double* w64, PeriodicTable* t,
+                                 cudaStream_t st);
 cudaError_t launch_periodic_source(int precision, const DevMesh& m, const void* I, int G, int nd,
                                    const double* om64, const double* w64, double* jn1, const double* jn,
-                                   unsigned long long* d_max, double* partial, int nblk, cudaStream_t st);
+                                   unsigned long long* d_max, double* partial, int nblk, cudaStream_t st,
+                                   const PeriodicTable* tab = nullptr);
 cudaError_t launch_reduce_sum(const double* partial, int n, double* out, cudaStream_t st);
 cudaError_t launch_grad_accum(int precision, const void* I, const void* lam, int64_t N, int G, int nd, int d0,
                               const double* w64, const double* vol, const double* dl_dG, double* gk, double* ge,

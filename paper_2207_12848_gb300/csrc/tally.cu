@@ -196,6 +196,113 @@ __global__ void __launch_bounds__(ROW_THREADS) k_periodic_source(const int32_t* 
     }
 }
 
+// Periodic-inflow weight table, fixed for a solve: for every periodic side of every periodic cell (in
+// row order) and every direction, w_d A |n.Omega| in FP64 where the side is an inflow side, else 0.
+// Built once per solve; each iteration then needs one FP64 multiply-add per inflow side and direction
+// instead of recomputing n.Omega and the weight on this part's narrow FP64 pipe.
+__global__ void k_pside_count(const int32_t* pcells, int64_t np, const uint32_t* rowptr, const int4* side,
+                              int32_t* cnt) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= np) return;
+    const int32_t c = pcells[k];
+    int n = 0;
+    for (uint32_t s = rowptr[c]; s < rowptr[c + 1]; ++s) {
+        const int32_t x = side[s].x;
+        if (x >= 0 && (x & NBR_PERIODIC)) ++n;
+    }
+    cnt[k] = n;
+}
+
+// exclusive scan of n counts by one block of 1024 threads; off[n] = total
+__global__ void k_scan_counts(const int32_t* cnt, int64_t n, int32_t* off) {
+    __shared__ int32_t s_sum[1024];
+    const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t i0 = threadIdx.x * per;
+    int32_t loc = 0;
+    for (int64_t i = i0; i < i0 + per && i < n; ++i) loc += cnt[i];
+    s_sum[threadIdx.x] = loc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t run = 0;
+        for (int t = 0; t < (int)blockDim.x; ++t) {
+            const int32_t v = s_sum[t];
+            s_sum[t] = run;
+            run += v;
+        }
+        off[n] = run;
+    }
+    __syncthreads();
+    int32_t run = s_sum[threadIdx.x];
+    for (int64_t i = i0; i < i0 + per && i < n; ++i) {
+        off[i] = run;
+        run += cnt[i];
+    }
+}
+
+__global__ void __launch_bounds__(ROW_THREADS) k_pside_weights(const int32_t* pcells, const int32_t* off,
+                                                               const uint32_t* rowptr, const int4* side,
+                                                               const d4* side64, int nd, const double* om64,
+                                                               const double* w64, double* wa) {
+    const int64_t k = blockIdx.x;
+    const int32_t c = pcells[k];
+    const uint32_t r0 = rowptr[c], r1 = rowptr[c + 1];
+    for (int d = threadIdx.x; d < nd; d += ROW_THREADS) {
+        int64_t j = off[k];
+        for (uint32_t s = r0; s < r1; ++s) {
+            const int32_t x = side[s].x;
+            if (x < 0 || !(x & NBR_PERIODIC)) continue;
+            const d4 n = side64[s];
+            const double t = exact_t(n, om64 + 3 * d);
+            wa[j * nd + d] = t < 0.0 ? dmul(w64[d], dmul(n.w, fabs(t))) : 0.0;
+            ++j;
+        }
+    }
+}
+
+// k_periodic_source with the weights from the table (same sums in the same order)
+template <typename real>
+__global__ void __launch_bounds__(ROW_THREADS) k_periodic_source_tab(const int32_t* pcells, const int32_t* off,
+                                                                     const uint32_t* rowptr, const int4* side,
+                                                                     const double* wa, const real* I, int64_t N, int G,
+                                                                     int nd, double* jn1, const double* jn,
+                                                                     unsigned long long* dmax, double* partial) {
+    __shared__ double sh[ROW_THREADS / 32];
+    const int64_t k = blockIdx.x;
+    const int32_t c = pcells[k];
+    const uint32_t r0 = rowptr[c], r1 = rowptr[c + 1];
+    double j[8];
+    for (int g = 0; g < 8; ++g) j[g] = 0.0;
+    for (int d = threadIdx.x; d < nd; d += ROW_THREADS) {
+        int64_t q = off[k];
+        for (uint32_t s = r0; s < r1; ++s) {
+            const int32_t nbr = side[s].x;
+            if (nbr < 0 || !(nbr & NBR_PERIODIC)) continue;
+            const double w = wa[q * nd + d];
+            ++q;
+            if (w == 0.0) continue;  // not an inflow side for this direction
+            const size_t base = ((size_t)d * N + (uint32_t)(nbr & NBR_MASK)) * G;
+            for (int g = 0; g < G; ++g) j[g] = dadd(j[g], dmul(w, mag(I + base + g)));
+        }
+    }
+    double esum = 0.0, emax = 0.0;
+    for (int g = 0; g < G; ++g) {
+        const double jt = block_sum_fixed(j[g], sh);
+        if (threadIdx.x == 0) {
+            const size_t i = (size_t)c * G + g;
+            const double s = jt + jn[i];
+            const double e = s > 0.0 ? fabs(jt - jn[i]) / s : 0.0;
+            jn1[i] = jt;
+            esum += e;
+            if (e > emax) emax = e;
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (emax > 0.0) atomicMax(dmax, (unsigned long long)__double_as_longlong(emax));
+        partial[2 * k] = esum;
+        partial[2 * k + 1] = 0.0;
+    }
+}
+
 __global__ void k_scat_residual(int64_t NG, const double* J, double* Jold, unsigned long long* dmax) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= NG) return;
@@ -315,12 +422,55 @@ cudaError_t launch_scat_residual(int64_t NG, const double* J, double* Jold, unsi
     return cudaGetLastError();
 }
 
+cudaError_t build_periodic_table(const DevMesh& m, int nd, const double* om64, const double* w64, PeriodicTable* t,
+                                 cudaStream_t st) {
+    if (m.n_pcells <= 0) return cudaSuccess;
+    const int64_t np = m.n_pcells;
+    cudaError_t e;
+    if (t->off_cap < 2 * (np + 1)) {
+        if (t->off) cudaFree(t->off);
+        t->off = nullptr;
+        t->off_cap = 0;
+        if ((e = cudaMalloc(&t->off, sizeof(int32_t) * 2 * (np + 1)))) return e;
+        t->off_cap = 2 * (np + 1);
+    }
+    int32_t* cnt = t->off + (np + 1);
+    k_pside_count<<<nb(np), 256, 0, st>>>(m.pcells, np, m.rowptr, m.side, cnt);
+    k_scan_counts<<<1, 1024, 0, st>>>(cnt, np, t->off);
+    int32_t total = 0;
+    if ((e = cudaMemcpyAsync(&total, t->off + np, sizeof total, cudaMemcpyDeviceToHost, st))) return e;
+    if ((e = cudaStreamSynchronize(st))) return e;
+    const size_t need = (size_t)(total > 0 ? total : 1) * nd;
+    if (t->wa_cap < need) {
+        if (t->wa) cudaFree(t->wa);
+        t->wa = nullptr;
+        t->wa_cap = 0;
+        if ((e = cudaMalloc(&t->wa, sizeof(double) * need))) return e;
+        t->wa_cap = need;
+    }
+    k_pside_weights<<<(unsigned)np, ROW_THREADS, 0, st>>>(m.pcells, t->off, m.rowptr, m.side, m.side64, nd, om64, w64,
+                                                          t->wa);
+    t->ready = true;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_periodic_source(int precision, const DevMesh& m, const void* I, int G, int nd, const double* om64,
                                    const double* w64, double* jn1, const double* jn, unsigned long long* d_max,
-                                   double* partial, int nblk_, cudaStream_t st) {
+                                   double* partial, int nblk_, cudaStream_t st, const PeriodicTable* tab) {
     (void)nblk_;
     if (m.n_pcells <= 0) return cudaSuccess;
     const unsigned b = (unsigned)m.n_pcells;
+    if (tab && tab->ready) {
+        if (precision == 64)
+            k_periodic_source_tab<double><<<b, ROW_THREADS, 0, st>>>(m.pcells, tab->off, m.rowptr, m.side, tab->wa,
+                                                                     (const double*)I, m.N, G, nd, jn1, jn, d_max,
+                                                                     partial);
+        else
+            k_periodic_source_tab<float><<<b, ROW_THREADS, 0, st>>>(m.pcells, tab->off, m.rowptr, m.side, tab->wa,
+                                                                    (const float*)I, m.N, G, nd, jn1, jn, d_max,
+                                                                    partial);
+        return cudaGetLastError();
+    }
     if (precision == 64)
         k_periodic_source<double><<<b, ROW_THREADS, 0, st>>>(m.pcells, m.rowptr, m.side, m.side64, (const double*)I,
                                                              m.N, G, nd, om64, w64, jn1, jn, d_max, partial);
