@@ -427,7 +427,7 @@ cudaError_t build_periodic_table(const DevMesh& m, int nd, const double* om64, c
     if (m.n_pcells <= 0) return cudaSuccess;
     const int64_t np = m.n_pcells;
     cudaError_t e;
-    if (t->off_cap < 2 * (np + 1)) {
+    if (t->off_cap < (size_t)(2 * (np + 1))) {
         if (t->off) cudaFree(t->off);
         t->off = nullptr;
         t->off_cap = 0;
