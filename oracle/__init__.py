@@ -12,8 +12,8 @@ and solves the same linear systems directly on small meshes.
 Parity status per function (what pins it; see tests/test_oracle_pins.py):
   oracle_levels  -- pinned: brute-force longest paths, the Voronoi ordering invariant (Appendix A)
   oracle_solve   -- pinned: 1-D column closed form, photon conservation, dense LU solves
-                    (plain, scattering, periodic), uniform periodic fixed point, linearity,
-                    pure streaming
+                    (plain, scattering, periodic, both at once for the nested and the fused
+                    loops), uniform periodic fixed point, linearity, pure streaming
   oracle_adjoint -- pinned: central finite differences of oracle_solve, dense transposed solve,
                     reciprocity of the transport operator
 """
@@ -64,7 +64,7 @@ def _lib():
             lib.oracle_levels.argtypes = [I64, I64, P, P, P, P, P, I32, P, P, P, ctypes.c_int]
             lib.oracle_solve.restype = ctypes.c_int
             lib.oracle_solve.argtypes = [I64, I64, P, P, P, P, P, I32, P, P, I32, P, P, P, P, D, I32, D, I32, P,
-                                         ctypes.c_int, P, P, P, ctypes.POINTER(Stats)]
+                                         ctypes.c_int, ctypes.c_int, P, P, P, ctypes.POINTER(Stats)]
             lib.oracle_adjoint.restype = ctypes.c_int
             lib.oracle_adjoint.argtypes = [I64, I64, P, P, P, P, P, I32, P, P, I32, P, P, P, P, P, ctypes.c_int, P,
                                            P]
@@ -105,7 +105,7 @@ def levels(mesh, omega, threads: int = 1):
 
 def solve(mesh, omega, weight, kappa_abs, emissivity, kappa_scat=None, bc_inflow=None, tol_scat=1e-6,
           max_it_scat=100, tol_pbc=1e-6, max_it_pbc=100, prev_init=None, threads: int = 1,
-          want_intensity: bool = False):
+          want_intensity: bool = False, fused: bool = False):
     """Mean intensity J[N,G], absorbed rate Gamma[N,G], stats (and I[D,N,G] if asked)."""
     om = _c(omega, np.float64).reshape(-1, 3)
     w = _c(weight, np.float64)
@@ -124,7 +124,8 @@ def solve(mesh, omega, weight, kappa_abs, emissivity, kappa_scat=None, bc_inflow
     I = np.zeros((D, N, G)) if want_intensity else None
     st = Stats()
     rc = _lib().oracle_solve(*margs, D, _ptr(om), _ptr(w), G, _ptr(ka), _ptr(ks), _ptr(em), _ptr(bc), tol_scat,
-                             max_it_scat, tol_pbc, max_it_pbc, _ptr(pi), threads, _ptr(J), _ptr(Gam), _ptr(I),
+                             max_it_scat, tol_pbc, max_it_pbc, _ptr(pi), int(fused), threads, _ptr(J), _ptr(Gam),
+                             _ptr(I),
                              ctypes.byref(st))
     out = {"rc": rc, "J": J, "Gamma": Gam, "stats": st.as_dict()}
     if want_intensity:

@@ -200,6 +200,35 @@ def test_dense_periodic_fixed_point():
     assert rel(r["J"], Jd) <= 1e-12
 
 
+@pytest.mark.parametrize("fused", [False, True])
+def test_dense_periodic_scattering_fixed_point(fused):
+    # both couplings at once: the nested loops and the fused loop (one source-iteration sweep per
+    # periodic iteration, Sec. 2.7) reach the same fixed point, the dense solve of the whole system
+    p = configs.voronoi_small(200, periodic_box=True, n_dir=6, n_groups=2, seed=29, scatter_albedo=0.5)
+    r = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, kappa_scat=p.kappa_scat,
+                     tol_scat=1e-15, max_it_scat=3000, tol_pbc=1e-15, max_it_pbc=5000, fused=fused)
+    assert r["rc"] == 0
+    _, Jd, Gd = dense.solve_coupled(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, p.kappa_scat)
+    assert rel(r["J"], Jd) <= 1e-12
+    assert rel(r["Gamma"], Gd) <= 1e-12
+    st = r["stats"]
+    if fused:
+        # one sweep per periodic iteration
+        assert st["it_scat"] == st["it_pbc"]
+    else:
+        assert st["it_scat"] > st["it_pbc"]
+
+
+def test_fused_loop_needs_both_couplings():
+    # with only one coupling present the fused option changes nothing, sweep for sweep
+    for box, alb in ((True, 0.0), (False, 0.5)):
+        p = configs.voronoi_small(150, periodic_box=box, n_dir=6, n_groups=1, seed=31, scatter_albedo=alb)
+        ks = p.kappa_scat if alb else None
+        a = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, kappa_scat=ks, fused=False)
+        b = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, kappa_scat=ks, fused=True)
+        assert np.array_equal(a["J"], b["J"]) and a["stats"] == b["stats"]
+
+
 def test_uniform_periodic_fixed_point():
     # eps_c = C kappa_a,c V_c with closed cells: I = C/(4pi) in every direction solves the balance
     p = configs.voronoi_small(300, periodic_box=True, n_dir=8, seed=27)
