@@ -12,6 +12,7 @@ weak scaling, no data-path collective.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -34,6 +35,9 @@ WORKLOADS = {
                "8 sources/mesh, 128 directions, 2 groups, one persistent launch",
     "scatter": "Voronoi mesh of 2^20 cells sampled ~rho (lognormal, P(k)~k^-3), albedo 0.5, 64 sources, "
                "96 directions, 4 groups, source iteration to relative change of J < 1e-6",
+    "periodic_scatter": "periodic Voronoi box, 2^20 cells sampled ~rho as in the periodic workload, 10^4 "
+                        "log-uniform sources, isotropic scattering with albedo 0.5, 128 directions, 1 group; "
+                        "scattering and periodic iterations to 1e-6, nested or fused (Sec. 2.7)",
     "adjoint": "Poisson-Voronoi mesh of 2^18 cells, lognormal kappa, 32 sources, 64 directions, 2 groups; "
                "gradient of sum (Gamma - T)^2 in kappa and emissivity by the transposed sweep, forward "
                "intensities recomputed",
@@ -187,9 +191,26 @@ def make_problem(workload: str, rank: int, threads: int | None, cells: int | Non
         return configs.batched(total=cells or 1 << 22, seed=1 + 100 * rank, threads=threads)
     if workload == "scatter":
         return configs.scatter(n_cells=cells or 1 << 20, seed=3 + 100 * rank, threads=threads)
+    if workload == "periodic_scatter":
+        p = configs.periodic(n_cells=cells or 1 << 20, seed=6 + 100 * rank, threads=threads)
+        return dataclasses.replace(p, name="periodic_scatter", kappa_scat=p.kappa_abs.copy())
     if workload == "adjoint":
         return configs.adjoint(n_cells=cells or 1 << 18, seed=5 + 100 * rank, threads=threads)
     raise ValueError(workload)
+
+
+def step_text(p, fused: int) -> str:
+    from synth.mesh import FACE_PERIODIC
+    pbc = bool((p.mesh.flags & FACE_PERIODIC).any())
+    scat = p.kappa_scat is not None and bool((p.kappa_scat != 0).any())
+    loops = []
+    if scat:
+        loops.append("source iteration to max|dJ|/J<=1e-6")
+    if pbc:
+        loops.append("periodic iteration to max|E|<1e-6")
+    it = " inside ".join(loops) if not (fused and pbc and scat) else \
+        "fused iteration (one sweep per periodic iteration) to both tolerances"
+    return "classify + levelise + " + (it or "one sweep")
 
 
 def bytes_per_update(p) -> float:
@@ -288,7 +309,8 @@ def run_ours(args, dist: Dist):
     ctx.set_material(ka, em, kappa_scat=ks)
     J = torch.empty((N, G), dtype=torch.float64, device="cuda")
     Gm = torch.empty_like(J)
-    opts = default_opts(precision=32, relevel=1, tol_pbc=1e-6, max_it_pbc=200, tol_scat=1e-6, max_it_scat=200)
+    opts = default_opts(precision=32, relevel=1, tol_pbc=1e-6, max_it_pbc=200, tol_scat=1e-6, max_it_scat=200,
+                        fused_loops=args.fused_loops)
     for _ in range(args.warmup):
         ctx.solve_dev(J, Gm, opts)
     torch.cuda.synchronize()
@@ -340,11 +362,12 @@ def run_ours(args, dist: Dist):
     extra = {}
     if dist.rank == 0 and not args.quick:
         # plain FP64 per-(direction, level) sweep, same mesh, one sweep; and FP32/FP64 batched single sweeps
-        o1 = default_opts(precision=32, max_it_pbc=1, tol_pbc=0.0)
+        one = dict(max_it_pbc=1, tol_pbc=0.0, max_it_scat=1, tol_scat=0.0)
+        o1 = default_opts(precision=32, **one)
         st32, _ = ctx.solve_dev(J, Gm, o1)
-        o64 = default_opts(precision=64, max_it_pbc=1, tol_pbc=0.0)
+        o64 = default_opts(precision=64, **one)
         st64, _ = ctx.solve_dev(J, Gm, o64)
-        op = default_opts(schedule="plain", max_it_pbc=1, tol_pbc=0.0)
+        op = default_opts(schedule="plain", **one)
         stp, _ = ctx.solve_dev(J, Gm, op)
         u1 = N * D * G
         extra["plain_fp64"] = {
@@ -365,7 +388,8 @@ def run_ours(args, dist: Dist):
         h2d = sum(a.nbytes for a in (hv, hfc, har, hnr, hfl, hom, hw, hka, hem) + (() if hks is None else (hks,)))
         d2h = 2 * N * G * 8
         ctx2 = Context(dist.local, stream.cuda_stream)
-        o = default_opts(precision=32, tol_pbc=1e-6, max_it_pbc=200, tol_scat=1e-6, max_it_scat=200)
+        o = default_opts(precision=32, tol_pbc=1e-6, max_it_pbc=200, tol_scat=1e-6, max_it_scat=200,
+                         fused_loops=args.fused_loops)
 
         def e2e_step():
             ctx2.set_mesh(volume=hv, face_cells=hfc, area=har, normal=hnr, flags=hfl)
@@ -401,7 +425,7 @@ def run_ours(args, dist: Dist):
                "config": {"workload": WORKLOADS[args.workload], "n_cells": N, "n_dir": D, "n_groups": G,
                           "face_sides_per_cell": round(fbar, 3), "precision": "FP32 intensities, FP64 tallies",
                           "l2": "no flush: >10 GB resident working set, 78x the 129 MB L2",
-                          "step": "classify + levelise + periodic iteration to max|E|<1e-6",
+                          "step": step_text(p, args.fused_loops), "fused_loops": args.fused_loops,
                           "parallelism": "one independent box per GPU" if dist.world > 1 else "1 GPU"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": agg["launches"],
                "clocks": clk,
@@ -521,6 +545,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the plain-FP64 comparison sweep")
+    ap.add_argument("--fused-loops", type=int, default=0, choices=[0, 1],
+                    help="with scattering and periodic faces: one sweep per periodic iteration (Sec. 2.7)")
     ap.add_argument("--profile-case", action="store_true", help="small fixed solve for ncu captures")
     ap.add_argument("--schedule", default="dataflow", choices=["level", "dataflow"])
     ap.add_argument("--lanes", type=int, default=8, choices=[1, 2, 4, 8, 16])

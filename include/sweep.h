@@ -75,8 +75,8 @@ typedef struct {
     int32_t relevel;      /* 1: redo classification and levelisation even if cached for this mesh+directions */
     int32_t block_threads;/* threads per block of the batched sweep (0 = autotuned) */
     int32_t use_graph;    /* 1 (default): run the periodic iteration or the source iteration as CUDA graphs, each
-                             distinct iteration captured once per solve and replayed (not with both loops on,
-                             the plain schedule or debug_stall, or when capture is refused: host loop) */
+                             distinct iteration captured once per solve and replayed (not with both loops
+                             nested, the plain schedule or debug_stall, or when capture is refused: host loop) */
     int64_t spin_budget;  /* bound on each device-side wait, in polls (0 = default, about 1 s) */
     int32_t debug_stall;  /* TEST ONLY: 1 makes the first sweep task wait on a word nothing writes */
     int32_t lanes_per_task; /* lanes cooperating on one task in the batched sweep: 1..16, a power of 2 (0 = autotuned);
@@ -84,6 +84,11 @@ typedef struct {
                                with two tasks per lane group (one group, dataflow schedule; else as 8) */
     int32_t geometry_only;  /* 1: the FP32 sweep reads the mesh every sweep instead of the assembled operator */
     int32_t blocks_per_sm;  /* resident blocks per SM of the batched sweep (0 = autotuned / maximum) */
+    int32_t fused_loops;    /* 1: with both scattering and periodic faces, fuse the two loops as Sec. 2.7 suggests:
+                               one source-iteration sweep per periodic iteration, J carried over between periodic
+                               iterations, stop when both changes are below tol_scat and tol_pbc (at most max_it_pbc
+                               sweeps). Same fixed point as the nested loops (0, default), far fewer sweeps.
+                               Ignored unless both loops are on. */
 } sweep_opts;
 
 typedef struct {

@@ -40,7 +40,7 @@ class sweep_opts(ctypes.Structure):
                 ("relevel", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("spin_budget", ctypes.c_int64), ("debug_stall", ctypes.c_int32),
                 ("lanes_per_task", ctypes.c_int32), ("geometry_only", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("fused_loops", ctypes.c_int32)]
 
 
 class sweep_stats(ctypes.Structure):

@@ -188,7 +188,7 @@ sweep_status ensure_common(sweep_ctx* c) {
         CK(cudaMalloc(&c->derr, sizeof(int)), "alloc");
         CK(cudaMalloc(&c->scratch, sizeof(int64_t) * 4), "alloc");
         CK(cudaMalloc(&c->red, sizeof(double) * 4), "alloc");
-        CK(cudaMalloc(&c->dmax, sizeof(unsigned long long)), "alloc");
+        CK(cudaMalloc(&c->dmax, 2 * sizeof(unsigned long long)), "alloc");  // [0] periodic or scattering, [1] scattering when fused
         CK(cudaMalloc(&c->stall_word, sizeof(double)), "alloc");
         CK(cudaMemset(c->stall_word, 0, sizeof(double)), "init");
     }
@@ -324,6 +324,7 @@ struct IterHost {
     int pad;
     unsigned long long dmax;
     double red[2];
+    unsigned long long dmax_scat;  // scattering change of a fused iteration
 };
 
 struct GraphSet {
@@ -378,13 +379,17 @@ struct LoopState {
     float t_sweep = 0.f, t_other = 0.f;
 };
 
-// Runs the iterations of a solve with exactly one of the two loops (periodic without scattering, or
-// scattering without periodic faces) as graphs. *done = false (nothing run) when the graphs cannot
-// be captured; the caller then runs the host loop from the same state.
+// Runs the iterations of a solve as graphs: with exactly one of the two loops (periodic without
+// scattering, or scattering without periodic faces), or with both fused (one source-iteration sweep per
+// periodic iteration). *done = false (nothing run) when the graphs cannot be captured; the caller then
+// runs the host loop from the same state.
 sweep_status graph_loop(sweep_ctx* c, const sweep_opts& o, int prec, const void* cm, const float* bc32, int sched,
                         int threads, int lanes, int bpsm, int nblk, LoopState& st, bool* done) {
     *done = false;
     const bool pbc = c->mesh.n_pcells > 0;
+    const bool scat = c->has_scat;
+    const bool fused = pbc && scat;
+    if (fused && !o.fused_loops) return SWEEP_OK;  // nested loops stay on the host
     SolveBuf& b = c->sb;
     const int64_t N = c->mesh.N;
     const int G = c->G, D = c->D;
@@ -411,7 +416,7 @@ sweep_status graph_loop(sweep_ctx* c, const sweep_opts& o, int prec, const void*
     auto enqueue = [&](int t, cudaEvent_t* ev) -> cudaError_t {
         cudaError_t e;
         const int cur = cur_of(t);
-        if (!pbc) {  // scattering source from the previous J (Alg. 1)
+        if (scat) {  // scattering source from the previous J (Alg. 1)
             if ((e = launch_prep_material(N, G, c->mesh.vol, c->ka, c->ks, c->em, c->Jold,
                                           prec == 32 ? c->cm32 : nullptr, prec == 64 ? c->cm64 : nullptr, gs)))
                 return e;
@@ -426,6 +431,17 @@ sweep_status graph_loop(sweep_ctx* c, const sweep_opts& o, int prec, const void*
         a.lanes = lanes;
         if ((e = launch_sweep(a, prec, c->sms * per_sm, threads, gs, &kid))) return e;
         if ((e = cudaEventRecordWithFlags(ev[1], gs, cudaEventRecordExternal))) return e;
+        if (scat) {
+            if ((e = launch_tally(prec, b.I[cur], N, G, D, 0, c->w64, c->wsum, c->mesh.vol, c->ka, c->em, c->J,
+                                  c->Gam, c->partial, nblk, gs)))
+                return e;
+            unsigned long long* ds = c->dmax + (fused ? 1 : 0);
+            if ((e = cudaMemsetAsync(ds, 0, sizeof(unsigned long long), gs))) return e;
+            if ((e = launch_scat_residual(NG, c->J, c->Jold, ds, gs))) return e;
+            if (fused && (e = cudaMemcpyAsync(&hp->dmax_scat, ds, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                              gs)))
+                return e;
+        }
         if (pbc) {
             double* jr = (t & 1) ? jB : jA;  // j of the previous iteration
             double* jw = (t & 1) ? jA : jB;
@@ -435,12 +451,6 @@ sweep_status graph_loop(sweep_ctx* c, const sweep_opts& o, int prec, const void*
                 return e;
             if ((e = launch_reduce_sum(c->partial, (int)c->mesh.n_pcells, c->red + 2, gs))) return e;
             if ((e = cudaMemcpyAsync(hp->red, c->red + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, gs))) return e;
-        } else {
-            if ((e = launch_tally(prec, b.I[cur], N, G, D, 0, c->w64, c->wsum, c->mesh.vol, c->ka, c->em, c->J,
-                                  c->Gam, c->partial, nblk, gs)))
-                return e;
-            if ((e = cudaMemsetAsync(c->dmax, 0, sizeof(unsigned long long), gs))) return e;
-            if ((e = launch_scat_residual(NG, c->J, c->Jold, c->dmax, gs))) return e;
         }
         if ((e = cudaEventRecordWithFlags(ev[2], gs, cudaEventRecordExternal))) return e;
         if ((e = cudaMemcpyAsync(&hp->err, c->derr, sizeof(int), cudaMemcpyDeviceToHost, gs))) return e;
@@ -460,7 +470,7 @@ sweep_status graph_loop(sweep_ctx* c, const sweep_opts& o, int prec, const void*
     cudaStreamWaitEvent(gs, fork, 0);
     cudaEventDestroy(fork);
     *done = true;
-    const int per_iter = pbc ? 3 : 4;  // kernels per iteration
+    const int per_iter = (pbc ? 3 : 1) + (scat ? 3 : 0);  // kernels per iteration
     for (int it = 0;; ++it) {
         const int t = it % period;
         CK(cudaGraphLaunch(gset.ex[t], gs), "graph launch");
@@ -489,6 +499,14 @@ sweep_status graph_loop(sweep_ctx* c, const sweep_opts& o, int prec, const void*
             std::swap(c->jn, c->jn1);
             st.prev = cur;
             st.cur = 1 - cur;
+            if (fused) {
+                memcpy(&st.res_scat, &hp->dmax_scat, sizeof st.res_scat);
+                st.conv_pbc = st.res_pbc < o.tol_pbc;
+                st.conv_scat = st.res_scat <= o.tol_scat;
+                if (st.conv_pbc && st.conv_scat) break;
+                if (st.it_pbc >= o.max_it_pbc) break;
+                continue;
+            }
             if (st.res_pbc < o.tol_pbc) { st.conv_pbc = true; break; }
             if (st.it_pbc >= o.max_it_pbc) { st.conv_pbc = false; break; }
         } else {
@@ -1038,9 +1056,11 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     cudaEventCreate(&u1);
     float t_other = 0.f;
     bool graphed = false;
-    if (o.use_graph && !plain && !o.debug_stall && has_pbc != c->has_scat) {
+    // Sec. 2.7's fused loops: one source-iteration sweep per periodic iteration, J carried over
+    const bool fused = o.fused_loops && has_pbc && c->has_scat;
+    if (o.use_graph && !plain && !o.debug_stall && (has_pbc != c->has_scat || fused)) {
         // what stays fixed over the iterations: the source without scattering, J_old before Alg. 1
-        if (has_pbc)
+        if (has_pbc && !fused)
             CKL(launch_prep_material(N, G, c->mesh.vol, c->ka, c->ks, c->em, nullptr, prec == 32 ? c->cm32 : nullptr,
                                     prec == 64 ? c->cm64 : nullptr, c->st), "prep");
         else
@@ -1069,7 +1089,7 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     }
     S.graph_used = graphed ? 1 : 0;
     for (; !graphed;) {
-        CK(cudaMemsetAsync(c->Jold, 0, sizeof(double) * NG, c->st), "init");
+        if (!fused || it_pbc == 0) CK(cudaMemsetAsync(c->Jold, 0, sizeof(double) * NG, c->st), "init");
         int it_scat = 0;
         for (;;) {
             CKL(launch_prep_material(N, G, c->mesh.vol, c->ka, c->ks, c->em, c->has_scat ? c->Jold : nullptr,
@@ -1095,6 +1115,10 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
             float tt = 0;
             cudaEventElapsedTime(&tt, u0, u1);
             t_other += tt;
+            if (fused) {
+                conv_scat = res_scat <= o.tol_scat;
+                break;
+            }
             if (res_scat <= o.tol_scat) { conv_scat = true; break; }
             if (it_scat >= o.max_it_scat) { conv_scat = false; break; }
         }
@@ -1118,6 +1142,11 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
         std::swap(c->jn, c->jn1);
         prev = cur;
         cur = 1 - cur;
+        if (fused) {
+            conv_pbc = res_pbc < o.tol_pbc;
+            if ((conv_pbc && conv_scat) || it_pbc >= o.max_it_pbc) break;
+            continue;
+        }
         if (res_pbc < o.tol_pbc) { conv_pbc = true; break; }
         if (it_pbc >= o.max_it_pbc) { conv_pbc = false; break; }
     }

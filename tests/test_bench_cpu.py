@@ -44,3 +44,13 @@ def test_single_rank_aggregate():
     assert d.world == 1
     v, t = bench.aggregate(d, 2.0, 10.0)
     assert (v, t) == (5.0, 2.0)
+
+
+def test_step_text_names_the_loops():
+    m = lattice_mesh(4, periodic=True)
+    one = np.ones((m.n_cells, 1))
+    p = configs.Problem("box", m, np.zeros((1, 3)), np.ones(1), one, 0 * one, kappa_scat=one)
+    assert "inside periodic iteration" in bench.step_text(p, 0)
+    assert "fused" in bench.step_text(p, 1)
+    q = configs.Problem("box", lattice_mesh(4), np.zeros((1, 3)), np.ones(1), one, 0 * one)
+    assert bench.step_text(q, 1).endswith("one sweep")

@@ -385,6 +385,49 @@ def test_iteration_graphs_match_the_host_loop(ctx, kind):
     assert fp32_err(Jg, r["J"]) <= FP32_TOL
 
 
+@pytest.mark.parametrize("precision", [32, 64])
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_fused_scattering_and_periodic_loops(ctx, precision, use_graph):
+    # Sec. 2.7's fused loops: one source-iteration sweep per periodic iteration, against the oracle's
+    # fused loop sweep for sweep, then converged against the nested loops' fixed point
+    p = configs.voronoi_small(4000, periodic_box=True, n_dir=12, n_groups=2, seed=47, scatter_albedo=0.5, n_src=8)
+    load(ctx, p)
+    J, Gm, st, s = ctx.solve(precision=precision, schedule="dataflow", tol_pbc=0.0, tol_scat=0.0, max_it_pbc=5,
+                             fused_loops=1, use_graph=use_graph)
+    r = run_oracle(p, tol_pbc=0.0, tol_scat=0.0, max_it_pbc=5, fused=True)
+    assert st["graph_used"] == use_graph
+    assert st["it_pbc"] == st["it_scat"] == st["n_sweeps"] == r["stats"]["it_pbc"] == r["stats"]["it_scat"] == 5
+    if precision == 64:
+        assert rel_max(J, r["J"]) <= 1e-12
+        assert st["res_pbc"] == pytest.approx(r["stats"]["res_pbc"], rel=1e-9)
+        assert st["res_scat"] == pytest.approx(r["stats"]["res_scat"], rel=1e-9)
+    else:
+        assert fp32_err(J, r["J"]) <= FP32_TOL
+    kw = dict(tol_pbc=1e-7, tol_scat=1e-8, max_it_pbc=400, max_it_scat=400)
+    Jf, Gf, sf, s = ctx.solve(precision=precision, fused_loops=1, use_graph=use_graph, **kw)
+    assert s == 0 and sf["res_pbc"] < 1e-7 and sf["res_scat"] <= 1e-8
+    r = run_oracle(p, fused=True, **kw)
+    assert sf["it_pbc"] == sf["it_scat"]
+    assert fp32_err(Jf, r["J"]) <= (1e-10 if precision == 64 else FP32_TOL)
+    assert abs(sf["defect"]) <= (1e-7 if precision == 64 else DEFECT_TOL)
+    Jn, _, sn, s = ctx.solve(precision=precision, fused_loops=0, **kw)
+    assert s == 0 and sn["n_sweeps"] > sf["n_sweeps"]
+    assert fp32_err(Jf, Jn) <= (1e-6 if precision == 64 else FP32_TOL)
+
+
+def test_fused_loops_graph_matches_the_host_loop(ctx):
+    p = configs.voronoi_small(4000, periodic_box=True, n_dir=12, n_groups=2, seed=93, scatter_albedo=0.5, n_src=8)
+    load(ctx, p)
+    Jg, Gg, sg, _ = ctx.solve(precision=32, schedule="dataflow", fused_loops=1, use_graph=1)
+    Jh, Gh, sh, _ = ctx.solve(precision=32, schedule="dataflow", fused_loops=1, use_graph=0)
+    assert sg["graph_used"] == 1 and sh["graph_used"] == 0
+    assert sg["n_sweeps"] == sh["n_sweeps"] and sg["it_pbc"] == sh["it_pbc"] == sg["it_scat"]
+    assert np.array_equal(Jg, Jh) and np.array_equal(Gg, Gh)
+    # the nested loops stay on the host loop
+    _, _, sn, _ = ctx.solve(precision=32, schedule="dataflow", fused_loops=0, use_graph=1)
+    assert sn["graph_used"] == 0
+
+
 def test_adjoint_against_central_differences(ctx):
     # the GPU's FP64 adjoint against FP64 central differences of the GPU's own solve, on the 2^12-cell
     # differentiation sub-mesh, loss sum (Gamma - T)^2
