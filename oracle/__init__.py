@@ -14,7 +14,8 @@ Parity status per function (what pins it; see tests/test_oracle_pins.py):
   oracle_solve   -- pinned: 1-D column closed form, photon conservation, dense LU solves
                     (plain, scattering, periodic, both at once for the nested and the fused
                     loops), uniform periodic fixed point, linearity, pure streaming
-  oracle_adjoint -- pinned: central finite differences of oracle_solve, dense transposed solve,
+  oracle_adjoint -- pinned: central finite differences of oracle_solve (also in kappa_scat, through
+                    the source iteration), dense transposed solve (also of the coupled system),
                     reciprocity of the transport operator
 """
 from __future__ import annotations
@@ -66,8 +67,8 @@ def _lib():
             lib.oracle_solve.argtypes = [I64, I64, P, P, P, P, P, I32, P, P, I32, P, P, P, P, D, I32, D, I32, P,
                                          ctypes.c_int, ctypes.c_int, P, P, P, ctypes.POINTER(Stats)]
             lib.oracle_adjoint.restype = ctypes.c_int
-            lib.oracle_adjoint.argtypes = [I64, I64, P, P, P, P, P, I32, P, P, I32, P, P, P, P, P, ctypes.c_int, P,
-                                           P]
+            lib.oracle_adjoint.argtypes = [I64, I64, P, P, P, P, P, I32, P, P, I32, P, P, P, P, P, P, D, I32,
+                                           ctypes.c_int, P, P, P, P]
             _LIB = lib
     return _LIB
 
@@ -136,18 +137,32 @@ def solve(mesh, omega, weight, kappa_abs, emissivity, kappa_scat=None, bc_inflow
 def adjoint(mesh, omega, weight, kappa_abs, emissivity, dl_dJ=None, dl_dGamma=None, bc_inflow=None,
             threads: int = 1):
     """Gradients (dL/dkappa_abs, dL/demissivity) [N,G] of a loss with the given dL/dJ and dL/dGamma."""
+    r = adjoint_full(mesh, omega, weight, kappa_abs, emissivity, dl_dJ=dl_dJ, dl_dGamma=dl_dGamma,
+                     bc_inflow=bc_inflow, threads=threads)
+    return r["rc"], r["grad_kappa_abs"], r["grad_emissivity"]
+
+
+def adjoint_full(mesh, omega, weight, kappa_abs, emissivity, kappa_scat=None, dl_dJ=None, dl_dGamma=None,
+                 bc_inflow=None, tol_scat=1e-6, max_it_scat=100, threads: int = 1):
+    """The adjoint with scattering (transposed source iteration): a dict with rc, the gradients in
+    kappa_abs, emissivity and kappa_scat [N,G], and the forward and transposed sweep counts."""
     om = _c(omega, np.float64).reshape(-1, 3)
     w = _c(weight, np.float64)
     N = mesh.n_cells
     ka = _c(kappa_abs, np.float64).reshape(N, -1)
     G = ka.shape[1]
     em = _c(emissivity, np.float64).reshape(N, G)
+    ks = None if kappa_scat is None else _c(kappa_scat, np.float64).reshape(N, G)
     dj = None if dl_dJ is None else _c(dl_dJ, np.float64).reshape(N, G)
     dg = None if dl_dGamma is None else _c(dl_dGamma, np.float64).reshape(N, G)
     bc = None if bc_inflow is None else _c(bc_inflow, np.float64)
     keep, margs = _mesh_args(mesh)
     gk = np.zeros((N, G))
     ge = np.zeros((N, G))
-    rc = _lib().oracle_adjoint(*margs, om.shape[0], _ptr(om), _ptr(w), G, _ptr(ka), _ptr(em), _ptr(bc), _ptr(dj),
-                               _ptr(dg), threads, _ptr(gk), _ptr(ge))
-    return rc, gk, ge
+    gs = np.zeros((N, G))
+    its = np.zeros(2, np.int32)
+    rc = _lib().oracle_adjoint(*margs, om.shape[0], _ptr(om), _ptr(w), G, _ptr(ka), _ptr(ks), _ptr(em), _ptr(bc),
+                               _ptr(dj), _ptr(dg), tol_scat, max_it_scat, threads, _ptr(gk), _ptr(ge), _ptr(gs),
+                               _ptr(its))
+    return {"rc": rc, "grad_kappa_abs": gk, "grad_emissivity": ge, "grad_kappa_scat": gs,
+            "it_forward": int(its[0]), "it_adjoint": int(its[1])}

@@ -67,6 +67,22 @@ def solve_direction(mesh, om, kappa_abs, emissivity, kappa_scat=None, bc_inflow=
     return I
 
 
+def coupled_matrix(mesh, omega, weight, kappa_t, kappa_scat, group, bc_inflow=None):
+    """The whole system of one group, all directions with the isotropic scattering coupling:
+    A [D*N, D*N] and the boundary part b of the right-hand side."""
+    D, N = omega.shape[0], mesh.n_cells
+    A = np.zeros((D * N, D * N))
+    b = np.zeros(D * N)
+    idx = np.arange(N)
+    for d in range(D):
+        L, bd = transport_matrix(mesh, omega[d], kappa_t, bc_inflow, group)
+        A[d * N:(d + 1) * N, d * N:(d + 1) * N] = L
+        b[d * N:(d + 1) * N] = bd
+        for d2 in range(D):
+            A[d * N + idx, d2 * N + idx] -= kappa_scat[:, group] * mesh.volume * weight[d2] / (4 * math.pi)
+    return A, b
+
+
 def solve_coupled(mesh, omega, weight, kappa_abs, emissivity, kappa_scat=None, bc_inflow=None):
     """All directions at once with isotropic scattering coupling; returns I[D,N,G], J[N,G], Gamma[N,G]."""
     D, N = omega.shape[0], mesh.n_cells
@@ -75,19 +91,23 @@ def solve_coupled(mesh, omega, weight, kappa_abs, emissivity, kappa_scat=None, b
     kt = kappa_abs + ks
     I = np.zeros((D, N, G))
     for g in range(G):
-        A = np.zeros((D * N, D * N))
-        rhs = np.zeros(D * N)
-        for d in range(D):
-            L, b = transport_matrix(mesh, omega[d], kt, bc_inflow, g)
-            A[d * N:(d + 1) * N, d * N:(d + 1) * N] = L
-            rhs[d * N:(d + 1) * N] = emissivity[:, g] / (4 * math.pi) + b
-            for d2 in range(D):
-                idx = np.arange(N)
-                A[d * N + idx, d2 * N + idx] -= ks[:, g] * mesh.volume * weight[d2] / (4 * math.pi)
+        A, b = coupled_matrix(mesh, omega, weight, kt, ks, g, bc_inflow)
+        rhs = np.tile(emissivity[:, g] / (4 * math.pi), D) + b
         I[:, :, g] = np.linalg.solve(A, rhs).reshape(D, N)
     J = np.einsum("d,dng->ng", weight, I) / (4 * math.pi)
     Gam = kappa_abs * mesh.volume[:, None] * 4 * math.pi * J
     return I, J, Gam
+
+
+def adjoint_coupled(mesh, omega, weight, kappa_abs, kappa_scat, g_src):
+    """lambda[D,N,G] solving A^T lambda = g for the coupled system of every group (no periodic faces)."""
+    D, N = omega.shape[0], mesh.n_cells
+    G = kappa_abs.shape[1]
+    lam = np.zeros((D, N, G))
+    for g in range(G):
+        A, _ = coupled_matrix(mesh, omega, weight, kappa_abs + kappa_scat, kappa_scat, g, None)
+        lam[:, :, g] = np.linalg.solve(A.T, g_src[:, :, g].reshape(D * N)).reshape(D, N)
+    return lam
 
 
 def adjoint_direction(mesh, om, kappa_abs, g_src):

@@ -551,66 +551,119 @@ out:
 }
 
 /*
- * O9: adjoint of a loss L(J, Gamma) for problems without scattering and without
- * periodic faces. dl_dJ, dl_dGamma [N][G] (either may be NULL = 0). Outputs
- * grad_kappa_abs, grad_emissivity [N][G]. For each direction d:
+ * O9: adjoint of a loss L(J, Gamma) for problems without periodic faces, with or without
+ * isotropic scattering. dl_dJ, dl_dGamma [N][G] (either may be NULL = 0). Outputs
+ * grad_kappa_abs, grad_emissivity and, if not NULL, grad_kappa_scat [N][G].
+ *
+ * The forward state is the converged source iteration (Alg. 1): L_d I_d = eps/4pi + kappa_s V J,
+ * J = (1/4pi) sum_d w_d I_d. Its transpose couples the directions the same way, with the
+ * direction weight moved to the other side:
  *   g_{d,c} = w_d (dl_dGamma_c kappa_a,c V_c + dl_dJ_c / 4pi)        (dL/dI_{c,d})
- *   L_d^T lambda_d = g_d, swept in reversed topological order
- *   dL/dkappa_a,c += V_c I_{c,d} (w_d dl_dGamma_c - lambda_{d,c})
- *   dL/deps_c     += lambda_{d,c} / 4pi
+ *   L_d^T lambda_d = g_d + w_d kappa_s,c V_c mu_c / 4pi,  mu_c = sum_d lambda_{d,c}
+ * solved by the transposed source iteration (mu starts at 0; each pass sweeps every direction in
+ * reversed topological order and recomputes mu), stopped when max |mu_new - mu_old| <=
+ * tol_scat * max |mu_new| (0/0 counts as converged) or after max_it_scat passes. Then
+ *   dL/dkappa_a,c = sum_d V_c I_{c,d} (w_d dl_dGamma_c - lambda_{d,c})
+ *   dL/deps_c     = sum_d lambda_{d,c} / 4pi
+ *   dL/dkappa_s,c = sum_d V_c lambda_{d,c} (J_c - I_{c,d})
+ * Without scattering one transposed sweep gives lambda exactly. iters (or NULL) receives the
+ * forward and the transposed sweep counts.
  */
 int oracle_adjoint(int64_t n_cells, int64_t n_faces, const double* volume, const int32_t* face_cells,
                    const double* area, const double* normal, const uint8_t* flags, int32_t n_dir,
                    const double* omega, const double* weight, int32_t n_groups, const double* kappa_abs,
-                   const double* emissivity, const double* bc_inflow, const double* dl_dJ,
-                   const double* dl_dGamma, int n_threads, double* grad_kappa_abs, double* grad_emissivity) {
+                   const double* kappa_scat, const double* emissivity, const double* bc_inflow,
+                   const double* dl_dJ, const double* dl_dGamma, double tol_scat, int32_t max_it_scat,
+                   int n_threads, double* grad_kappa_abs, double* grad_emissivity, double* grad_kappa_scat,
+                   int32_t* iters) {
     problem p;
     memset(&p, 0, sizeof p);
     p.n_cells = n_cells; p.n_faces = n_faces; p.volume = volume; p.face_cells = face_cells;
     p.area = area; p.normal = normal; p.flags = flags; p.n_dir = n_dir; p.omega = omega;
-    p.weight = weight; p.n_groups = n_groups; p.kappa_abs = kappa_abs; p.kappa_scat = NULL;
+    p.weight = weight; p.n_groups = n_groups; p.kappa_abs = kappa_abs; p.kappa_scat = kappa_scat;
     p.emissivity = emissivity; p.bc_inflow = bc_inflow;
     int rc = check_problem(&p);
     if (rc != OR_OK) return rc;
     for (int64_t f = 0; f < n_faces; ++f)
         if (flags[f] & OR_FACE_PERIODIC) return OR_ERR_ARG;
+    if (max_it_scat < 1) return OR_ERR_ARG;
     rc = build_sides(&p);
     if (rc != OR_OK) { free_sides(&p); return rc; }
     int64_t N = n_cells, G = n_groups, NG = N * G, D = n_dir;
+    int has_scat = 0;
+    if (kappa_scat)
+        for (int64_t i = 0; i < NG; ++i)
+            if (kappa_scat[i] != 0.0) { has_scat = 1; break; }
+    int it_fwd = 0, it_adj = 0;
     double* I = (double*)calloc((size_t)(D * NG > 0 ? D * NG : 1), sizeof(double));
     double* lam = (double*)calloc((size_t)(D * NG > 0 ? D * NG : 1), sizeof(double));
     double* q = (double*)malloc(sizeof(double) * (size_t)(NG > 0 ? NG : 1));
     double* g = (double*)calloc((size_t)(D * NG > 0 ? D * NG : 1), sizeof(double));
-    if (!I || !lam || !q || !g) { rc = OR_ERR_MEM; goto out; }
-    for (int64_t i = 0; i < NG; ++i) q[i] = emissivity[i] / FOURPI;
-    rc = run_dirs(&p, n_threads, 0, q, 0, NULL, I, NULL, NULL, 1);
-    if (rc != OR_OK) goto out;
-    for (int32_t d = 0; d < n_dir; ++d)
+    double* J = (double*)calloc((size_t)(NG > 0 ? NG : 1), sizeof(double));
+    double* Jold = (double*)calloc((size_t)(NG > 0 ? NG : 1), sizeof(double));
+    double* mu = (double*)calloc((size_t)(NG > 0 ? NG : 1), sizeof(double));
+    if (!I || !lam || !q || !g || !J || !Jold || !mu) { rc = OR_ERR_MEM; goto out; }
+    /* forward: the source iteration of Alg. 1 (a single sweep without scattering) */
+    for (;;) {
         for (int64_t c = 0; c < N; ++c)
             for (int k = 0; k < G; ++k) {
                 int64_t i = c * G + k;
-                double gd = dl_dGamma ? dl_dGamma[i] * kappa_abs[i] * volume[c] : 0.0;
-                double gj = dl_dJ ? dl_dJ[i] / FOURPI : 0.0;
-                g[(int64_t)d * NG + i] = weight[d] * (gd + gj);
+                q[i] = emissivity[i] / FOURPI + (has_scat ? kappa_scat[i] * volume[c] * Jold[i] : 0.0);
             }
-    rc = run_dirs(&p, n_threads, 1, g, NG, NULL, lam, NULL, NULL, 1);
-    if (rc != OR_OK) goto out;
+        rc = run_dirs(&p, n_threads, 0, q, 0, NULL, I, NULL, NULL, 1);
+        if (rc != OR_OK) goto out;
+        ++it_fwd;
+        mean_intensity(&p, I, J);
+        if (!has_scat) break;
+        double res = scat_residual(NG, J, Jold);
+        memcpy(Jold, J, sizeof(double) * (size_t)NG);
+        if (res <= tol_scat || it_fwd >= max_it_scat) break;
+    }
+    /* transposed source iteration */
+    for (;;) {
+        for (int32_t d = 0; d < n_dir; ++d)
+            for (int64_t c = 0; c < N; ++c)
+                for (int k = 0; k < G; ++k) {
+                    int64_t i = c * G + k;
+                    double gd = dl_dGamma ? dl_dGamma[i] * kappa_abs[i] * volume[c] : 0.0;
+                    double gj = dl_dJ ? dl_dJ[i] / FOURPI : 0.0;
+                    double gs = has_scat ? kappa_scat[i] * volume[c] * mu[i] / FOURPI : 0.0;
+                    g[(int64_t)d * NG + i] = weight[d] * (gd + gj + gs);
+                }
+        rc = run_dirs(&p, n_threads, 1, g, NG, NULL, lam, NULL, NULL, 1);
+        if (rc != OR_OK) goto out;
+        ++it_adj;
+        if (!has_scat) break;
+        double dmax = 0.0, mmax = 0.0;
+        for (int64_t i = 0; i < NG; ++i) {
+            double m = 0.0;
+            for (int32_t d = 0; d < n_dir; ++d) m += lam[(int64_t)d * NG + i];
+            double dm = fabs(m - mu[i]);
+            if (dm > dmax) dmax = dm;
+            if (fabs(m) > mmax) mmax = fabs(m);
+            mu[i] = m;
+        }
+        if (dmax == 0.0 || dmax <= tol_scat * mmax || it_adj >= max_it_scat) break;
+    }
     for (int64_t c = 0; c < N; ++c)
         for (int k = 0; k < G; ++k) {
             int64_t i = c * G + k;
-            double gk = 0.0, ge = 0.0;
+            double gk = 0.0, ge = 0.0, gs = 0.0;
+            double rg = dl_dGamma ? dl_dGamma[i] : 0.0;
             for (int32_t d = 0; d < n_dir; ++d) {
                 double Icd = I[(int64_t)d * NG + i];
                 double lcd = lam[(int64_t)d * NG + i];
-                double rg = dl_dGamma ? dl_dGamma[i] : 0.0;
                 gk += volume[c] * Icd * (weight[d] * rg - lcd);
                 ge += lcd / FOURPI;
+                gs += volume[c] * lcd * (J[i] - Icd);
             }
             grad_kappa_abs[i] = gk;
             grad_emissivity[i] = ge;
+            if (grad_kappa_scat) grad_kappa_scat[i] = gs;
         }
+    if (iters) { iters[0] = it_fwd; iters[1] = it_adj; }
 out:
-    free(I); free(lam); free(q); free(g);
+    free(I); free(lam); free(q); free(g); free(J); free(Jold); free(mu);
     free_sides(&p);
     return rc;
 }

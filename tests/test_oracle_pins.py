@@ -355,3 +355,68 @@ def test_oracle_matches_stored_plain32_golden():
     assert g["depths"] == [3 * 31 + 1] * p.n_dir
     rc, _, depth = oracle.levels(p.mesh, p.omega)
     assert rc == 0 and list(depth) == g["depths"]
+
+
+# ---- (f) the adjoint through the source iteration (scattering) ------------------------------------
+def _scat_problem(n=300, seed=37):
+    return configs.voronoi_small(n, n_dir=8, n_groups=2, seed=seed, scatter_albedo=0.5, n_src=6)
+
+
+def test_adjoint_scattering_dense_transpose():
+    # lambda of the transposed source iteration is the solution of A^T lambda = dL/dI for the whole
+    # coupled system (every direction and the scattering coupling in one dense matrix)
+    p = _scat_problem(200, 39)
+    rng = np.random.default_rng(5)
+    dg = rng.normal(size=p.kappa_abs.shape)
+    dj = rng.normal(size=p.kappa_abs.shape)
+    r = oracle.adjoint_full(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, kappa_scat=p.kappa_scat,
+                            dl_dJ=dj, dl_dGamma=dg, tol_scat=1e-15, max_it_scat=5000)
+    assert r["rc"] == 0 and r["it_adjoint"] > 1
+    V = p.mesh.volume[:, None]
+    gsrc = p.weight[:, None, None] * (dg * p.kappa_abs * V + dj / (4 * math.pi))[None]
+    lam = dense.adjoint_coupled(p.mesh, p.omega, p.weight, p.kappa_abs, p.kappa_scat, gsrc)
+    assert rel(r["grad_emissivity"], lam.sum(axis=0) / (4 * math.pi)) <= 1e-11
+
+
+def test_adjoint_scattering_finite_differences():
+    p = _scat_problem()
+    rng = np.random.default_rng(6)
+    T = rng.random(p.kappa_abs.shape) * np.median(p.emissivity[p.emissivity > 0])
+    rJ = rng.normal(size=p.kappa_abs.shape)
+    kw = dict(tol_scat=1e-15, max_it_scat=5000)
+
+    def loss(ka, em, ks):
+        r = oracle.solve(p.mesh, p.omega, p.weight, ka, em, kappa_scat=ks, **kw)
+        assert r["rc"] == 0
+        return math.fsum(((r["Gamma"] - T) ** 2).ravel()) + math.fsum((rJ * r["J"]).ravel()), r["Gamma"]
+
+    _, G0 = loss(p.kappa_abs, p.emissivity, p.kappa_scat)
+    r = oracle.adjoint_full(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, kappa_scat=p.kappa_scat,
+                            dl_dJ=rJ, dl_dGamma=2 * (G0 - T), **kw)
+    assert r["rc"] == 0
+    grads = {"ka": r["grad_kappa_abs"], "em": r["grad_emissivity"], "ks": r["grad_kappa_scat"]}
+    base = {"ka": p.kappa_abs, "em": p.emissivity, "ks": p.kappa_scat}
+    for name, gr in grads.items():
+        big = np.argsort(np.abs(gr).ravel())[-30:]
+        for flat in rng.choice(big, 4, replace=False):
+            c, g = divmod(int(flat), p.n_groups)
+            h = 1e-4 * max(base[name][c, g], 1e-3 * base[name].max())
+            args_p = {k: v.copy() for k, v in base.items()}
+            args_m = {k: v.copy() for k, v in base.items()}
+            args_p[name][c, g] += h
+            args_m[name][c, g] -= h
+            fd = (loss(args_p["ka"], args_p["em"], args_p["ks"])[0]
+                  - loss(args_m["ka"], args_m["em"], args_m["ks"])[0]) / (2 * h)
+            assert gr[c, g] == pytest.approx(fd, rel=1e-5, abs=1e-7 * np.abs(gr).max()), (name, c, g)
+
+
+def test_adjoint_without_scattering_is_one_transposed_sweep():
+    p = configs.voronoi_small(300, n_dir=8, n_groups=2, seed=41)
+    rng = np.random.default_rng(7)
+    dg = rng.normal(size=p.kappa_abs.shape)
+    rc, gk, ge = oracle.adjoint(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, dl_dGamma=dg)
+    r = oracle.adjoint_full(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity,
+                            kappa_scat=np.zeros_like(p.kappa_abs), dl_dGamma=dg)
+    assert r["it_forward"] == r["it_adjoint"] == 1
+    assert np.array_equal(r["grad_kappa_abs"], gk) and np.array_equal(r["grad_emissivity"], ge)
+
