@@ -90,8 +90,8 @@ def load(path: str | None = None):
         "sweep_solve_dev": (S, [P, OP, P, P, SP]),
         "sweep_levels": (S, [P, I32, P, ctypes.POINTER(I32)]),
         "sweep_intensity": (S, [P, I32, P]),
-        "sweep_adjoint": (S, [P, OP, P, P, P, P, SP]),
-        "sweep_adjoint_dev": (S, [P, OP, P, P, P, P, SP]),
+        "sweep_adjoint": (S, [P, OP, P, P, P, P, P, SP]),
+        "sweep_adjoint_dev": (S, [P, OP, P, P, P, P, P, SP]),
         "sweep_status_string": (ctypes.c_char_p, [S]),
         "sweep_last_error": (ctypes.c_char_p, [P]),
         "sweep_levels_noalloc": (S, [ctypes.c_int, P, I64, I64, P, P, P, P, P, ctypes.POINTER(I32)]),
@@ -249,22 +249,27 @@ class Context:
         self._check(self.lib.sweep_intensity(self.h, direction, _hp(out)))
         return out
 
-    def adjoint(self, dl_dJ=None, dl_dGamma=None, opts: sweep_opts | None = None, **kw):
+    def adjoint(self, dl_dJ=None, dl_dGamma=None, opts: sweep_opts | None = None, with_kappa_scat: bool = False,
+                allow_not_converged: bool = False, **kw):
+        """Host gradients (dL/dkappa_abs, dL/demissivity[, dL/dkappa_scat], stats dict) [N,G]."""
         o = opts or default_opts(**kw)
         N, G = self.n_cells, self.n_groups
         dj = None if dl_dJ is None else _host(dl_dJ, np.float64).reshape(N, G)
         dg = None if dl_dGamma is None else _host(dl_dGamma, np.float64).reshape(N, G)
         gk = np.zeros((N, G))
         ge = np.zeros((N, G))
+        gs = np.zeros((N, G)) if with_kappa_scat else None
         st = sweep_stats()
-        self._check(self.lib.sweep_adjoint(self.h, ctypes.byref(o), _hp(dj), _hp(dg), _hp(gk), _hp(ge),
-                                           ctypes.byref(st)))
-        return gk, ge, st.as_dict()
+        ok = (SWEEP_OK, SWEEP_NOT_CONVERGED) if allow_not_converged else (SWEEP_OK,)
+        self._check(self.lib.sweep_adjoint(self.h, ctypes.byref(o), _hp(dj), _hp(dg), _hp(gk), _hp(ge), _hp(gs),
+                                           ctypes.byref(st)), ok)
+        return (gk, ge, gs, st.as_dict()) if with_kappa_scat else (gk, ge, st.as_dict())
 
     def adjoint_dev(self, grad_kappa_out, grad_emissivity_out, dl_dJ=None, dl_dGamma=None,
-                    opts: sweep_opts | None = None, **kw):
+                    opts: sweep_opts | None = None, grad_kappa_scat_out=None, **kw):
         o = opts or default_opts(**kw)
         st = sweep_stats()
         self._check(self.lib.sweep_adjoint_dev(self.h, ctypes.byref(o), _dp(dl_dJ), _dp(dl_dGamma),
-                                               _dp(grad_kappa_out), _dp(grad_emissivity_out), ctypes.byref(st)))
+                                               _dp(grad_kappa_out), _dp(grad_emissivity_out),
+                                               _dp(grad_kappa_scat_out), ctypes.byref(st)))
         return st.as_dict()

@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "adjoint.cuh"
 #include "common.cuh"
 
 using namespace sw;
@@ -1206,11 +1207,10 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
 }
 
 sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double* dlj, const double* dlg, double* gk_out,
-                          double* ge_out, bool dev, sweep_stats* stats) {
+                          double* ge_out, double* gks_out, bool dev, sweep_stats* stats) {
     if (!c) return SWEEP_ERR_INVALID_ARG;
     cudaSetDevice(c->device);
     if (!c->has_mesh || !c->has_dirs || !c->has_mat) return bad(c, "set mesh, directions and material first");
-    if (c->has_scat) return bad(c, "the adjoint does not support scattering");
     if (c->mesh.n_pcells > 0) return bad(c, "the adjoint does not support periodic faces");
     if (c->G > 4) return bad(c, "the adjoint supports at most 4 groups");
     if (!gk_out || !ge_out) return bad(c, "null gradient output");
@@ -1225,7 +1225,12 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
     const int64_t N = c->mesh.N;
     const int G = c->G, D = c->D;
     const size_t NG = (size_t)N * G;
-    int B = (o.dir_batch > 0 && o.dir_batch < D) ? o.dir_batch : D;
+    // with scattering both source iterations couple all directions (and the kappa_s gradient needs J):
+    // one batch of every direction
+    const bool scat = c->has_scat;
+    const bool need_J = scat || gks_out;
+    if (scat && o.max_it_scat < 1) return bad(c, "max_it_scat must be >= 1");
+    int B = (!need_J && o.dir_batch > 0 && o.dir_batch < D) ? o.dir_batch : D;
     sweep_stats S;
     memset(&S, 0, sizeof S);
     const int64_t launches0 = c->launches;
@@ -1249,8 +1254,21 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
     double *d_dlj = b_dlj.p, *d_dlg = b_dlg.p, *gk = b_gk.p, *ge = b_ge.p;
     CK(cudaMemsetAsync(gk, 0, sizeof(double) * NG, c->st), "init");
     CK(cudaMemsetAsync(ge, 0, sizeof(double) * NG, c->st), "init");
+    DevBuf<double> b_gks, b_mu;
+    if (gks_out) CK(cudaMalloc(&b_gks.p, sizeof(double) * (NG > 0 ? NG : 1)), "alloc");
+    if (scat) {
+        CK(cudaMalloc(&b_mu.p, sizeof(double) * (2 * NG > 0 ? 2 * NG : 1)), "alloc");
+        CK(cudaMemsetAsync(b_mu.p, 0, sizeof(double) * 2 * NG, c->st), "init");
+    }
     sweep_status s = ensure_cm(c, 2 * NG);
     if (s != SWEEP_OK) return s;
+    const int nblk = nblocks256(NG);
+    if (need_J) {
+        s = ensure_ng(c, NG);
+        if (s != SWEEP_OK) return s;
+        s = ensure_partial(c, nblk + 1);
+        if (s != SWEEP_OK) return s;
+    }
     // batch buffers
     const size_t es = prec == 64 ? 8 : 4;
     size_t bI = es * (size_t)N * B * G, bL = es * (size_t)N * B * 2 * G;
@@ -1274,7 +1292,9 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
         ++c->launches;
     }
     float t_sweep = 0.f, tcl = 0.f, tlv = 0.f;
-    int n_sweeps = 0;
+    int n_sweeps = 0, it_fwd = 0, it_adj = 0;
+    bool conv_fwd = true, conv_adj = true;
+    double res_fwd = 0.0, res_adj = 0.0;
     for (int d0 = 0; d0 < D; d0 += B) {
         const int nb = (D - d0) < B ? (D - d0) : B;
         Levels* L;
@@ -1289,32 +1309,68 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
         if (s != SWEEP_OK) return s;
         tcl += a1;
         tlv += a2;
-        // forward intensities of this batch (recomputed, not stored across batches)
-        CKL(launch_prep_material(N, G, c->mesh.vol, c->ka, nullptr, c->em, nullptr, prec == 32 ? c->cm32 : nullptr,
-                                prec == 64 ? c->cm64 : nullptr, c->st), "prep");
+        // forward intensities of this batch (recomputed, not stored across batches); with scattering the
+        // source iteration of Alg. 1 to convergence, J_old starting at 0
         const void* cm = prec == 64 ? (const void*)c->cm64 : (const void*)c->cm32;
-        int pI = !signI;
-        SweepArgs a = make_args(c, *L, prec, cm, c->adjI, nullptr, G, pI, 0, 0, &o);
-        a.debug_stall = 0;
-        s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, lanes, 0, a, bc32.p, &t_sweep);
-        if (s != SWEEP_OK) return s;
-        signI = pI;
-        // transposed sweep with split non-negative sources (2G groups)
-        CKL(launch_prep_adjoint_src(N, G, c->mesh.vol, c->ka, nullptr, d_dlj, d_dlg, prec == 32 ? c->cm32 : nullptr,
-                                   prec == 64 ? c->cm64 : nullptr, c->st), "prep adjoint");
-        int pL = !signL;
-        SweepArgs r = make_args(c, *L, prec, cm, c->adjL, nullptr, 2 * G, pL, 1, 0, &o);
-        r.debug_stall = 0;
-        s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, lanes, 0, r, nullptr, &t_sweep);
-        if (s != SWEEP_OK) return s;
-        signL = pL;
-        n_sweeps += 2;
-        CKL(launch_grad_accum(prec, c->adjI, c->adjL, N, G, nb, d0, c->w64, c->mesh.vol, d_dlg, gk, ge, c->st),
+        if (scat) CK(cudaMemsetAsync(c->Jold, 0, sizeof(double) * NG, c->st), "init");
+        for (;;) {
+            CKL(launch_prep_material(N, G, c->mesh.vol, c->ka, scat ? c->ks : nullptr, c->em, scat ? c->Jold : nullptr,
+                                    prec == 32 ? c->cm32 : nullptr, prec == 64 ? c->cm64 : nullptr, c->st), "prep");
+            int pI = !signI;
+            SweepArgs a = make_args(c, *L, prec, cm, c->adjI, nullptr, G, pI, 0, 0, &o);
+            a.debug_stall = 0;
+            s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, lanes, 0, a, bc32.p, &t_sweep);
+            if (s != SWEEP_OK) return s;
+            signI = pI;
+            ++n_sweeps;
+            ++it_fwd;
+            if (!need_J) break;
+            CKL(launch_tally(prec, c->adjI, N, G, D, 0, c->w64, c->wsum, c->mesh.vol, c->ka, c->em, c->J, c->Gam,
+                            c->partial, nblk, c->st), "tally");
+            if (!scat) break;
+            CK(cudaMemsetAsync(c->dmax, 0, sizeof(unsigned long long), c->st), "init");
+            CKL(launch_scat_residual(NG, c->J, c->Jold, c->dmax, c->st), "scattering residual");
+            res_fwd = read_max(c);
+            if (res_fwd <= o.tol_scat) break;
+            if (it_fwd >= o.max_it_scat) { conv_fwd = false; break; }
+        }
+        // transposed sweep with split non-negative sources (2G groups); with scattering the transposed
+        // source iteration, mu starting at 0
+        CKL(launch_prep_adjoint_src(N, G, c->mesh.vol, c->ka, scat ? c->ks : nullptr, d_dlj, d_dlg,
+                                   prec == 32 ? c->cm32 : nullptr, prec == 64 ? c->cm64 : nullptr, c->st),
+           "prep adjoint");
+        for (;;) {
+            int pL = !signL;
+            SweepArgs r = make_args(c, *L, prec, cm, c->adjL, nullptr, 2 * G, pL, 1, 0, &o);
+            r.debug_stall = 0;
+            s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, lanes, 0, r, nullptr, &t_sweep);
+            if (s != SWEEP_OK) return s;
+            signL = pL;
+            ++n_sweeps;
+            ++it_adj;
+            if (!scat) break;
+            CK(cudaMemsetAsync(c->dmax, 0, 2 * sizeof(unsigned long long), c->st), "init");
+            CKL(launch_adjoint_mu(prec, c->adjL, N, G, D, c->mesh.vol, c->ka, c->ks, d_dlj, d_dlg, b_mu.p,
+                                 prec == 32 ? c->cm32 : nullptr, prec == 64 ? c->cm64 : nullptr, c->dmax, c->st),
+               "transposed source");
+            unsigned long long hm[2] = {0, 0};
+            CK(cudaMemcpyAsync(hm, c->dmax, sizeof hm, cudaMemcpyDeviceToHost, c->st), "read");
+            CK(cudaStreamSynchronize(c->st), "read");
+            double dm, mm;
+            memcpy(&dm, &hm[0], sizeof dm);
+            memcpy(&mm, &hm[1], sizeof mm);
+            res_adj = dm == 0.0 ? 0.0 : (mm > 0.0 ? dm / mm : INFINITY);
+            if (dm == 0.0 || dm <= o.tol_scat * mm) break;
+            if (it_adj >= o.max_it_scat) { conv_adj = false; break; }
+        }
+        CKL(launch_grad_scat(prec, c->adjI, c->adjL, N, G, nb, d0, c->w64, c->mesh.vol, d_dlg,
+                            need_J ? c->J : nullptr, gk, ge, b_gks.p, c->st),
            "gradient");
     }
     cudaMemcpyKind kout = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     CK(cudaMemcpyAsync(gk_out, gk, sizeof(double) * NG, kout, c->st), "copy gradient");
     CK(cudaMemcpyAsync(ge_out, ge, sizeof(double) * NG, kout, c->st), "copy gradient");
+    if (gks_out) CK(cudaMemcpyAsync(gks_out, b_gks.p, sizeof(double) * NG, kout, c->st), "copy gradient");
     cudaEventRecord(t1, c->st);
     CK(cudaStreamSynchronize(c->st), "adjoint");
     float ttot = 0;
@@ -1322,17 +1378,21 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     S.n_sweeps = n_sweeps;
+    S.it_scat = it_fwd;
+    S.it_pbc = it_adj;
+    S.res_scat = res_fwd;
+    S.res_pbc = res_adj;
     S.t_ms[0] = tcl;
     S.t_ms[1] = tlv;
     S.t_ms[2] = t_sweep;
     S.t_ms[4] = ttot;
-    S.updates = (double)N * D * G * 3;  // forward, and the transposed sweep over 2G split groups
+    S.updates = (double)N * D * G * (it_fwd + 2.0 * it_adj);  // forward, transposed over 2G split groups
     S.updates_per_s = ttot > 0 ? S.updates / (ttot * 1e-3) : 0.0;
     S.schedule_used = plain ? SWEEP_SCHED_PLAIN : sched;
     S.kernel_used = c->last_kernel;
     S.kernel_launches = (int32_t)(c->launches - launches0);
     if (stats) *stats = S;
-    return SWEEP_OK;
+    return (conv_fwd && conv_adj) ? SWEEP_OK : SWEEP_NOT_CONVERGED;
 }
 
 }  // namespace
@@ -1381,13 +1441,13 @@ sweep_status sweep_intensity(sweep_ctx* c, int32_t dir, double* out) {
 }
 
 sweep_status sweep_adjoint(sweep_ctx* c, const sweep_opts* o, const double* dlj, const double* dlg, double* gk,
-                           double* ge, sweep_stats* st) {
-    return adjoint_impl(c, o, dlj, dlg, gk, ge, false, st);
+                           double* ge, double* gks, sweep_stats* st) {
+    return adjoint_impl(c, o, dlj, dlg, gk, ge, gks, false, st);
 }
 
 sweep_status sweep_adjoint_dev(sweep_ctx* c, const sweep_opts* o, const double* dlj, const double* dlg, double* gk,
-                               double* ge, sweep_stats* st) {
-    return adjoint_impl(c, o, dlj, dlg, gk, ge, true, st);
+                               double* ge, double* gks, sweep_stats* st) {
+    return adjoint_impl(c, o, dlj, dlg, gk, ge, gks, true, st);
 }
 
 }  // extern "C"

@@ -9,6 +9,7 @@
 //   source update   q_c = eps_c/4pi + kappa_s,c V_c J_c                (Alg. 1, scattering as a fixed source)
 //   periodic source j_c = sum_d w_d sum_{periodic inflow sides} |a_f| I_partner,d   (Sec. 2.7)
 //   relative change E_c = |j^n - j^(n-1)| / (j^n + j^(n-1))             (Eq. relativeErrorPbc)
+#include "adjoint.cuh"
 #include "common.cuh"
 
 namespace sw {
@@ -338,26 +339,71 @@ __global__ void k_reduce_sum(const double* partial, int n, double* out) {
     }
 }
 
-// lambda of group g = lambda+ (group g) - lambda- (group G+g) of the split adjoint sweep
+// lambda of group g = lambda+ (group g) - lambda- (group G+g) of the split adjoint sweep. With
+// scattering (J != nullptr) also dL/dkappa_s = V sum_d lambda_d (J - I_d).
 template <typename real>
 __global__ void k_grad(const real* I, const real* lam, int64_t N, int G, int nd, const double* w64, const double* vol,
-                       const double* dlg, double* gk, double* ge) {
+                       const double* dlg, const double* J, double* gk, double* ge, double* gks) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N * G) return;
     int64_t c = i / G;
     int g = (int)(i - c * G);
     double V = vol[c];
     double rg = dlg ? dlg[i] : 0.0;
-    double sk = gk[i], se = ge[i];
+    double Jc = J ? J[i] : 0.0;
+    double sk = gk[i], se = ge[i], ss = 0.0;
     for (int d = 0; d < nd; ++d) {
         double Icd = mag(I + ((size_t)d * N + c) * G + g);
         const real* lp = lam + ((size_t)d * N + c) * (2 * G);
         double lcd = mag(lp + g) - mag(lp + G + g);
         sk = dadd(sk, dmul(dmul(V, Icd), dmul(w64[d], rg) - lcd));
         se = dadd(se, lcd / FOURPI);
+        ss = dadd(ss, dmul(dmul(V, lcd), Jc - Icd));
     }
     gk[i] = sk;
     ge[i] = se;
+    if (J && gks) gks[i] = ss;
+}
+
+// Transposed source iteration: mu+- = sum_d lambda+-_d (no direction weight: the reverse sweep puts
+// w_d on its source), the largest change and the largest magnitude of mu = mu+ - mu- (dmax[0],
+// dmax[1]), and the split sources of the next transposed sweep, g+- + kappa_s V mu+- / 4pi.
+template <typename real>
+__global__ void k_adj_mu(const real* lam, int64_t N, int G, int nd, const double* vol, const double* ka,
+                         const double* ks, const double* dlj, const double* dlg, double* mu, float2* cm32,
+                         double2* cm64, unsigned long long* dmax) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * G) return;
+    int64_t c = i / G;
+    int g = (int)(i - c * G);
+    const size_t G2 = 2 * (size_t)G;
+    double sp = 0.0, sm = 0.0;
+    for (int d = 0; d < nd; ++d) {
+        const real* lp = lam + ((size_t)d * N + c) * G2;
+        sp = dadd(sp, mag(lp + g));
+        sm = dadd(sm, mag(lp + G + g));
+    }
+    const size_t o = (size_t)c * G2;
+    double change = fabs((sp - sm) - (mu[o + g] - mu[o + G + g]));
+    double size = fabs(sp - sm);
+    mu[o + g] = sp;
+    mu[o + G + g] = sm;
+    if (change > 0.0) atomicMax(dmax, (unsigned long long)__double_as_longlong(change));
+    if (size > 0.0) atomicMax(dmax + 1, (unsigned long long)__double_as_longlong(size));
+    double V = vol[c];
+    double src = dadd(dlg ? dmul(dmul(dlg[i], ka[i]), V) : 0.0, dlj ? dlj[i] / FOURPI : 0.0);
+    double gp = src > 0.0 ? src : 0.0, gm = src < 0.0 ? -src : 0.0;
+    double kv = dmul(ks[i], V);
+    double qp = dadd(gp, dmul(kv, sp) / FOURPI), qm = dadd(gm, dmul(kv, sm) / FOURPI);
+    double dnm = dmul(dadd(ka[i], ks[i]), V);
+    if (cm64) {
+        cm64[o + g] = make_double2(qp, dnm);
+        cm64[o + G + g] = make_double2(qm, dnm);
+    }
+    if (cm32) {
+        cm32[o + g] = make_float2((float)qp, (float)dnm);
+        cm32[o + G + g] = make_float2((float)qm, (float)dnm);
+    }
 }
 
 __global__ void k_fill_u32(uint32_t* p, uint32_t v, int64_t n) {
@@ -488,13 +534,32 @@ cudaError_t launch_reduce_sum(const double* partial, int n, double* out, cudaStr
 cudaError_t launch_grad_accum(int precision, const void* I, const void* lam, int64_t N, int G, int nd, int d0,
                               const double* w64, const double* vol, const double* dl_dG, double* gk, double* ge,
                               cudaStream_t st) {
+    return launch_grad_scat(precision, I, lam, N, G, nd, d0, w64, vol, dl_dG, nullptr, gk, ge, nullptr, st);
+}
+
+cudaError_t launch_grad_scat(int precision, const void* I, const void* lam, int64_t N, int G, int nd, int d0,
+                             const double* w64, const double* vol, const double* dl_dG, const double* J, double* gk,
+                             double* ge, double* gks, cudaStream_t st) {
     if (N * G <= 0) return cudaSuccess;
     if (precision == 64)
         k_grad<double><<<nb(N * G), 256, 0, st>>>((const double*)I, (const double*)lam, N, G, nd, w64 + d0, vol,
-                                                  dl_dG, gk, ge);
+                                                  dl_dG, J, gk, ge, gks);
     else
         k_grad<float><<<nb(N * G), 256, 0, st>>>((const float*)I, (const float*)lam, N, G, nd, w64 + d0, vol, dl_dG,
-                                                 gk, ge);
+                                                 J, gk, ge, gks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_mu(int precision, const void* lam, int64_t N, int G, int nd, const double* vol,
+                              const double* ka, const double* ks, const double* dl_dJ, const double* dl_dG,
+                              double* mu, float2* cm32, double2* cm64, unsigned long long* d_max, cudaStream_t st) {
+    if (N * G <= 0) return cudaSuccess;
+    if (precision == 64)
+        k_adj_mu<double><<<nb(N * G), 256, 0, st>>>((const double*)lam, N, G, nd, vol, ka, ks, dl_dJ, dl_dG, mu,
+                                                    cm32, cm64, d_max);
+    else
+        k_adj_mu<float><<<nb(N * G), 256, 0, st>>>((const float*)lam, N, G, nd, vol, ka, ks, dl_dJ, dl_dG, mu, cm32,
+                                                   cm64, d_max);
     return cudaGetLastError();
 }
 

@@ -230,13 +230,55 @@ def test_adjoint_matches_oracle(ctx, precision, batch):
     assert rel_max(ge, oe) <= tol
 
 
-def test_adjoint_rejects_scattering(ctx):
+def test_adjoint_rejects_periodic_faces(ctx):
     from paper_2207_12848_gb300 import SweepError
-    p = configs.voronoi_small(500, n_dir=4, seed=53, scatter_albedo=0.3)
+    p = configs.voronoi_small(500, periodic_box=True, n_dir=4, seed=53)
     load(ctx, p)
     with pytest.raises(SweepError) as e:
         ctx.adjoint(dl_dGamma=np.ones_like(p.kappa_abs))
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_adjoint_through_the_source_iteration(ctx, precision):
+    # the transposed source iteration against the oracle's: first sweep for sweep (a fixed number of
+    # forward and transposed passes), then both converged, with the gradient in kappa_scat
+    p = configs.voronoi_small(3000, n_dir=16, n_groups=2, seed=55, scatter_albedo=0.5, n_src=6)
+    load(ctx, p)
+    rng = np.random.default_rng(56)
+    dg = rng.normal(size=p.kappa_abs.shape)
+    dj = rng.normal(size=p.kappa_abs.shape)
+    tol = 1e-10 if precision == 64 else 1e-4
+    gk, ge, gs, st = ctx.adjoint(dl_dJ=dj, dl_dGamma=dg, precision=precision, schedule="dataflow", tol_scat=0.0,
+                                 max_it_scat=5, with_kappa_scat=True, allow_not_converged=True)
+    r = oracle.adjoint_full(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, kappa_scat=p.kappa_scat,
+                            dl_dJ=dj, dl_dGamma=dg, tol_scat=0.0, max_it_scat=5, threads=8)
+    assert r["rc"] == 0 and st["it_scat"] == r["it_forward"] == 5 and st["it_pbc"] == r["it_adjoint"] == 5
+    assert rel_max(gk, r["grad_kappa_abs"]) <= tol
+    assert rel_max(ge, r["grad_emissivity"]) <= tol
+    assert rel_max(gs, r["grad_kappa_scat"]) <= tol
+    kw = dict(tol_scat=1e-11 if precision == 64 else 1e-6, max_it_scat=500)
+    gk, ge, gs, st = ctx.adjoint(dl_dJ=dj, dl_dGamma=dg, precision=precision, with_kappa_scat=True, **kw)
+    r = oracle.adjoint_full(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, kappa_scat=p.kappa_scat,
+                            dl_dJ=dj, dl_dGamma=dg, threads=8, **kw)
+    assert st["res_pbc"] <= kw["tol_scat"] and st["it_pbc"] > 5
+    tol = 1e-9 if precision == 64 else 1e-4
+    assert rel_max(gk, r["grad_kappa_abs"]) <= tol
+    assert rel_max(ge, r["grad_emissivity"]) <= tol
+    assert rel_max(gs, r["grad_kappa_scat"]) <= tol
+
+
+def test_adjoint_kappa_scat_gradient_without_scattering(ctx):
+    # the derivative at kappa_s = 0 needs J but no source iteration: one forward and one transposed sweep
+    p = configs.voronoi_small(3000, n_dir=16, n_groups=2, seed=57, n_src=6)
+    load(ctx, p)
+    dg = np.random.default_rng(58).normal(size=p.kappa_abs.shape)
+    gk, ge, gs, st = ctx.adjoint(dl_dGamma=dg, precision=64, dir_batch=5, with_kappa_scat=True)
+    r = oracle.adjoint_full(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity,
+                            kappa_scat=np.zeros_like(p.kappa_abs), dl_dGamma=dg, threads=8)
+    assert st["it_scat"] == st["it_pbc"] == 1
+    assert rel_max(gk, r["grad_kappa_abs"]) <= 1e-10
+    assert rel_max(gs, r["grad_kappa_scat"]) <= 1e-10
 
 
 # ---- edge cases -------------------------------------------------------------------------------------------
