@@ -15,7 +15,8 @@ Parity status per function (what pins it; see tests/test_oracle_pins.py):
                     (plain, scattering, periodic, both at once for the nested and the fused
                     loops), uniform periodic fixed point, linearity, pure streaming
   oracle_adjoint -- pinned: central finite differences of oracle_solve (also in kappa_scat, through
-                    the source iteration), dense transposed solve (also of the coupled system),
+                    the source iteration, and through the periodic iteration), dense transposed
+                    solve (also of the coupled system, with scattering and periodic faces),
                     reciprocity of the transport operator
 """
 from __future__ import annotations
@@ -67,8 +68,8 @@ def _lib():
             lib.oracle_solve.argtypes = [I64, I64, P, P, P, P, P, I32, P, P, I32, P, P, P, P, D, I32, D, I32, P,
                                          ctypes.c_int, ctypes.c_int, P, P, P, ctypes.POINTER(Stats)]
             lib.oracle_adjoint.restype = ctypes.c_int
-            lib.oracle_adjoint.argtypes = [I64, I64, P, P, P, P, P, I32, P, P, I32, P, P, P, P, P, P, D, I32,
-                                           ctypes.c_int, P, P, P, P]
+            lib.oracle_adjoint.argtypes = [I64, I64, P, P, P, P, P, I32, P, P, I32, P, P, P, P, P, P, D, I32, D,
+                                           I32, ctypes.c_int, P, P, P, P]
             _LIB = lib
     return _LIB
 
@@ -143,9 +144,10 @@ def adjoint(mesh, omega, weight, kappa_abs, emissivity, dl_dJ=None, dl_dGamma=No
 
 
 def adjoint_full(mesh, omega, weight, kappa_abs, emissivity, kappa_scat=None, dl_dJ=None, dl_dGamma=None,
-                 bc_inflow=None, tol_scat=1e-6, max_it_scat=100, threads: int = 1):
-    """The adjoint with scattering (transposed source iteration): a dict with rc, the gradients in
-    kappa_abs, emissivity and kappa_scat [N,G], and the forward and transposed sweep counts."""
+                 bc_inflow=None, tol_scat=1e-6, max_it_scat=100, tol_pbc=1e-6, max_it_pbc=100, threads: int = 1):
+    """The adjoint through the scattering and periodic iterations (their transpose): a dict with rc, the
+    gradients in kappa_abs, emissivity and kappa_scat [N,G], and the forward sweep and transposed pass
+    counts."""
     om = _c(omega, np.float64).reshape(-1, 3)
     w = _c(weight, np.float64)
     N = mesh.n_cells
@@ -162,7 +164,7 @@ def adjoint_full(mesh, omega, weight, kappa_abs, emissivity, kappa_scat=None, dl
     gs = np.zeros((N, G))
     its = np.zeros(2, np.int32)
     rc = _lib().oracle_adjoint(*margs, om.shape[0], _ptr(om), _ptr(w), G, _ptr(ka), _ptr(ks), _ptr(em), _ptr(bc),
-                               _ptr(dj), _ptr(dg), tol_scat, max_it_scat, threads, _ptr(gk), _ptr(ge), _ptr(gs),
-                               _ptr(its))
+                               _ptr(dj), _ptr(dg), tol_scat, max_it_scat, tol_pbc, max_it_pbc, threads, _ptr(gk),
+                               _ptr(ge), _ptr(gs), _ptr(its))
     return {"rc": rc, "grad_kappa_abs": gk, "grad_emissivity": ge, "grad_kappa_scat": gs,
             "it_forward": int(its[0]), "it_adjoint": int(its[1])}

@@ -190,7 +190,9 @@ static int sweep_one(dir_sweep* s, int solve) {
                         for (int g = 0; g < G; ++g) acc[g] += a * p->bc_inflow[b * G + g];
                     }
                 } else if (fl & OR_FACE_PERIODIC) {
-                    if (!s->reverse && s->prev) {
+                    /* forward: the partner's intensity of the previous sweep flows in; adjoint: the
+                     * transpose, the partner's lambda of the previous pass across the outflow side */
+                    if (s->prev) {
                         int32_t up = other_cell(p, f, sign);
                         for (int g = 0; g < G; ++g) acc[g] += a * s->prev[(int64_t)up * G + g];
                     }
@@ -551,31 +553,37 @@ out:
 }
 
 /*
- * O9: adjoint of a loss L(J, Gamma) for problems without periodic faces, with or without
- * isotropic scattering. dl_dJ, dl_dGamma [N][G] (either may be NULL = 0). Outputs
- * grad_kappa_abs, grad_emissivity and, if not NULL, grad_kappa_scat [N][G].
+ * O9: adjoint of a loss L(J, Gamma), with or without isotropic scattering and periodic faces.
+ * dl_dJ, dl_dGamma [N][G] (either may be NULL = 0). Outputs grad_kappa_abs, grad_emissivity
+ * and, if not NULL, grad_kappa_scat [N][G].
  *
- * The forward state is the converged source iteration (Alg. 1): L_d I_d = eps/4pi + kappa_s V J,
- * J = (1/4pi) sum_d w_d I_d. Its transpose couples the directions the same way, with the
- * direction weight moved to the other side:
+ * The forward state is oracle_solve's (the source iteration of Alg. 1 inside the periodic
+ * iteration of Sec. 2.7, both to their tolerances). Write the converged system as A I = b with
+ *   (A I)_d = L_d I_d - P_d I_d - kappa_s V J,   J = (1/4pi) sum_d w_d I_d,
+ * L_d the transport operator without periodic faces and P_d the periodic inflow coupling. Its
+ * transpose is solved for lambda with
  *   g_{d,c} = w_d (dl_dGamma_c kappa_a,c V_c + dl_dJ_c / 4pi)        (dL/dI_{c,d})
- *   L_d^T lambda_d = g_d + w_d kappa_s,c V_c mu_c / 4pi,  mu_c = sum_d lambda_{d,c}
- * solved by the transposed source iteration (mu starts at 0; each pass sweeps every direction in
- * reversed topological order and recomputes mu), stopped when max |mu_new - mu_old| <=
- * tol_scat * max |mu_new| (0/0 counts as converged) or after max_it_scat passes. Then
+ *   L_d^T lambda_d = g_d + P_d^T lambda_d + w_d kappa_s,c V_c mu_c / 4pi,  mu_c = sum_d lambda_{d,c}
+ * by one transposed iteration that lags both couplings by a pass: mu and the periodic lambda start
+ * at 0; each pass sweeps every direction in reversed topological order, reading the partner's
+ * lambda of the previous pass across each periodic outflow side (P_d^T), then recomputes mu. It
+ * stops when max |mu_new - mu_old| <= tol_scat * max |mu_new| (0/0 counts as converged) or after
+ * max_it_scat passes. Then
  *   dL/dkappa_a,c = sum_d V_c I_{c,d} (w_d dl_dGamma_c - lambda_{d,c})
  *   dL/deps_c     = sum_d lambda_{d,c} / 4pi
  *   dL/dkappa_s,c = sum_d V_c lambda_{d,c} (J_c - I_{c,d})
- * Without scattering one transposed sweep gives lambda exactly. iters (or NULL) receives the
- * forward and the transposed sweep counts.
+ * Without either coupling one transposed sweep gives lambda exactly. iters (or NULL) receives the
+ * forward sweep count and the transposed pass count. Returns OR_NOT_CONVERGED (gradients still
+ * written) when the forward solve or the transposed iteration hit its maximum.
  */
 int oracle_adjoint(int64_t n_cells, int64_t n_faces, const double* volume, const int32_t* face_cells,
                    const double* area, const double* normal, const uint8_t* flags, int32_t n_dir,
                    const double* omega, const double* weight, int32_t n_groups, const double* kappa_abs,
                    const double* kappa_scat, const double* emissivity, const double* bc_inflow,
                    const double* dl_dJ, const double* dl_dGamma, double tol_scat, int32_t max_it_scat,
-                   int n_threads, double* grad_kappa_abs, double* grad_emissivity, double* grad_kappa_scat,
-                   int32_t* iters) {
+                   double tol_pbc, int32_t max_it_pbc, int n_threads, double* grad_kappa_abs,
+                   double* grad_emissivity, double* grad_kappa_scat, int32_t* iters) {
+    if (max_it_scat < 1 || max_it_pbc < 1) return OR_ERR_ARG;
     problem p;
     memset(&p, 0, sizeof p);
     p.n_cells = n_cells; p.n_faces = n_faces; p.volume = volume; p.face_cells = face_cells;
@@ -584,42 +592,33 @@ int oracle_adjoint(int64_t n_cells, int64_t n_faces, const double* volume, const
     p.emissivity = emissivity; p.bc_inflow = bc_inflow;
     int rc = check_problem(&p);
     if (rc != OR_OK) return rc;
-    for (int64_t f = 0; f < n_faces; ++f)
-        if (flags[f] & OR_FACE_PERIODIC) return OR_ERR_ARG;
-    if (max_it_scat < 1) return OR_ERR_ARG;
-    rc = build_sides(&p);
-    if (rc != OR_OK) { free_sides(&p); return rc; }
     int64_t N = n_cells, G = n_groups, NG = N * G, D = n_dir;
-    int has_scat = 0;
+    int has_scat = 0, has_pbc = 0;
     if (kappa_scat)
         for (int64_t i = 0; i < NG; ++i)
             if (kappa_scat[i] != 0.0) { has_scat = 1; break; }
-    int it_fwd = 0, it_adj = 0;
+    for (int64_t f = 0; f < n_faces; ++f)
+        if (flags[f] & OR_FACE_PERIODIC) { has_pbc = 1; break; }
     double* I = (double*)calloc((size_t)(D * NG > 0 ? D * NG : 1), sizeof(double));
-    double* lam = (double*)calloc((size_t)(D * NG > 0 ? D * NG : 1), sizeof(double));
-    double* q = (double*)malloc(sizeof(double) * (size_t)(NG > 0 ? NG : 1));
-    double* g = (double*)calloc((size_t)(D * NG > 0 ? D * NG : 1), sizeof(double));
     double* J = (double*)calloc((size_t)(NG > 0 ? NG : 1), sizeof(double));
-    double* Jold = (double*)calloc((size_t)(NG > 0 ? NG : 1), sizeof(double));
+    double* Gam = (double*)calloc((size_t)(NG > 0 ? NG : 1), sizeof(double));
+    double* lam = (double*)calloc((size_t)(D * NG > 0 ? D * NG : 1), sizeof(double));
+    double* lam_prev = (double*)calloc((size_t)(D * NG > 0 ? D * NG : 1), sizeof(double));
+    double* g = (double*)calloc((size_t)(D * NG > 0 ? D * NG : 1), sizeof(double));
     double* mu = (double*)calloc((size_t)(NG > 0 ? NG : 1), sizeof(double));
-    if (!I || !lam || !q || !g || !J || !Jold || !mu) { rc = OR_ERR_MEM; goto out; }
-    /* forward: the source iteration of Alg. 1 (a single sweep without scattering) */
-    for (;;) {
-        for (int64_t c = 0; c < N; ++c)
-            for (int k = 0; k < G; ++k) {
-                int64_t i = c * G + k;
-                q[i] = emissivity[i] / FOURPI + (has_scat ? kappa_scat[i] * volume[c] * Jold[i] : 0.0);
-            }
-        rc = run_dirs(&p, n_threads, 0, q, 0, NULL, I, NULL, NULL, 1);
-        if (rc != OR_OK) goto out;
-        ++it_fwd;
-        mean_intensity(&p, I, J);
-        if (!has_scat) break;
-        double res = scat_residual(NG, J, Jold);
-        memcpy(Jold, J, sizeof(double) * (size_t)NG);
-        if (res <= tol_scat || it_fwd >= max_it_scat) break;
-    }
-    /* transposed source iteration */
+    int built = 0, conv_fwd = 1, conv_adj = 1, it_adj = 0;
+    oracle_stats fst;
+    if (!I || !J || !Gam || !lam || !lam_prev || !g || !mu) { rc = OR_ERR_MEM; goto out; }
+    /* forward: the converged state, every intensity of the final sweep */
+    rc = oracle_solve(n_cells, n_faces, volume, face_cells, area, normal, flags, n_dir, omega, weight, n_groups,
+                      kappa_abs, kappa_scat, emissivity, bc_inflow, tol_scat, max_it_scat, tol_pbc, max_it_pbc,
+                      NULL, 0, n_threads, J, Gam, I, &fst);
+    if (rc == OR_NOT_CONVERGED) conv_fwd = 0;
+    else if (rc != OR_OK) goto out;
+    rc = build_sides(&p);
+    built = 1;
+    if (rc != OR_OK) goto out;
+    /* the transposed iteration */
     for (;;) {
         for (int32_t d = 0; d < n_dir; ++d)
             for (int64_t c = 0; c < N; ++c)
@@ -630,10 +629,10 @@ int oracle_adjoint(int64_t n_cells, int64_t n_faces, const double* volume, const
                     double gs = has_scat ? kappa_scat[i] * volume[c] * mu[i] / FOURPI : 0.0;
                     g[(int64_t)d * NG + i] = weight[d] * (gd + gj + gs);
                 }
-        rc = run_dirs(&p, n_threads, 1, g, NG, NULL, lam, NULL, NULL, 1);
+        rc = run_dirs(&p, n_threads, 1, g, NG, has_pbc ? lam_prev : NULL, lam, NULL, NULL, 1);
         if (rc != OR_OK) goto out;
         ++it_adj;
-        if (!has_scat) break;
+        if (!has_scat && !has_pbc) break;
         double dmax = 0.0, mmax = 0.0;
         for (int64_t i = 0; i < NG; ++i) {
             double m = 0.0;
@@ -643,7 +642,9 @@ int oracle_adjoint(int64_t n_cells, int64_t n_faces, const double* volume, const
             if (fabs(m) > mmax) mmax = fabs(m);
             mu[i] = m;
         }
-        if (dmax == 0.0 || dmax <= tol_scat * mmax || it_adj >= max_it_scat) break;
+        if (has_pbc) memcpy(lam_prev, lam, sizeof(double) * (size_t)(D * NG));
+        if (dmax == 0.0 || dmax <= tol_scat * mmax) break;
+        if (it_adj >= max_it_scat) { conv_adj = 0; break; }
     }
     for (int64_t c = 0; c < N; ++c)
         for (int k = 0; k < G; ++k) {
@@ -661,9 +662,10 @@ int oracle_adjoint(int64_t n_cells, int64_t n_faces, const double* volume, const
             grad_emissivity[i] = ge;
             if (grad_kappa_scat) grad_kappa_scat[i] = gs;
         }
-    if (iters) { iters[0] = it_fwd; iters[1] = it_adj; }
+    if (iters) { iters[0] = fst.it_scat; iters[1] = it_adj; }
+    rc = (conv_fwd && conv_adj) ? OR_OK : OR_NOT_CONVERGED;
 out:
-    free(I); free(lam); free(q); free(g); free(J); free(Jold); free(mu);
-    free_sides(&p);
+    free(I); free(J); free(Gam); free(lam); free(lam_prev); free(g); free(mu);
+    if (built) free_sides(&p);
     return rc;
 }

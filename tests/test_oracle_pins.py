@@ -420,3 +420,57 @@ def test_adjoint_without_scattering_is_one_transposed_sweep():
     assert r["it_forward"] == r["it_adjoint"] == 1
     assert np.array_equal(r["grad_kappa_abs"], gk) and np.array_equal(r["grad_emissivity"], ge)
 
+
+# ---- (g) the adjoint through the periodic iteration ---------------------------------------------
+@pytest.mark.parametrize("albedo", [0.0, 0.5])
+def test_adjoint_periodic_dense_transpose(albedo):
+    # the transposed iteration reads the partner's lambda across periodic outflow sides: its fixed
+    # point is the transposed solve of the whole system with the periodic coupling in the matrix
+    p = configs.voronoi_small(200, periodic_box=True, n_dir=6, n_groups=2, seed=43, scatter_albedo=albedo)
+    ks = p.kappa_scat if albedo else np.zeros_like(p.kappa_abs)
+    rng = np.random.default_rng(8)
+    dg = rng.normal(size=p.kappa_abs.shape)
+    dj = rng.normal(size=p.kappa_abs.shape)
+    r = oracle.adjoint_full(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, kappa_scat=ks, dl_dJ=dj,
+                            dl_dGamma=dg, tol_scat=1e-15, max_it_scat=5000, tol_pbc=1e-15, max_it_pbc=5000)
+    assert r["rc"] == 0 and r["it_adjoint"] > 1
+    V = p.mesh.volume[:, None]
+    gsrc = p.weight[:, None, None] * (dg * p.kappa_abs * V + dj / (4 * math.pi))[None]
+    lam = dense.adjoint_coupled(p.mesh, p.omega, p.weight, p.kappa_abs, ks, gsrc)
+    assert rel(r["grad_emissivity"], lam.sum(axis=0) / (4 * math.pi)) <= 1e-11
+
+
+@pytest.mark.parametrize("albedo", [0.0, 0.5])
+def test_adjoint_periodic_finite_differences(albedo):
+    p = configs.voronoi_small(300, periodic_box=True, n_dir=8, n_groups=1, seed=45, scatter_albedo=albedo,
+                              n_src=6)
+    ks = p.kappa_scat if albedo else np.zeros_like(p.kappa_abs)
+    rng = np.random.default_rng(9)
+    T = rng.random(p.kappa_abs.shape) * np.median(p.emissivity[p.emissivity > 0])
+    kw = dict(tol_scat=1e-15, max_it_scat=5000, tol_pbc=1e-15, max_it_pbc=5000)
+
+    def loss(ka, em, k_s):
+        # the fused loops reach the nested loops' fixed point in far fewer sweeps
+        r = oracle.solve(p.mesh, p.omega, p.weight, ka, em, kappa_scat=k_s, fused=bool(albedo), threads=4, **kw)
+        assert r["rc"] == 0
+        return math.fsum(((r["Gamma"] - T) ** 2).ravel()), r["Gamma"]
+
+    _, G0 = loss(p.kappa_abs, p.emissivity, ks)
+    r = oracle.adjoint_full(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, kappa_scat=ks,
+                            dl_dGamma=2 * (G0 - T), **kw)
+    assert r["rc"] == 0
+    grads = {"ka": r["grad_kappa_abs"], "em": r["grad_emissivity"]}
+    base = {"ka": p.kappa_abs, "em": p.emissivity, "ks": ks}
+    if albedo:
+        grads["ks"] = r["grad_kappa_scat"]
+    for name, gr in grads.items():
+        big = np.argsort(np.abs(gr).ravel())[-30:]
+        for c in rng.choice(big, 4, replace=False):
+            h = 1e-4 * max(base[name][c, 0], 1e-3 * base[name].max())
+            a_p = {k: v.copy() for k, v in base.items()}
+            a_m = {k: v.copy() for k, v in base.items()}
+            a_p[name][c, 0] += h
+            a_m[name][c, 0] -= h
+            fd = (loss(a_p["ka"], a_p["em"], a_p["ks"])[0] - loss(a_m["ka"], a_m["em"], a_m["ks"])[0]) / (2 * h)
+            assert gr[c, 0] == pytest.approx(fd, rel=1e-5, abs=1e-7 * np.abs(gr).max()), (name, c)
+
