@@ -191,25 +191,29 @@ sweep_status sweep_levels(sweep_ctx* ctx, int32_t dir, int32_t* level, int32_t* 
  * host pointer. Errors: INVALID_ARG (no solve yet or bad dir). */
 sweep_status sweep_intensity(sweep_ctx* ctx, int32_t dir, double* intensity);
 
-/* Adjoint (transpose) of the sweep for a loss L(J, Gamma), for problems without periodic
- * faces. For each direction it solves
+/* Adjoint (transpose) of the sweep for a loss L(J, Gamma). For each direction it solves
  * L_Omega^T lambda = g, g_c = w_d (dL/dGamma_c kappa_a,c V_c + dL/dJ_c / 4pi), as a sweep
- * in reversed level order, recomputing the forward intensities per batch of
- * opts->dir_batch directions instead of storing them, and accumulates in FP64
+ * in reversed level order, and accumulates in FP64
  *   dL/dkappa_a,c = sum_d V_c I_c,d (w_d dL/dGamma_c - lambda_c,d),  dL/deps_c = sum_d lambda_c,d / 4pi.
- * With scattering (Alg. 1) the forward intensities are the converged source iteration
- * (tol_scat, max_it_scat) and lambda solves the transposed coupled system
- *   L_Omega^T lambda_d = g_d + w_d kappa_s,c V_c mu_c / 4pi,  mu_c = sum_d lambda_c,d,
- * by the transposed source iteration: mu starts at 0, each pass sweeps every direction in
- * reversed level order, and the iteration stops when max |change of mu| <= tol_scat max |mu|
- * or after max_it_scat passes. grad_kappa_scat (or NULL) receives
+ * Without scattering and periodic faces the forward intensities are recomputed per batch of
+ * opts->dir_batch directions instead of stored. With scattering (Alg. 1) or periodic faces
+ * (Sec. 2.7) the forward state is the solve itself (sweep_solve with the same opts, both
+ * iterations to their tolerances), and lambda solves the transpose of the coupled system,
+ *   L_Omega^T lambda_d = g_d + P_d^T lambda_d + w_d kappa_s,c V_c mu_c / 4pi,  mu_c = sum_d lambda_c,d,
+ * P_d the periodic inflow coupling, by one transposed iteration that lags both couplings by a
+ * pass: mu and the previous pass's lambda start at 0, each pass sweeps every direction in
+ * reversed level order reading the partner's lambda of the previous pass across periodic outflow
+ * sides, and the iteration stops when max |change of mu| <= tol_scat max |mu| or after
+ * max_it_scat passes. grad_kappa_scat (or NULL) receives
  *   dL/dkappa_s,c = sum_d V_c lambda_c,d (J_c - I_c,d).
- * With scattering or grad_kappa_scat, dir_batch is ignored (the iterations couple all directions).
+ * With scattering, periodic faces or grad_kappa_scat, dir_batch is ignored.
  * dl_dJ, dl_dGamma [n_cells][G] (either may be NULL = zero); outputs [n_cells][G], host pointers
  * for sweep_adjoint and device pointers for sweep_adjoint_dev. stats (or NULL): it_scat = forward
- * sweeps, it_pbc = transposed sweeps, res_scat / res_pbc = their last relative changes.
- * Errors: INVALID_ARG (periodic faces present, missing set_*), CYCLE, TIMEOUT, OOM, CUDA;
- * NOT_CONVERGED (gradients still written) when either source iteration hit max_it_scat. */
+ * sweeps, it_pbc = transposed passes, res_scat / res_pbc = their last relative changes. The solve
+ * buffers (sweep_intensity) then hold the forward state.
+ * Errors: INVALID_ARG (more than 4 groups, missing set_*), CYCLE, TIMEOUT, OOM, CUDA;
+ * NOT_CONVERGED (gradients still written) when the forward solve or the transposed iteration hit
+ * its maximum. */
 sweep_status sweep_adjoint(sweep_ctx* ctx, const sweep_opts* opts, const double* dl_dJ, const double* dl_dGamma,
                            double* grad_kappa_abs, double* grad_emissivity, double* grad_kappa_scat,
                            sweep_stats* stats);

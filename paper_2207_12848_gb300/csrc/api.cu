@@ -1211,7 +1211,6 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
     if (!c) return SWEEP_ERR_INVALID_ARG;
     cudaSetDevice(c->device);
     if (!c->has_mesh || !c->has_dirs || !c->has_mat) return bad(c, "set mesh, directions and material first");
-    if (c->mesh.n_pcells > 0) return bad(c, "the adjoint does not support periodic faces");
     if (c->G > 4) return bad(c, "the adjoint supports at most 4 groups");
     if (!gk_out || !ge_out) return bad(c, "null gradient output");
     sweep_opts o;
@@ -1225,12 +1224,13 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
     const int64_t N = c->mesh.N;
     const int G = c->G, D = c->D;
     const size_t NG = (size_t)N * G;
-    // with scattering both source iterations couple all directions (and the kappa_s gradient needs J):
-    // one batch of every direction
-    const bool scat = c->has_scat;
-    const bool need_J = scat || gks_out;
-    if (scat && o.max_it_scat < 1) return bad(c, "max_it_scat must be >= 1");
-    int B = (!need_J && o.dir_batch > 0 && o.dir_batch < D) ? o.dir_batch : D;
+    // With scattering or periodic faces the iterations couple all directions, and the kappa_s gradient
+    // needs J: the forward state is then the solve itself (one batch of every direction), and the
+    // transposed iteration lags both couplings by a pass.
+    const bool scat = c->has_scat, pbc = c->mesh.n_pcells > 0;
+    const bool coupled = scat || pbc || gks_out;
+    if ((scat || pbc) && o.max_it_scat < 1) return bad(c, "max_it_scat must be >= 1");
+    int B = (!coupled && o.dir_batch > 0 && o.dir_batch < D) ? o.dir_batch : D;
     sweep_stats S;
     memset(&S, 0, sizeof S);
     const int64_t launches0 = c->launches;
@@ -1256,22 +1256,29 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
     CK(cudaMemsetAsync(ge, 0, sizeof(double) * NG, c->st), "init");
     DevBuf<double> b_gks, b_mu;
     if (gks_out) CK(cudaMalloc(&b_gks.p, sizeof(double) * (NG > 0 ? NG : 1)), "alloc");
-    if (scat) {
+    if (scat || pbc) {
         CK(cudaMalloc(&b_mu.p, sizeof(double) * (2 * NG > 0 ? 2 * NG : 1)), "alloc");
         CK(cudaMemsetAsync(b_mu.p, 0, sizeof(double) * 2 * NG, c->st), "init");
     }
-    sweep_status s = ensure_cm(c, 2 * NG);
-    if (s != SWEEP_OK) return s;
-    const int nblk = nblocks256(NG);
-    if (need_J) {
-        s = ensure_ng(c, NG);
-        if (s != SWEEP_OK) return s;
-        s = ensure_partial(c, nblk + 1);
-        if (s != SWEEP_OK) return s;
+    sweep_status s = SWEEP_OK;
+    // forward state of the coupled problems: the solve (both iterations to their tolerances), whose
+    // final sweep's intensities and J stay on the device
+    int it_fwd = 0;
+    bool conv_fwd = true;
+    double res_fwd = 0.0;
+    if (coupled) {
+        sweep_stats fs;
+        s = solve_impl(c, &o, nullptr, nullptr, true, &fs);
+        if (s == SWEEP_NOT_CONVERGED) conv_fwd = false;
+        else if (s != SWEEP_OK) return s;
+        it_fwd = fs.n_sweeps;
+        res_fwd = pbc ? fs.res_pbc : fs.res_scat;
     }
+    s = ensure_cm(c, 2 * NG);
+    if (s != SWEEP_OK) return s;
     // batch buffers
     const size_t es = prec == 64 ? 8 : 4;
-    size_t bI = es * (size_t)N * B * G, bL = es * (size_t)N * B * 2 * G;
+    size_t bI = coupled ? es : es * (size_t)N * B * G, bL = es * (size_t)N * B * 2 * G;  // coupled: the solve's
     if (c->adj_bytes_I != bI || c->adj_bytes_L != bL) {
         dfree(c->adjI);
         dfree(c->adjL);
@@ -1280,10 +1287,17 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
         c->adj_bytes_I = bI;
         c->adj_bytes_L = bL;
     }
-    // fresh buffers each call: sign state starts at 0 after clearing
+    // fresh buffers each call: sign state starts at 0 after clearing; with periodic faces a second
+    // lambda buffer holds the previous pass
     CK(cudaMemsetAsync(c->adjI, 0, bI, c->st), "init");
     CK(cudaMemsetAsync(c->adjL, 0, bL, c->st), "init");
-    int signI = 0, signL = 0;
+    DevBuf<char> b_lam2;
+    if (pbc) {
+        CK(cudaMalloc(&b_lam2.p, bL > 0 ? bL : 4), "alloc adjoint batch");
+        CK(cudaMemsetAsync(b_lam2.p, 0, bL, c->st), "init");
+    }
+    void* lbuf[2] = {c->adjL, b_lam2.p};
+    int signI = 0, signL[2] = {0, 0}, kl = 0;
     Bc32 bc32;
     if (prec == 32 && c->bc) {
         int64_t n = c->mesh.NB * G;
@@ -1292,9 +1306,9 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
         ++c->launches;
     }
     float t_sweep = 0.f, tcl = 0.f, tlv = 0.f;
-    int n_sweeps = 0, it_fwd = 0, it_adj = 0;
-    bool conv_fwd = true, conv_adj = true;
-    double res_fwd = 0.0, res_adj = 0.0;
+    int n_sweeps = it_fwd, it_adj = 0;
+    bool conv_adj = true;
+    double res_adj = 0.0;
     for (int d0 = 0; d0 < D; d0 += B) {
         const int nb = (D - d0) < B ? (D - d0) : B;
         Levels* L;
@@ -1309,12 +1323,13 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
         if (s != SWEEP_OK) return s;
         tcl += a1;
         tlv += a2;
-        // forward intensities of this batch (recomputed, not stored across batches); with scattering the
-        // source iteration of Alg. 1 to convergence, J_old starting at 0
         const void* cm = prec == 64 ? (const void*)c->cm64 : (const void*)c->cm32;
-        if (scat) CK(cudaMemsetAsync(c->Jold, 0, sizeof(double) * NG, c->st), "init");
-        for (;;) {
-            CKL(launch_prep_material(N, G, c->mesh.vol, c->ka, scat ? c->ks : nullptr, c->em, scat ? c->Jold : nullptr,
+        const void* Ifwd = c->adjI;
+        if (coupled) {
+            Ifwd = c->sb.I[c->sb.last];
+        } else {
+            // forward intensities of this batch (recomputed, not stored across batches)
+            CKL(launch_prep_material(N, G, c->mesh.vol, c->ka, nullptr, c->em, nullptr,
                                     prec == 32 ? c->cm32 : nullptr, prec == 64 ? c->cm64 : nullptr, c->st), "prep");
             int pI = !signI;
             SweepArgs a = make_args(c, *L, prec, cm, c->adjI, nullptr, G, pI, 0, 0, &o);
@@ -1324,34 +1339,26 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
             signI = pI;
             ++n_sweeps;
             ++it_fwd;
-            if (!need_J) break;
-            CKL(launch_tally(prec, c->adjI, N, G, D, 0, c->w64, c->wsum, c->mesh.vol, c->ka, c->em, c->J, c->Gam,
-                            c->partial, nblk, c->st), "tally");
-            if (!scat) break;
-            CK(cudaMemsetAsync(c->dmax, 0, sizeof(unsigned long long), c->st), "init");
-            CKL(launch_scat_residual(NG, c->J, c->Jold, c->dmax, c->st), "scattering residual");
-            res_fwd = read_max(c);
-            if (res_fwd <= o.tol_scat) break;
-            if (it_fwd >= o.max_it_scat) { conv_fwd = false; break; }
         }
-        // transposed sweep with split non-negative sources (2G groups); with scattering the transposed
-        // source iteration, mu starting at 0
+        // transposed sweep with split non-negative sources (2G groups); with scattering or periodic faces
+        // the transposed iteration: mu and the previous pass's lambda start at 0
         CKL(launch_prep_adjoint_src(N, G, c->mesh.vol, c->ka, scat ? c->ks : nullptr, d_dlj, d_dlg,
                                    prec == 32 ? c->cm32 : nullptr, prec == 64 ? c->cm64 : nullptr, c->st),
            "prep adjoint");
         for (;;) {
-            int pL = !signL;
-            SweepArgs r = make_args(c, *L, prec, cm, c->adjL, nullptr, 2 * G, pL, 1, 0, &o);
+            int pL = !signL[kl];
+            SweepArgs r = make_args(c, *L, prec, cm, lbuf[kl], pbc ? lbuf[1 - kl] : nullptr, 2 * G, pL, 1, 0, &o);
             r.debug_stall = 0;
             s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, lanes, 0, r, nullptr, &t_sweep);
             if (s != SWEEP_OK) return s;
-            signL = pL;
+            signL[kl] = pL;
             ++n_sweeps;
             ++it_adj;
-            if (!scat) break;
+            if (!scat && !pbc) break;
             CK(cudaMemsetAsync(c->dmax, 0, 2 * sizeof(unsigned long long), c->st), "init");
-            CKL(launch_adjoint_mu(prec, c->adjL, N, G, D, c->mesh.vol, c->ka, c->ks, d_dlj, d_dlg, b_mu.p,
-                                 prec == 32 ? c->cm32 : nullptr, prec == 64 ? c->cm64 : nullptr, c->dmax, c->st),
+            CKL(launch_adjoint_mu(prec, lbuf[kl], N, G, D, c->mesh.vol, c->ka, scat ? c->ks : nullptr, d_dlj, d_dlg,
+                                 b_mu.p, prec == 32 ? c->cm32 : nullptr, prec == 64 ? c->cm64 : nullptr, c->dmax,
+                                 c->st),
                "transposed source");
             unsigned long long hm[2] = {0, 0};
             CK(cudaMemcpyAsync(hm, c->dmax, sizeof hm, cudaMemcpyDeviceToHost, c->st), "read");
@@ -1362,9 +1369,10 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
             res_adj = dm == 0.0 ? 0.0 : (mm > 0.0 ? dm / mm : INFINITY);
             if (dm == 0.0 || dm <= o.tol_scat * mm) break;
             if (it_adj >= o.max_it_scat) { conv_adj = false; break; }
+            if (pbc) kl = 1 - kl;
         }
-        CKL(launch_grad_scat(prec, c->adjI, c->adjL, N, G, nb, d0, c->w64, c->mesh.vol, d_dlg,
-                            need_J ? c->J : nullptr, gk, ge, b_gks.p, c->st),
+        CKL(launch_grad_scat(prec, Ifwd, lbuf[kl], N, G, nb, d0, c->w64, c->mesh.vol, d_dlg,
+                            coupled ? c->J : nullptr, gk, ge, b_gks.p, c->st),
            "gradient");
     }
     cudaMemcpyKind kout = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;

@@ -131,7 +131,7 @@ __device__ __forceinline__ bool group_task(const SweepArgs& a, uint32_t entry, u
             rec[k] = s < r1 ? ld_stream_int4(a.side + s, pol) : make_int4(0, 0, 0, 0);
         }
         real w[U];
-        int kind[U];  // 0 none, 1 interior inflow, 2 periodic inflow, 3 boundary inflow
+        int kind[U];  // 0 none, 1 interior inflow, 2 periodic inflow (adjoint: its transpose), 3 boundary inflow
 #pragma unroll
         for (int k = 0; k < U; ++k) {
             const uint32_t s = base + gl + k * L;
@@ -155,7 +155,8 @@ __device__ __forceinline__ bool group_task(const SweepArgs& a, uint32_t entry, u
                 if (inflow) {
                     const int32_t nb = rec[k].x;
                     if (nb >= 0 && !(nb & NBR_PERIODIC)) kind[k] = 1;
-                    else if (!a.reverse) kind[k] = nb >= 0 ? 2 : 3;
+                    else if (nb >= 0) kind[k] = 2;  // the partner's value of the previous sweep or pass
+                    else if (!a.reverse) kind[k] = 3;
                 }
             }
         }
@@ -1014,9 +1015,9 @@ __device__ __forceinline__ void plain_task(const SweepArgs& a, uint32_t entry) {
         if (!inflow) continue;
         const double* src = nullptr;
         if (nb >= 0 && !(nb & NBR_PERIODIC)) src = I + (slab + (uint32_t)nb) * G;
-        else if (a.reverse) continue;
         else if (nb >= 0) src = a.Iprev ? reinterpret_cast<const double*>(a.Iprev) + (slab + (nb & NBR_MASK)) * G
                                         : nullptr;
+        else if (a.reverse) continue;
         else src = a.bc ? reinterpret_cast<const double*>(a.bc) + (size_t)(-1 - nb) * G : nullptr;
         if (!src) continue;
         for (int g = 0; g < GM; ++g)

@@ -365,9 +365,9 @@ __global__ void k_grad(const real* I, const real* lam, int64_t N, int G, int nd,
     if (J && gks) gks[i] = ss;
 }
 
-// Transposed source iteration: mu+- = sum_d lambda+-_d (no direction weight: the reverse sweep puts
-// w_d on its source), the largest change and the largest magnitude of mu = mu+ - mu- (dmax[0],
-// dmax[1]), and the split sources of the next transposed sweep, g+- + kappa_s V mu+- / 4pi.
+// Transposed iteration: mu+- = sum_d lambda+-_d (no direction weight: the reverse sweep puts w_d on
+// its source), the largest change and the largest magnitude of mu = mu+ - mu- (dmax[0], dmax[1]), and
+// the split sources of the next transposed sweep, g+- + kappa_s V mu+- / 4pi (ks may be null).
 template <typename real>
 __global__ void k_adj_mu(const real* lam, int64_t N, int G, int nd, const double* vol, const double* ka,
                          const double* ks, const double* dlj, const double* dlg, double* mu, float2* cm32,
@@ -393,9 +393,9 @@ __global__ void k_adj_mu(const real* lam, int64_t N, int G, int nd, const double
     double V = vol[c];
     double src = dadd(dlg ? dmul(dmul(dlg[i], ka[i]), V) : 0.0, dlj ? dlj[i] / FOURPI : 0.0);
     double gp = src > 0.0 ? src : 0.0, gm = src < 0.0 ? -src : 0.0;
-    double kv = dmul(ks[i], V);
+    double kv = ks ? dmul(ks[i], V) : 0.0;
     double qp = dadd(gp, dmul(kv, sp) / FOURPI), qm = dadd(gm, dmul(kv, sm) / FOURPI);
-    double dnm = dmul(dadd(ka[i], ks[i]), V);
+    double dnm = dmul(dadd(ka[i], ks ? ks[i] : 0.0), V);
     if (cm64) {
         cm64[o + g] = make_double2(qp, dnm);
         cm64[o + G + g] = make_double2(qm, dnm);

@@ -69,28 +69,33 @@ def test_autograd_only_gamma_used_and_context_reused(ctx):
     assert _rel_max(ge.cpu().numpy(), oe) <= 1e-9
 
 
-def test_autograd_through_scattering(ctx):
-    # kappa_scat as a third differentiable input: forward the source iteration, backward its transpose
+@pytest.mark.parametrize("kind", ["scattering", "periodic", "both"])
+def test_autograd_through_the_iterations(ctx, kind):
+    # forward the scattering and/or periodic iterations, backward their transpose; kappa_scat as a
+    # third differentiable input where there is scattering
     torch = pytest.importorskip("torch")
     from paper_2207_12848_gb300 import transport_solve
-    p = configs.voronoi_small(3000, n_dir=12, n_groups=2, seed=75, scatter_albedo=0.5, n_src=6)
+    scat, box = kind != "periodic", kind != "scattering"
+    p = configs.voronoi_small(3000, periodic_box=box, n_dir=12, n_groups=2, seed=75,
+                              scatter_albedo=0.5 if scat else 0.0, n_src=6)
     ctx.set_mesh(p.mesh)
     ctx.set_directions(p.omega, p.weight)
     rng = np.random.default_rng(76)
     T = rng.random(p.kappa_abs.shape) * 1e-3
     c = rng.normal(size=p.kappa_abs.shape)
-    kw = dict(precision=64, tol_scat=1e-12, max_it_scat=2000)
+    it = dict(tol_scat=1e-12, max_it_scat=2000, tol_pbc=1e-12, max_it_pbc=2000)
     dev = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda", requires_grad=True)
-    ka, em, ks = dev(p.kappa_abs), dev(p.emissivity), dev(p.kappa_scat)
-    J, Gamma = transport_solve(ctx, ka, em, ks, **kw)
+    ka, em = dev(p.kappa_abs), dev(p.emissivity)
+    ks = dev(p.kappa_scat) if scat else None
+    J, Gamma = transport_solve(ctx, ka, em, ks, precision=64, **it)
     loss = ((Gamma - torch.tensor(T, device="cuda")) ** 2).sum() + (torch.tensor(c, device="cuda") * J).sum()
-    gk, ge, gs = torch.autograd.grad(loss, (ka, em, ks))
-    r = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, kappa_scat=p.kappa_scat,
-                     tol_scat=1e-12, max_it_scat=2000, threads=8)
-    o = oracle.adjoint_full(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, kappa_scat=p.kappa_scat,
-                            dl_dJ=c, dl_dGamma=2.0 * (r["Gamma"] - T), tol_scat=1e-12, max_it_scat=2000, threads=8)
+    grads = torch.autograd.grad(loss, (ka, em, ks) if scat else (ka, em))
+    k_s = p.kappa_scat if scat else None
+    r = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, kappa_scat=k_s, threads=8, **it)
+    o = oracle.adjoint_full(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, kappa_scat=k_s, dl_dJ=c,
+                            dl_dGamma=2.0 * (r["Gamma"] - T), threads=8, **it)
     assert _rel_max(J.detach().cpu().numpy(), r["J"]) <= 1e-9
-    assert _rel_max(gk.cpu().numpy(), o["grad_kappa_abs"]) <= 1e-8
-    assert _rel_max(ge.cpu().numpy(), o["grad_emissivity"]) <= 1e-8
-    assert _rel_max(gs.cpu().numpy(), o["grad_kappa_scat"]) <= 1e-8
+    names = ("grad_kappa_abs", "grad_emissivity", "grad_kappa_scat")
+    for gr, name in zip(grads, names):
+        assert _rel_max(gr.cpu().numpy(), o[name]) <= 1e-8, name
 
