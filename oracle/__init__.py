@@ -33,6 +33,7 @@ _LIB = None
 _LOCK = threading.Lock()
 
 OK, ERR_ARG, ERR_CYCLE, NOT_CONVERGED, ERR_MEM = 0, 1, 2, 3, 5
+LAWS = {"balance": 0, "exp": 1}
 
 
 def build(force: bool = False) -> str:
@@ -66,7 +67,7 @@ def _lib():
             lib.oracle_levels.argtypes = [I64, I64, P, P, P, P, P, I32, P, P, P, ctypes.c_int]
             lib.oracle_solve.restype = ctypes.c_int
             lib.oracle_solve.argtypes = [I64, I64, P, P, P, P, P, I32, P, P, I32, P, P, P, P, D, I32, D, I32, P,
-                                         ctypes.c_int, ctypes.c_int, P, P, P, ctypes.POINTER(Stats)]
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, ctypes.POINTER(Stats)]
             lib.oracle_adjoint.restype = ctypes.c_int
             lib.oracle_adjoint.argtypes = [I64, I64, P, P, P, P, P, I32, P, P, I32, P, P, P, P, P, P, D, I32, D,
                                            I32, ctypes.c_int, P, P, P, P]
@@ -107,7 +108,7 @@ def levels(mesh, omega, threads: int = 1):
 
 def solve(mesh, omega, weight, kappa_abs, emissivity, kappa_scat=None, bc_inflow=None, tol_scat=1e-6,
           max_it_scat=100, tol_pbc=1e-6, max_it_pbc=100, prev_init=None, threads: int = 1,
-          want_intensity: bool = False, fused: bool = False):
+          want_intensity: bool = False, fused: bool = False, law: str = "balance"):
     """Mean intensity J[N,G], absorbed rate Gamma[N,G], stats (and I[D,N,G] if asked)."""
     om = _c(omega, np.float64).reshape(-1, 3)
     w = _c(weight, np.float64)
@@ -126,7 +127,8 @@ def solve(mesh, omega, weight, kappa_abs, emissivity, kappa_scat=None, bc_inflow
     I = np.zeros((D, N, G)) if want_intensity else None
     st = Stats()
     rc = _lib().oracle_solve(*margs, D, _ptr(om), _ptr(w), G, _ptr(ka), _ptr(ks), _ptr(em), _ptr(bc), tol_scat,
-                             max_it_scat, tol_pbc, max_it_pbc, _ptr(pi), int(fused), threads, _ptr(J), _ptr(Gam),
+                             max_it_scat, tol_pbc, max_it_pbc, _ptr(pi), int(fused), LAWS[law], threads, _ptr(J),
+                             _ptr(Gam),
                              _ptr(I),
                              ctypes.byref(st))
     out = {"rc": rc, "J": J, "Gamma": Gam, "stats": st.as_dict()}

@@ -9,6 +9,10 @@ this matrix lower triangular; here it is simply solved):
     row c:  (P_c + kappa_t,c V_c) I_c  -  sum_{faces f with inflow into c} |a_f| I_other(f)  =  q_c (+ boundary inflow)
     a_f = A_f n_f . Omega,  P_c = sum over faces with outward n.Omega > 0 of |a_f|
 
+The EXP law (solve_coupled_exp) is the same kind of system with the outgoing intensity
+P_c I_c = exp(-tau_c) F_in,c + q_c, tau_c = kappa_t,c V_c / P_c, and J formed from the cell mean
+(F_in,c / P_c)(1 - exp(-tau_c)) / tau_c.
+
 Periodic faces enter as ordinary couplings to the partner cell, so the matrix is
 cyclic and its solution is the fixed point the periodic iteration of Sec. 2.7
 converges to. Isotropic scattering couples the directions through
@@ -118,3 +122,73 @@ def adjoint_direction(mesh, om, kappa_abs, g_src):
         L, _ = transport_matrix(mesh, om, kappa_abs, None, g)
         lam[:, g] = np.linalg.solve(L.T, g_src[:, g])
     return lam
+
+
+# ---- the EXP law: outgoing (exp(-tau) F_in + q) / P, cell mean (F_in / P)(1 - exp(-tau)) / tau ----
+def inflow_operator(mesh, om, bc_inflow=None, group=0):
+    """For one direction: M (N x N) and b (N) with the inflow flux F_in = M I + b of every cell, and
+    the projected outflow area P (N). Periodic faces couple to the partner cell."""
+    N = mesh.n_cells
+    M = np.zeros((N, N))
+    b = np.zeros(N)
+    P = np.zeros(N)
+    t = _dot(mesh.normal, om)
+    a = mesh.area * np.abs(t)
+    bidx = np.cumsum((mesh.flags & FACE_BOUNDARY) != 0) - 1
+    for f in range(mesh.n_faces):
+        c0, c1 = int(mesh.face_cells[f, 0]), int(mesh.face_cells[f, 1])
+        if t[f] == 0.0:
+            continue
+        if mesh.flags[f] & FACE_BOUNDARY:
+            if t[f] > 0:
+                P[c0] += a[f]
+            elif bc_inflow is not None:
+                b[c0] += a[f] * bc_inflow[bidx[f], group]
+            continue
+        up, down = (c0, c1) if t[f] > 0 else (c1, c0)
+        P[up] += a[f]
+        M[down, up] += a[f]
+    return M, b, P
+
+
+def _exp_factors(kt_V, P):
+    tau = kt_V / P
+    f = np.where(tau > 0, -np.expm1(-tau) / np.where(tau > 0, tau, 1.0), 1.0)
+    return np.exp(-tau), f
+
+
+def solve_coupled_exp(mesh, omega, weight, kappa_abs, emissivity, kappa_scat=None, bc_inflow=None):
+    """EXP law, all directions with isotropic scattering through the cell-mean J; returns the outgoing
+    I[D,N,G], the cell mean Ibar[D,N,G], J[N,G] and Gamma[N,G]."""
+    D, N = omega.shape[0], mesh.n_cells
+    G = kappa_abs.shape[1]
+    ks = np.zeros_like(kappa_abs) if kappa_scat is None else kappa_scat
+    I = np.zeros((D, N, G))
+    Ibar = np.zeros((D, N, G))
+    for g in range(G):
+        ktV = (kappa_abs[:, g] + ks[:, g]) * mesh.volume
+        ops = [inflow_operator(mesh, omega[d], bc_inflow, g) for d in range(D)]
+        assert all((P > 0).all() for _, _, P in ops)
+        A = np.zeros((D * N, D * N))
+        rhs = np.zeros(D * N)
+        # mean operator of each direction: Ibar_d = diag(f_d / P_d) (M_d I_d + b_d)
+        mean_op = []
+        for d, (M, b, P) in enumerate(ops):
+            e, f = _exp_factors(ktV, P)
+            mean_op.append(((f / P)[:, None] * M, (f / P) * b))
+            sl = slice(d * N, (d + 1) * N)
+            A[sl, sl] = np.diag(P) - e[:, None] * M
+            rhs[sl] = emissivity[:, g] / (4 * math.pi) + e * b
+        c = ks[:, g] * mesh.volume / (4 * math.pi)
+        for d in range(D):
+            for d2 in range(D):
+                Mm, bm = mean_op[d2]
+                A[d * N:(d + 1) * N, d2 * N:(d2 + 1) * N] -= weight[d2] * c[:, None] * Mm
+                rhs[d * N:(d + 1) * N] += weight[d2] * c * bm
+        I[:, :, g] = np.linalg.solve(A, rhs).reshape(D, N)
+        for d in range(D):
+            Mm, bm = mean_op[d]
+            Ibar[d, :, g] = Mm @ I[d, :, g] + bm
+    J = np.einsum("d,dng->ng", weight, Ibar) / (4 * math.pi)
+    Gam = kappa_abs * mesh.volume[:, None] * 4 * math.pi * J
+    return I, Ibar, J, Gam

@@ -52,6 +52,7 @@
 
 enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_CYCLE = 2, OR_NOT_CONVERGED = 3, OR_ERR_MEM = 5 };
 enum { OR_FACE_BOUNDARY = 1, OR_FACE_PERIODIC = 2 };
+enum { OR_LAW_BALANCE = 0, OR_LAW_EXP = 1 };
 
 typedef struct {
     /* problem (caller-owned) */
@@ -69,6 +70,8 @@ typedef struct {
     const double* kappa_scat; /* [N][G] or NULL */
     const double* emissivity; /* [N][G] */
     const double* bc_inflow;  /* [n_boundary_faces][G] or NULL */
+    int law;                  /* OR_LAW_BALANCE or OR_LAW_EXP (forward sweeps only) */
+    double* mean;             /* EXP: [D][N][G] cell-mean intensity of the last sweep (solver-owned) */
     /* derived: per-cell list of face sides */
     int64_t* side_start; /* [N+1] */
     int64_t* side_face;  /* face index */
@@ -142,6 +145,7 @@ typedef struct {
     const double* src; /* [N][G] source q (forward) or adjoint source g */
     const double* prev; /* [N][G] previous-sweep intensity for periodic inflow, or NULL */
     double* out;       /* [N][G] solution */
+    double* mean;      /* [N][G] EXP law: cell-mean intensity, or NULL */
     int32_t* level;    /* [N] or NULL */
     int32_t* depth;
     /* scratch */
@@ -174,7 +178,8 @@ static int sweep_one(dir_sweep* s, int solve) {
         if (solve) {
             double P = 0.0;
             double acc[64];
-            for (int g = 0; g < G; ++g) acc[g] = s->src[c * G + g];
+            /* BALANCE sums the source first, then the inflows; EXP keeps the inflow F_in apart */
+            for (int g = 0; g < G; ++g) acc[g] = s->mean ? 0.0 : s->src[c * G + g];
             for (int64_t k = p->side_start[c]; k < p->side_start[c + 1]; ++k) {
                 int64_t f = p->side_face[k];
                 int sign = p->side_sign[k];
@@ -203,7 +208,23 @@ static int sweep_one(dir_sweep* s, int solve) {
             }
             for (int g = 0; g < G; ++g) {
                 double kt = p->kappa_abs[c * G + g] + (p->kappa_scat ? p->kappa_scat[c * G + g] : 0.0);
-                s->out[c * G + g] = acc[g] / (P + kt * p->volume[c]);
+                if (!s->mean) {
+                    s->out[c * G + g] = acc[g] / (P + kt * p->volume[c]);
+                } else if (P > 0.0) {
+                    /* EXP: the inflow crosses the mean chord V/P with transmission exp(-tau) and the
+                     * cell's own source leaves unattenuated (Sec. 2.6); the cell-mean intensity of
+                     * the attenuated inflow is (F_in/P)(1 - exp(-tau))/tau */
+                    double q = s->src[c * G + g];
+                    double tau = kt * p->volume[c] / P;
+                    double f = tau > 0.0 ? -expm1(-tau) / tau : 1.0;
+                    s->out[c * G + g] = (exp(-tau) * acc[g] + q) / P;
+                    s->mean[c * G + g] = acc[g] / P * f;
+                } else {
+                    /* no outflow in this direction: everything that enters or is emitted stays */
+                    double v = (acc[g] + s->src[c * G + g]) / (kt * p->volume[c]);
+                    s->out[c * G + g] = v;
+                    s->mean[c * G + g] = v;
+                }
             }
         }
         /* release the downwind tasks */
@@ -263,6 +284,7 @@ static void* run_job(void* arg) {
         s.src = j->src ? j->src + (int64_t)d * j->src_stride : NULL;
         s.prev = j->prev ? j->prev + (int64_t)d * N * G : NULL;
         s.out = j->out ? j->out + (int64_t)d * N * G : NULL;
+        s.mean = (p->law == OR_LAW_EXP && !j->reverse && p->mean) ? p->mean + (int64_t)d * N * G : NULL;
         s.level = j->level ? j->level + (int64_t)d * N : lev;
         s.depth = j->depth ? j->depth + d : NULL;
         s.count = count;
@@ -376,9 +398,14 @@ static void periodic_source(const problem* p, const double* I, double* j) {
     }
 }
 
+/* the field J is taken from: the intensity itself (BALANCE) or the cell mean (EXP) */
+static const double* tally_field(const problem* p, const double* I) {
+    return p->law == OR_LAW_EXP ? p->mean : I;
+}
+
 static void tallies(const problem* p, const double* I, double* J, double* Gam, oracle_stats* st) {
     int64_t N = p->n_cells, G = p->n_groups;
-    mean_intensity(p, I, J);
+    mean_intensity(p, tally_field(p, I), J);
     double emitted = 0.0, absorbed = 0.0, escaped = 0.0, injected = 0.0, wsum = 0.0;
     for (int32_t d = 0; d < p->n_dir; ++d) wsum += p->weight[d];
     for (int64_t c = 0; c < N; ++c)
@@ -426,6 +453,11 @@ static double scat_residual(int64_t n, const double* Jnew, const double* Jold) {
 /*
  * Full solve (O3-O7). Outputs J, Gamma [N][G]; optionally every intensity I_out [D][N][G]
  * (final sweep). prev_init [D][N][G] seeds the periodic inflow (warm start) or NULL.
+ * law: OR_LAW_BALANCE (O3) or OR_LAW_EXP, the exponential reading of Sec. 2.6's "non-absorbed
+ * inflow plus source": with tau = kappa_t V / P_c, the outgoing intensity is
+ * (exp(-tau) F_in + q) / P_c and J is formed from the cell-mean intensity (F_in / P_c)(1 - exp(-tau))/tau,
+ * so that kappa_t V times it is the removed flux; Gamma, the scattering source and the
+ * conservation tally keep their form.
  * Returns OR_OK, OR_NOT_CONVERGED (outputs still written), or an error.
  */
 int oracle_solve(int64_t n_cells, int64_t n_faces, const double* volume, const int32_t* face_cells,
@@ -433,7 +465,8 @@ int oracle_solve(int64_t n_cells, int64_t n_faces, const double* volume, const i
                  const double* omega, const double* weight, int32_t n_groups, const double* kappa_abs,
                  const double* kappa_scat, const double* emissivity, const double* bc_inflow, double tol_scat,
                  int32_t max_it_scat, double tol_pbc, int32_t max_it_pbc, const double* prev_init,
-                 int fused, int n_threads, double* J, double* Gam, double* I_out, oracle_stats* st) {
+                 int fused, int law, int n_threads, double* J, double* Gam, double* I_out, oracle_stats* st) {
+    if (law != OR_LAW_BALANCE && law != OR_LAW_EXP) return OR_ERR_ARG;
     problem p;
     memset(&p, 0, sizeof p);
     p.n_cells = n_cells; p.n_faces = n_faces; p.volume = volume; p.face_cells = face_cells;
@@ -452,6 +485,11 @@ int oracle_solve(int64_t n_cells, int64_t n_faces, const double* volume, const i
             if (kappa_scat[i] != 0.0) { has_scat = 1; break; }
     for (int64_t f = 0; f < n_faces; ++f)
         if (flags[f] & OR_FACE_PERIODIC) { has_pbc = 1; break; }
+    p.law = law;
+    if (law == OR_LAW_EXP) {
+        p.mean = (double*)calloc((size_t)(D * NG > 0 ? D * NG : 1), sizeof(double));
+        if (!p.mean) { free_sides(&p); return OR_ERR_MEM; }
+    }
     double* I = (double*)calloc((size_t)(D * NG > 0 ? D * NG : 1), sizeof(double));
     double* Iprev = (double*)calloc((size_t)(D * NG > 0 ? D * NG : 1), sizeof(double));
     double* q = (double*)malloc(sizeof(double) * (size_t)(NG > 0 ? NG : 1));
@@ -478,7 +516,7 @@ int oracle_solve(int64_t n_cells, int64_t n_faces, const double* volume, const i
             if (rc != OR_OK) goto out;
             ++it_scat_total;
             ++it_pbc;
-            mean_intensity(&p, I, J);
+            mean_intensity(&p, tally_field(&p, I), J);
             res_scat = scat_residual(NG, J, Jold);
             memcpy(Jold, J, sizeof(double) * (size_t)NG);
             periodic_source(&p, I, jn1);
@@ -512,7 +550,7 @@ int oracle_solve(int64_t n_cells, int64_t n_faces, const double* volume, const i
             rc = run_dirs(&p, n_threads, 0, q, 0, has_pbc ? Iprev : NULL, I, NULL, NULL, 1);
             if (rc != OR_OK) goto out;
             ++it_scat;
-            mean_intensity(&p, I, J);
+            mean_intensity(&p, tally_field(&p, I), J);
             if (!has_scat) break;
             res_scat = scat_residual(NG, J, Jold);
             memcpy(Jold, J, sizeof(double) * (size_t)NG);
@@ -547,7 +585,7 @@ int oracle_solve(int64_t n_cells, int64_t n_faces, const double* volume, const i
     if (I_out) memcpy(I_out, I, sizeof(double) * (size_t)(D * NG));
     rc = (conv_pbc && conv_scat) ? OR_OK : OR_NOT_CONVERGED;
 out:
-    free(I); free(Iprev); free(q); free(Jold); free(jn); free(jn1);
+    free(I); free(Iprev); free(q); free(Jold); free(jn); free(jn1); free(p.mean);
     free_sides(&p);
     return rc;
 }
@@ -612,7 +650,7 @@ int oracle_adjoint(int64_t n_cells, int64_t n_faces, const double* volume, const
     /* forward: the converged state, every intensity of the final sweep */
     rc = oracle_solve(n_cells, n_faces, volume, face_cells, area, normal, flags, n_dir, omega, weight, n_groups,
                       kappa_abs, kappa_scat, emissivity, bc_inflow, tol_scat, max_it_scat, tol_pbc, max_it_pbc,
-                      NULL, 0, n_threads, J, Gam, I, &fst);
+                      NULL, 0, OR_LAW_BALANCE, n_threads, J, Gam, I, &fst);
     if (rc == OR_NOT_CONVERGED) conv_fwd = 0;
     else if (rc != OR_OK) goto out;
     rc = build_sides(&p);

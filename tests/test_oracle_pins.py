@@ -474,3 +474,66 @@ def test_adjoint_periodic_finite_differences(albedo):
             fd = (loss(a_p["ka"], a_p["em"], a_p["ks"])[0] - loss(a_m["ka"], a_m["em"], a_m["ks"])[0]) / (2 * h)
             assert gr[c, 0] == pytest.approx(fd, rel=1e-5, abs=1e-7 * np.abs(gr).max()), (name, c)
 
+
+# ---- (h) the EXP law: exact attenuation through each cell's mean chord ---------------------------
+def test_exp_column_is_the_exact_transport_solution():
+    # along a column of cubes the mean chord V/P is the cell length h, so the EXP update is exact:
+    # the outgoing intensity of cell k is exp(-kappa (k+1) h) and the cell mean is the chord average
+    # of exp(-kappa x) over the cell, (1/h) int_kh^(k+1)h exp(-kappa x) dx
+    n, h, kap = 96, 1.0 / 64, 2.5
+    p = configs.column(n, kappa=kap, h=h)
+    r = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, bc_inflow=p.boundary_inflow,
+                     want_intensity=True, law="exp")
+    assert r["rc"] == oracle.OK
+    k = np.arange(n)
+    assert rel(r["I"][0, :, 0], np.exp(-kap * h * (k + 1.0))) <= 1e-14
+    mean = (np.exp(-kap * h * k) - np.exp(-kap * h * (k + 1.0))) / (kap * h)
+    # one direction of weight 4pi: J is the cell mean itself
+    assert rel(r["J"][:, 0], mean) <= 1e-14
+    st = r["stats"]
+    assert abs(st["defect"]) <= 1e-14
+
+
+def test_exp_column_with_sources():
+    # the cell's own emission leaves unattenuated: I_k = r I_(k-1) + q / A with r = exp(-kappa h)
+    n, h, kap, s = 80, 1.0 / 32, 1.7, 0.3
+    p = configs.column(n, kappa=kap, h=h, source=s)
+    r = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, bc_inflow=p.boundary_inflow,
+                     want_intensity=True, law="exp")
+    A, rr = h * h, math.exp(-kap * h)
+    b = (s / (4 * math.pi)) / A
+    k = np.arange(n) + 1.0
+    assert rel(r["I"][0, :, 0], rr ** k + b * (1.0 - rr ** k) / (1.0 - rr)) <= 1e-13
+
+
+@pytest.mark.parametrize("box,albedo", [(False, 0.0), (False, 0.6), (True, 0.0), (True, 0.5)])
+def test_exp_dense_and_conservation(box, albedo):
+    p = configs.voronoi_small(150, periodic_box=box, n_dir=6, n_groups=2, seed=47, scatter_albedo=albedo,
+                              bc_inflow=not box)
+    ks = p.kappa_scat if albedo else None
+    r = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, kappa_scat=ks,
+                     bc_inflow=p.boundary_inflow, tol_scat=1e-15, max_it_scat=5000, tol_pbc=1e-15, max_it_pbc=5000,
+                     want_intensity=True, law="exp")
+    assert r["rc"] == 0
+    I, _, J, Gam = dense.solve_coupled_exp(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, ks,
+                                           p.boundary_inflow)
+    assert rel(r["I"], I) <= 1e-11
+    assert rel(r["J"], J) <= 1e-11 and rel(r["Gamma"], Gam) <= 1e-11
+    assert abs(r["stats"]["defect"]) <= 1e-12
+
+
+def test_exp_and_balance_agree_when_thin_away_from_sources():
+    # in an optically thin medium both laws stream the radiation unchanged, so the cells without a
+    # source see the same J; a source cell's J differs by its own emission, which BALANCE counts in
+    # the cell and EXP lets leave unattenuated
+    p = configs.voronoi_small(200, n_dir=6, n_groups=1, seed=49)
+    free = p.emissivity[:, 0] == 0.0
+    assert free.any() and not free.all()
+    a = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity)
+    b = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, law="exp")
+    assert rel(a["J"][free], b["J"][free]) > 1e-3
+    thin = p.kappa_abs * 1e-7
+    a = oracle.solve(p.mesh, p.omega, p.weight, thin, p.emissivity)
+    b = oracle.solve(p.mesh, p.omega, p.weight, thin, p.emissivity, law="exp")
+    assert rel(a["J"][free], b["J"][free]) <= 1e-5
+
