@@ -60,11 +60,18 @@ enum {
     SWEEP_SCHED_PLAIN = 3     /* plain FP64 path: one kernel launch per (direction, level), no batching */
 };
 
-enum { SWEEP_LAW_BALANCE = 0 }; /* transport scheme (a) of Sec. 2.6 as a cell balance */
+/* Absorption laws of the cell update (transport scheme (a) of Sec. 2.6, outflow = non-absorbed inflow
+ * plus source; F_in = the inflow flux, P = the projected outflow area, tau = kappa_t V / P):
+ *   BALANCE: (P + kappa_t V) I = q + F_in, and J is formed from I;
+ *   EXP:     P I = exp(-tau) F_in + q (the source leaves unattenuated), and J is formed from the
+ *            cell-mean intensity (F_in / P)(1 - exp(-tau)) / tau, so that kappa_t V times it is the
+ *            removed flux; with kappa_a = 0 the scattered fraction is 1 - exp(-kappa_s V / P), the
+ *            scattering law of Sec. 3.3. Forward solves only (the adjoint takes BALANCE). */
+enum { SWEEP_LAW_BALANCE = 0, SWEEP_LAW_EXP = 1 };
 
 typedef struct {
     int32_t precision;    /* 32: FP32 intensities, FP64 tallies and norms; 64: FP64 throughout */
-    int32_t law;          /* SWEEP_LAW_BALANCE */
+    int32_t law;          /* SWEEP_LAW_BALANCE (default) or SWEEP_LAW_EXP */
     int32_t schedule;     /* SWEEP_SCHED_*; SWEEP_SCHED_PLAIN implies precision 64 */
     int32_t max_it_scat;  /* source iteration (Alg. 1): maximum sweeps per periodic iteration */
     double tol_scat;      /* stop when max_c |J_new - J_old| / J_new <= tol_scat (0/0 counts as converged) */

@@ -23,6 +23,7 @@ SWEEP_FACE_BOUNDARY = 1
 SWEEP_FACE_PERIODIC = 2
 SWEEP_SCHED_AUTO, SWEEP_SCHED_LEVEL, SWEEP_SCHED_DATAFLOW, SWEEP_SCHED_PLAIN = 0, 1, 2, 3
 SCHEDULES = {"auto": 0, "level": 1, "dataflow": 2, "plain": 3}
+LAWS = {"balance": 0, "exp": 1}
 # forms of the batched sweep kernel (sweep_stats.kernel_used)
 KERNELS = {0: "none", 1: "k_plain", 2: "k_sweep", 3: "k_sweep_rec", 4: "k_sweep_op", 5: "k_sweep_op1", 6: "k_sweep_op2"}
 
@@ -116,6 +117,8 @@ def default_opts(**kw) -> sweep_opts:
     for k, v in kw.items():
         if k == "schedule" and isinstance(v, str):
             v = SCHEDULES[v]
+        if k == "law" and isinstance(v, str):
+            v = LAWS[v]
         if not hasattr(o, k):
             raise KeyError(k)
         setattr(o, k, v)

@@ -67,6 +67,9 @@ struct sweep_ctx {
     void* adjI = nullptr;
     void* adjL = nullptr;
     size_t adj_bytes_I = 0, adj_bytes_L = 0;
+    // EXP law: cell-mean intensities of the last sweep, [nd][N][G] in the solve precision
+    void* Imean = nullptr;
+    size_t imean_bytes = 0;
     // autotuner: schedule and block size per (precision, G)
     int tuned[2][9][2][4] = {};  // [precision][groups][operator mode] -> schedule, threads, lanes, blocks/SM
     int64_t launches = 0;  // kernels launched by this context
@@ -123,6 +126,8 @@ void free_solution(sweep_ctx* c) {
     c->sb = SolveBuf();
     dfree(c->adjI); dfree(c->adjL);
     c->adj_bytes_I = c->adj_bytes_L = 0;
+    dfree(c->Imean);
+    c->imean_bytes = 0;
 }
 
 void free_material(sweep_ctx* c) {
@@ -235,7 +240,10 @@ SweepArgs make_args(sweep_ctx* c, const Levels& L, int precision, const void* cm
     memset(&a, 0, sizeof a);
     a.task = L.task;
     a.trec = L.trec;
-    a.op = (precision == 32 && !reverse && L.op_valid && !(o && o->geometry_only)) ? L.op : nullptr;
+    // the EXP law runs in the generic and plain kernels; the adjoint takes BALANCE
+    a.law = (!reverse && o) ? o->law : SWEEP_LAW_BALANCE;
+    a.Imean = a.law ? c->Imean : nullptr;
+    a.op = (precision == 32 && !reverse && !a.law && L.op_valid && !(o && o->geometry_only)) ? L.op : nullptr;
     a.n_chunks = L.h_lev_chunk.empty() ? 0 : L.h_lev_chunk.back();
     a.lev_chunk = L.lev_chunk;
     a.n_levels = L.n_levels;
@@ -289,7 +297,8 @@ sweep_status run_sweep(sweep_ctx* c, const Levels& L, int precision, int schedul
             }
         }
     } else {
-        int per_sm = sweep_occupancy(precision, a.G, threads, L.nd, lanes, a.reverse, a.op != nullptr);
+        // the EXP law runs in the generic kernel, whose occupancy the reverse query gives
+        int per_sm = sweep_occupancy(precision, a.G, threads, L.nd, lanes, a.reverse || a.law, a.op != nullptr);
         if (per_sm < 1) return bad(c, "sweep kernel does not fit on an SM");
         if (bpsm > 0 && bpsm < per_sm) per_sm = bpsm;
         a.level_sync = schedule == SWEEP_SCHED_LEVEL ? 1 : 0;
@@ -399,7 +408,8 @@ sweep_status graph_loop(sweep_ctx* c, const sweep_opts& o, int prec, const void*
     if (s != SWEEP_OK) return s;
     cudaStream_t gs = c->gst;
     IterHost* hp = reinterpret_cast<IterHost*>(c->hpin);
-    int per_sm = sweep_occupancy(prec, G, threads, c->lev.nd, lanes, 0, prec == 32 && c->lev.op_valid && !o.geometry_only);
+    int per_sm = sweep_occupancy(prec, G, threads, c->lev.nd, lanes, o.law ? 1 : 0,
+                                 prec == 32 && !o.law && c->lev.op_valid && !o.geometry_only);
     if (per_sm < 1) return bad(c, "sweep kernel does not fit on an SM");
     if (bpsm > 0 && bpsm < per_sm) per_sm = bpsm;
     const int period = pbc ? 4 : 2;
@@ -433,7 +443,8 @@ sweep_status graph_loop(sweep_ctx* c, const sweep_opts& o, int prec, const void*
         if ((e = launch_sweep(a, prec, c->sms * per_sm, threads, gs, &kid))) return e;
         if ((e = cudaEventRecordWithFlags(ev[1], gs, cudaEventRecordExternal))) return e;
         if (scat) {
-            if ((e = launch_tally(prec, b.I[cur], N, G, D, 0, c->w64, c->wsum, c->mesh.vol, c->ka, c->em, c->J,
+            if ((e = launch_tally(prec, o.law ? c->Imean : b.I[cur], N, G, D, 0, c->w64, c->wsum, c->mesh.vol, c->ka,
+                                  c->em, c->J,
                                   c->Gam, c->partial, nblk, gs)))
                 return e;
             unsigned long long* ds = c->dmax + (fused ? 1 : 0);
@@ -867,6 +878,16 @@ sweep_status ensure_solution(sweep_ctx* c, int prec, bool two) {
     return SWEEP_OK;
 }
 
+sweep_status ensure_mean(sweep_ctx* c, int prec) {
+    const size_t bytes = (prec == 64 ? 8 : 4) * (size_t)c->mesh.N * c->D * c->G;
+    if (c->Imean && c->imean_bytes == bytes) return SWEEP_OK;
+    dfree(c->Imean);
+    c->imean_bytes = 0;
+    CK(cudaMalloc(&c->Imean, bytes > 0 ? bytes : 4), "alloc cell means");
+    c->imean_bytes = bytes;
+    return SWEEP_OK;
+}
+
 double read_max(sweep_ctx* c) {
     unsigned long long v = 0;
     cudaMemcpyAsync(&v, c->dmax, sizeof v, cudaMemcpyDeviceToHost, c->st);
@@ -961,7 +982,7 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     sweep_opts o;
     if (opts_in) o = *opts_in;
     else sweep_default_opts(&o);
-    if (o.law != SWEEP_LAW_BALANCE) return bad(c, "unsupported law");
+    if (o.law != SWEEP_LAW_BALANCE && o.law != SWEEP_LAW_EXP) return bad(c, "unsupported law");
     const bool plain = o.schedule == SWEEP_SCHED_PLAIN;
     const int prec = plain ? 64 : (o.precision == 64 ? 64 : 32);
     if (o.precision != 32 && o.precision != 64) return bad(c, "precision must be 32 or 64");
@@ -992,6 +1013,10 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     if (s != SWEEP_OK) return s;
     s = ensure_solution(c, prec, has_pbc);
     if (s != SWEEP_OK) return s;
+    if (o.law) {
+        s = ensure_mean(c, prec);
+        if (s != SWEEP_OK) return s;
+    }
     // partial sums: one pair per 256-thread block of the tallies, one pair per periodic or boundary cell
     const int nblk = nblocks256(NG);
     int64_t npart = nblk + 1;
@@ -1011,6 +1036,8 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     int sched = o.schedule, threads = o.block_threads ? o.block_threads : 256;
     int lanes = o.lanes_per_task ? o.lanes_per_task : 4;
     int bpsm = o.blocks_per_sm;
+    // the EXP law has one kernel form (the generic one): no tuning, the dataflow schedule
+    if (!plain && sched == SWEEP_SCHED_AUTO && o.law) sched = SWEEP_SCHED_DATAFLOW;
     if (!plain && sched == SWEEP_SCHED_AUTO) {
         CKL(launch_prep_material(N, G, c->mesh.vol, c->ka, c->ks, c->em, nullptr, prec == 32 ? c->cm32 : nullptr,
                                 prec == 64 ? c->cm64 : nullptr, c->st), "prep");
@@ -1107,8 +1134,8 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
             // without scattering nothing inside the iteration needs J: the final tally below computes it
             if (!c->has_scat) break;
             cudaEventRecord(u0, c->st);
-            CKL(launch_tally(prec, b.I[cur], N, G, D, 0, c->w64, c->wsum, c->mesh.vol, c->ka, c->em, c->J, c->Gam,
-                            c->partial, nblk, c->st), "tally");
+            CKL(launch_tally(prec, o.law ? c->Imean : b.I[cur], N, G, D, 0, c->w64, c->wsum, c->mesh.vol, c->ka,
+                            c->em, c->J, c->Gam, c->partial, nblk, c->st), "tally");
             CK(cudaMemsetAsync(c->dmax, 0, sizeof(unsigned long long), c->st), "init");
             CKL(launch_scat_residual(NG, c->J, c->Jold, c->dmax, c->st), "scattering residual");
             cudaEventRecord(u1, c->st);
@@ -1154,8 +1181,8 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     const int fin = has_pbc ? prev : cur;
     b.last = fin;
     // final tallies: absorbed/emitted from the last tally, escaped/injected over boundary cells
-    CKL(launch_tally(prec, b.I[fin], N, G, D, 0, c->w64, c->wsum, c->mesh.vol, c->ka, c->em, c->J, c->Gam, c->partial,
-                    nblk, c->st), "tally");
+    CKL(launch_tally(prec, o.law ? c->Imean : b.I[fin], N, G, D, 0, c->w64, c->wsum, c->mesh.vol, c->ka, c->em, c->J,
+                    c->Gam, c->partial, nblk, c->st), "tally");
     CKL(launch_reduce_sum(c->partial, nblocks256(NG), c->red, c->st), "reduce");
     if (c->mesh.n_bcells > 0) {
         CKL(launch_boundary_tally(prec, c->mesh, b.I[fin], G, D, 0, c->om64, c->w64, c->bc, c->partial, nblk, c->st),
@@ -1212,6 +1239,7 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
     cudaSetDevice(c->device);
     if (!c->has_mesh || !c->has_dirs || !c->has_mat) return bad(c, "set mesh, directions and material first");
     if (c->G > 4) return bad(c, "the adjoint supports at most 4 groups");
+    if (opts_in && opts_in->law != SWEEP_LAW_BALANCE) return bad(c, "the adjoint takes the BALANCE law");
     if (!gk_out || !ge_out) return bad(c, "null gradient output");
     sweep_opts o;
     if (opts_in) o = *opts_in;

@@ -300,6 +300,8 @@ struct SweepArgs {
     int reverse;          // 1 = adjoint (transposed) sweep
     int level_sync;       // 1 = grid barrier between levels
     int lanes;            // lanes cooperating on one task (4 or 8) in the batched kernel
+    int law;              // 0 = BALANCE, 1 = EXP (forward sweeps of the generic and plain kernels)
+    void* Imean;          // EXP: [nd][N][G] cell-mean intensity written by the sweep
     GridBar* bar;
     int* err;
     long long spin_budget;

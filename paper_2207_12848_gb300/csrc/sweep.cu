@@ -40,6 +40,29 @@ __device__ __forceinline__ double fmar(double a, double b, double c) { return __
 __device__ __forceinline__ float divr(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double divr(double a, double b) { return __ddiv_rn(a, b); }
 
+// EXP law of one cell and group: outgoing (exp(-tau) F_in + q) / P and cell mean (F_in / P)(1 - exp(-tau)) / tau,
+// tau = kappa_t V / P; with no outflow (P = 0) everything that enters or is emitted stays: (q + F_in) / kappa_t V
+__device__ __noinline__ void exp_law(float fin, float q, float ktv, float P, float& out, float& mean) {
+    if (P > 0.f) {
+        const float tau = ktv / P;
+        const float f = tau > 0.f ? -expm1f(-tau) / tau : 1.f;
+        out = fmaf(expf(-tau), fin, q) / P;
+        mean = fin / P * f;
+    } else {
+        out = mean = (q + fin) / ktv;
+    }
+}
+__device__ __noinline__ void exp_law(double fin, double q, double ktv, double P, double& out, double& mean) {
+    if (P > 0.0) {
+        const double tau = ktv / P;
+        const double f = tau > 0.0 ? -expm1(-tau) / tau : 1.0;
+        out = (exp(-tau) * fin + q) / P;
+        mean = fin / P * f;
+    } else {
+        out = mean = (q + fin) / ktv;
+    }
+}
+
 // Rare path, kept out of line so the common path stays short:
 // Wait (bounded) until *p carries this sweep's parity; returns the magnitude. false on give-up.
 template <typename real>
@@ -222,6 +245,13 @@ __device__ __forceinline__ bool group_task(const SweepArgs& a, uint32_t entry, u
 #pragma unroll
         for (int g = 0; g < GM; ++g) {
             if (g < G) {
+                if (a.law) {
+                    real val, mean;
+                    exp_law(acc[g], q[g].x, q[g].y, P, val, mean);
+                    reinterpret_cast<real*>(a.Imean)[(slab + c) * G + g] = mean;
+                    st_relaxed(dst + g, a.parity ? -val : val);
+                    continue;
+                }
                 const real src = a.reverse ? mulr(wsc, q[g].x) : q[g].x;
                 const real val = divr(addr(src, acc[g]), addr(P, q[g].y));
                 st_relaxed(dst + g, a.parity ? -val : val);
@@ -1001,8 +1031,8 @@ __device__ __forceinline__ void plain_task(const SweepArgs& a, uint32_t entry) {
     double* I = reinterpret_cast<double*>(a.I);
     const size_t slab = (size_t)dl * a.N;
     double acc[GM];
-    for (int g = 0; g < GM; ++g)
-        if (g < G) acc[g] = a.reverse ? __dmul_rn(a.w64[dl], cm[g].x) : cm[g].x;
+    for (int g = 0; g < GM; ++g)  // EXP keeps the inflow apart from the source
+        if (g < G) acc[g] = a.law ? 0.0 : (a.reverse ? __dmul_rn(a.w64[dl], cm[g].x) : cm[g].x);
     double P = 0.0;
     for (uint32_t s = r0; s < r1; ++s) {
         const int32_t nb = a.side[s].x;
@@ -1026,7 +1056,14 @@ __device__ __forceinline__ void plain_task(const SweepArgs& a, uint32_t entry) {
     double* dst = I + (slab + c) * G;
     for (int g = 0; g < GM; ++g) {
         if (g < G) {
-            const double v = __ddiv_rn(acc[g], __dadd_rn(P, cm[g].y));
+            double v;
+            if (a.law) {
+                double mean;
+                exp_law(acc[g], cm[g].x, cm[g].y, P, v, mean);
+                reinterpret_cast<double*>(a.Imean)[(slab + c) * G + g] = mean;
+            } else {
+                v = __ddiv_rn(acc[g], __dadd_rn(P, cm[g].y));
+            }
             dst[g] = a.parity ? -v : v;
         }
     }
@@ -1093,7 +1130,7 @@ cudaError_t launch_typed(const SweepArgs& a, int blocks, int threads, cudaStream
         if (a.lanes == 4) return launch_op_lanes<4>(a, cfg);
         return launch_op_lanes<8>(a, cfg);
     }
-    if (sizeof(real) == 4 && !a.reverse) {  // FP32 forward: the record kernel
+    if (sizeof(real) == 4 && !a.reverse && !a.law) {  // FP32 forward: the record kernel
         *kid = SWEEP_KERNEL_RECORDS;
         if (a.lanes == 1) return launch_rec_lanes<1>(a, cfg);
         if (a.lanes == 2) return launch_rec_lanes<2>(a, cfg);

@@ -137,6 +137,53 @@ def test_column_closed_form(ctx, precision, reverse):
     assert np.max(np.abs(I - exact) / exact) <= (1e-13 if precision == 64 else 2e-5)
 
 
+# ---- the EXP absorption law ------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", [64, 32])
+def test_exp_law_column(ctx, precision):
+    # the EXP update is the exact transport solution along a column of cubes: exp(-kappa x) at each
+    # cell's exit, and J the chord average of exp(-kappa x) over the cell
+    n, h, kap = 256, 1.0 / 256, 3.2
+    p = configs.column(n, kappa=kap, h=h)
+    load(ctx, p)
+    J, _, st, _ = ctx.solve(precision=precision, law="exp")
+    k = np.arange(n)
+    tol = 1e-13 if precision == 64 else 1e-5
+    assert rel_max(ctx.intensity(0)[:, 0], np.exp(-kap * h * (k + 1.0))) <= tol
+    assert rel_max(J[:, 0], (np.exp(-kap * h * k) - np.exp(-kap * h * (k + 1.0))) / (kap * h)) <= tol
+    assert st["kernel_used"] == 2  # the generic kernel
+
+
+@pytest.mark.parametrize("precision,schedule", [(64, "dataflow"), (64, "plain"), (32, "dataflow"), (32, "level")])
+@pytest.mark.parametrize("kind", ["vacuum", "scattering", "periodic"])
+def test_exp_law_matches_oracle(ctx, precision, schedule, kind):
+    p = configs.voronoi_small(4000, periodic_box=kind == "periodic", n_dir=12, n_groups=2, seed=63,
+                              scatter_albedo=0.5 if kind != "vacuum" else 0.0, n_src=8,
+                              bc_inflow=kind == "vacuum")
+    load(ctx, p)
+    it = dict(tol_scat=1e-10, max_it_scat=500, tol_pbc=1e-10, max_it_pbc=500)
+    J, Gm, st, s = ctx.solve(precision=precision, schedule=schedule, law="exp", **it)
+    r = run_oracle(p, law="exp", **it)
+    assert s == 0
+    if precision == 64:
+        assert rel_max(J, r["J"]) <= 1e-9 and rel_max(Gm, r["Gamma"]) <= 1e-9
+    else:
+        assert fp32_err(J, r["J"]) <= FP32_TOL
+    assert abs(st["defect"]) <= (1e-9 if precision == 64 else DEFECT_TOL)
+    assert st["kernel_used"] == (1 if schedule == "plain" else 2)  # plain or generic kernel
+    # the BALANCE answer on the same context is unchanged by an EXP solve in between
+    Jb, _, _, _ = ctx.solve(precision=precision, **it)
+    assert fp32_err(Jb, run_oracle(p, **it)["J"]) <= (1e-9 if precision == 64 else FP32_TOL)
+
+
+def test_exp_law_rejected_by_the_adjoint(ctx):
+    from paper_2207_12848_gb300 import SweepError
+    p = configs.voronoi_small(500, n_dir=4, seed=65)
+    load(ctx, p)
+    with pytest.raises(SweepError) as e:
+        ctx.adjoint(dl_dGamma=np.ones_like(p.kappa_abs), law="exp")
+    assert e.value.status == 1
+
+
 def test_column_deeper_than_the_level_tables(ctx):
     # 70000 levels of one cell: more than the direction-parallel levelisation's 65536-level tables, so the
     # level-synchronous form takes over; levels and the closed form must come out the same
