@@ -64,10 +64,11 @@ def _lib():
             lib = ctypes.CDLL(build())
             P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
             lib.oracle_levels.restype = ctypes.c_int
-            lib.oracle_levels.argtypes = [I64, I64, P, P, P, P, P, I32, P, P, P, ctypes.c_int]
+            lib.oracle_levels.argtypes = [I64, I64, P, P, P, P, P, I32, P, ctypes.c_int, P, P, ctypes.c_int]
             lib.oracle_solve.restype = ctypes.c_int
             lib.oracle_solve.argtypes = [I64, I64, P, P, P, P, P, I32, P, P, I32, P, P, P, P, D, I32, D, I32, P,
-                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, ctypes.POINTER(Stats)]
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P,
+                                         ctypes.POINTER(Stats)]
             lib.oracle_adjoint.restype = ctypes.c_int
             lib.oracle_adjoint.argtypes = [I64, I64, P, P, P, P, P, I32, P, P, I32, P, P, P, P, P, P, D, I32, D,
                                            I32, ctypes.c_int, P, P, P, P]
@@ -95,20 +96,21 @@ def _mesh_args(mesh):
     return keep, (mesh.n_cells, mesh.n_faces, _ptr(vol), _ptr(fc), _ptr(ar), _ptr(nr), _ptr(fl))
 
 
-def levels(mesh, omega, threads: int = 1):
-    """Wavefront level of every cell for every direction, and the depth per direction."""
+def levels(mesh, omega, threads: int = 1, dc_n: int = 0):
+    """Wavefront level of every cell for every direction, and the depth per direction (dc_n > 0: the
+    dependency graph of direction-conserving transport to dc_n neighbours)."""
     om = _c(omega, np.float64).reshape(-1, 3)
     keep, margs = _mesh_args(mesh)
     D = om.shape[0]
     lev = np.zeros((D, mesh.n_cells), np.int32)
     depth = np.zeros(D, np.int32)
-    rc = _lib().oracle_levels(*margs, D, _ptr(om), _ptr(lev), _ptr(depth), threads)
+    rc = _lib().oracle_levels(*margs, D, _ptr(om), dc_n, _ptr(lev), _ptr(depth), threads)
     return rc, lev, depth
 
 
 def solve(mesh, omega, weight, kappa_abs, emissivity, kappa_scat=None, bc_inflow=None, tol_scat=1e-6,
           max_it_scat=100, tol_pbc=1e-6, max_it_pbc=100, prev_init=None, threads: int = 1,
-          want_intensity: bool = False, fused: bool = False, law: str = "balance"):
+          want_intensity: bool = False, fused: bool = False, law: str = "balance", dc_n: int = 0):
     """Mean intensity J[N,G], absorbed rate Gamma[N,G], stats (and I[D,N,G] if asked)."""
     om = _c(omega, np.float64).reshape(-1, 3)
     w = _c(weight, np.float64)
@@ -127,7 +129,7 @@ def solve(mesh, omega, weight, kappa_abs, emissivity, kappa_scat=None, bc_inflow
     I = np.zeros((D, N, G)) if want_intensity else None
     st = Stats()
     rc = _lib().oracle_solve(*margs, D, _ptr(om), _ptr(w), G, _ptr(ka), _ptr(ks), _ptr(em), _ptr(bc), tol_scat,
-                             max_it_scat, tol_pbc, max_it_pbc, _ptr(pi), int(fused), LAWS[law], threads, _ptr(J),
+                             max_it_scat, tol_pbc, max_it_pbc, _ptr(pi), int(fused), LAWS[law], dc_n, threads, _ptr(J),
                              _ptr(Gam),
                              _ptr(I),
                              ctypes.byref(st))

@@ -192,3 +192,68 @@ def solve_coupled_exp(mesh, omega, weight, kappa_abs, emissivity, kappa_scat=Non
     J = np.einsum("d,dng->ng", weight, Ibar) / (4 * math.pi)
     Gam = kappa_abs * mesh.volume[:, None] * 4 * math.pi * J
     return I, Ibar, J, Gam
+
+
+# ---- direction-conserving transport, scheme (b): equal parts to the n faces most nearly along Omega ----
+def dc_operator(mesh, om, kappa_t, n, bc_inflow=None, group=0):
+    """Matrix L (N x N) and boundary right-hand side b (N) of scheme (b) for one direction: row c is
+    (P_c + kappa_t,c V_c) I_c - sum over the cells u that chose a face to c of (P_u / n_u) I_u. Also
+    returns the downwind dependencies {u: [cells u hands flux to]} over interior, non-periodic faces."""
+    N = mesh.n_cells
+    t = _dot(mesh.normal, om)
+    a = mesh.area * np.abs(t)
+    bidx = np.cumsum((mesh.flags & FACE_BOUNDARY) != 0) - 1
+    out = [[] for _ in range(N)]  # (n . Omega outward, face, downwind cell or -1)
+    L = np.zeros((N, N))
+    b = np.zeros(N)
+    P = np.zeros(N)
+    for f in range(mesh.n_faces):
+        c0, c1 = int(mesh.face_cells[f, 0]), int(mesh.face_cells[f, 1])
+        if t[f] == 0.0:
+            continue
+        if mesh.flags[f] & FACE_BOUNDARY:
+            if t[f] > 0:
+                out[c0].append((t[f], f, -1))
+                P[c0] += a[f]
+            elif bc_inflow is not None:
+                b[c0] += a[f] * bc_inflow[bidx[f], group]
+            continue
+        up, down, tu = (c0, c1, t[f]) if t[f] > 0 else (c1, c0, -t[f])
+        out[up].append((tu, f, down))
+        P[up] += a[f]
+    deps = {}
+    for u in range(N):
+        chosen = sorted(out[u], key=lambda x: (-x[0], x[1]))[:n]
+        if not chosen:
+            continue
+        share = P[u] / len(chosen)
+        for _, f, down in chosen:
+            if down >= 0:
+                L[down, u] -= share
+                if not (mesh.flags[f] & FACE_PERIODIC):
+                    deps.setdefault(u, []).append(down)
+    L[np.arange(N), np.arange(N)] += P + kappa_t[:, group] * mesh.volume
+    return L, b, deps
+
+
+def solve_coupled_dc(mesh, omega, weight, kappa_abs, emissivity, n, kappa_scat=None, bc_inflow=None):
+    """Scheme (b), BALANCE law, all directions with isotropic scattering; returns I[D,N,G], J, Gamma."""
+    D, N = omega.shape[0], mesh.n_cells
+    G = kappa_abs.shape[1]
+    ks = np.zeros_like(kappa_abs) if kappa_scat is None else kappa_scat
+    kt = kappa_abs + ks
+    I = np.zeros((D, N, G))
+    idx = np.arange(N)
+    for g in range(G):
+        A = np.zeros((D * N, D * N))
+        rhs = np.zeros(D * N)
+        for d in range(D):
+            L, bd, _ = dc_operator(mesh, omega[d], kt, n, bc_inflow, g)
+            A[d * N:(d + 1) * N, d * N:(d + 1) * N] = L
+            rhs[d * N:(d + 1) * N] = emissivity[:, g] / (4 * math.pi) + bd
+            for d2 in range(D):
+                A[d * N + idx, d2 * N + idx] -= ks[:, g] * mesh.volume * weight[d2] / (4 * math.pi)
+        I[:, :, g] = np.linalg.solve(A, rhs).reshape(D, N)
+    J = np.einsum("d,dng->ng", weight, I) / (4 * math.pi)
+    Gam = kappa_abs * mesh.volume[:, None] * 4 * math.pi * J
+    return I, J, Gam

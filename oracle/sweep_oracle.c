@@ -71,12 +71,14 @@ typedef struct {
     const double* emissivity; /* [N][G] */
     const double* bc_inflow;  /* [n_boundary_faces][G] or NULL */
     int law;                  /* OR_LAW_BALANCE or OR_LAW_EXP (forward sweeps only) */
+    int dc_n;                 /* 0: scheme (a); n > 0: direction-conserving transport to n neighbours */
     double* mean;             /* EXP: [D][N][G] cell-mean intensity of the last sweep (solver-owned) */
     /* derived: per-cell list of face sides */
     int64_t* side_start; /* [N+1] */
     int64_t* side_face;  /* face index */
     int8_t* side_sign;   /* +1 if the cell is c0 (outward normal = n), -1 if c1 */
     int64_t* bc_index;   /* [F] boundary face ordinal, -1 otherwise */
+    int64_t* face_side;  /* [F][2] side index of the face in c0's and in c1's list (-1 if none) */
 } problem;
 
 /* O1: the classification dot product, fixed order, no fused multiply-add */
@@ -103,11 +105,14 @@ static int build_sides(problem* p) {
     int64_t S = p->side_start[N];
     p->side_face = (int64_t*)malloc(sizeof(int64_t) * (size_t)(S > 0 ? S : 1));
     p->side_sign = (int8_t*)malloc((size_t)(S > 0 ? S : 1));
+    p->face_side = (int64_t*)malloc(sizeof(int64_t) * 2 * (size_t)(F > 0 ? F : 1));
     int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
-    if (!p->side_face || !p->side_sign || !fill) { free(fill); return OR_ERR_MEM; }
+    if (!p->side_face || !p->side_sign || !p->face_side || !fill) { free(fill); return OR_ERR_MEM; }
     for (int64_t c = 0; c < N; ++c) fill[c] = p->side_start[c];
     for (int64_t f = 0; f < F; ++f) {
         int32_t c0 = p->face_cells[2 * f], c1 = p->face_cells[2 * f + 1];
+        p->face_side[2 * f] = fill[c0];
+        p->face_side[2 * f + 1] = c1 >= 0 ? fill[c1] : -1;
         p->side_face[fill[c0]] = f;
         p->side_sign[fill[c0]++] = 1;
         if (c1 >= 0) {
@@ -124,11 +129,57 @@ static void free_sides(problem* p) {
     free(p->side_face);
     free(p->side_sign);
     free(p->bc_index);
+    free(p->face_side);
 }
 
 /* cell on the other side of a face side (interior or periodic partner) */
 static int32_t other_cell(const problem* p, int64_t f, int sign) {
     return sign > 0 ? p->face_cells[2 * f + 1] : p->face_cells[2 * f];
+}
+
+/*
+ * Direction-conserving transport (scheme (b) of Sec. 2.6): every cell hands its outflow in equal
+ * parts to the dc_n outflow sides whose outward normal is most nearly along Omega (largest
+ * n . Omega; on a tie the lower face index), or to all its outflow sides if it has fewer. For one
+ * direction (t[f] = n_f . Omega) this marks chosen[k] for every side k and gives share[c] =
+ * P_c / n_c, the flux per unit intensity through each chosen side (P_c the projected outflow
+ * area, as in scheme (a), n_c the number of chosen sides).
+ */
+static void dc_choose(const problem* p, const double* t, uint8_t* chosen, double* share) {
+    for (int64_t c = 0; c < p->n_cells; ++c) {
+        int64_t k0 = p->side_start[c], k1 = p->side_start[c + 1];
+        double P = 0.0;
+        int n = 0;
+        for (int64_t k = k0; k < k1; ++k) {
+            chosen[k] = 0;
+            int64_t f = p->side_face[k];
+            double tout = p->side_sign[k] > 0 ? t[f] : -t[f];
+            if (tout > 0.0) P += p->area[f] * tout;
+        }
+        for (int m = 0; m < p->dc_n; ++m) {
+            int64_t best = -1;
+            double bt = 0.0;
+            for (int64_t k = k0; k < k1; ++k) {
+                if (chosen[k]) continue;
+                int64_t f = p->side_face[k];
+                double tout = p->side_sign[k] > 0 ? t[f] : -t[f];
+                if (!(tout > 0.0)) continue;
+                if (best < 0 || tout > bt || (tout == bt && f < p->side_face[best])) { best = k; bt = tout; }
+            }
+            if (best < 0) break;
+            chosen[best] = 1;
+            ++n;
+        }
+        share[c] = n > 0 ? P / n : 0.0;
+    }
+}
+
+/* flux per unit upwind intensity through face f from its upwind cell u (side ku of u): |a_f| in
+ * scheme (a); share[u] if the side is one of u's chosen ones, else 0, in scheme (b) */
+static double face_weight(const problem* p, const uint8_t* chosen, const double* share, int64_t f, double tabs,
+                          int32_t u, int64_t ku) {
+    if (!chosen) return p->area[f] * tabs;
+    return chosen[ku] ? share[u] : 0.0;
 }
 
 /*
@@ -146,6 +197,8 @@ typedef struct {
     const double* prev; /* [N][G] previous-sweep intensity for periodic inflow, or NULL */
     double* out;       /* [N][G] solution */
     double* mean;      /* [N][G] EXP law: cell-mean intensity, or NULL */
+    const uint8_t* chosen; /* [S] scheme (b): the chosen outflow sides of this direction, or NULL */
+    const double* share;   /* [N] scheme (b): flux per unit intensity through each chosen side */
     int32_t* level;    /* [N] or NULL */
     int32_t* depth;
     /* scratch */
@@ -157,14 +210,17 @@ static int sweep_one(dir_sweep* s, int solve) {
     const problem* p = s->p;
     int64_t N = p->n_cells;
     int G = p->n_groups;
-    /* count upwind fluxes n(c, Omega) over interior, non-periodic faces */
+    /* count upwind fluxes n(c, Omega) over interior, non-periodic faces (scheme (b): the faces the
+     * upwind cell hands flux to) */
     for (int64_t c = 0; c < N; ++c) s->count[c] = 0;
     for (int64_t f = 0; f < p->n_faces; ++f) {
         if (p->flags[f] & (OR_FACE_BOUNDARY | OR_FACE_PERIODIC)) continue;
         double t = s->t[f];
         if (s->reverse) t = -t;
+        if (t == 0.0) continue;
+        if (s->chosen && !s->chosen[p->face_side[2 * f + (t > 0.0 ? 0 : 1)]]) continue;
         if (t > 0.0) s->count[p->face_cells[2 * f + 1]]++;
-        else if (t < 0.0) s->count[p->face_cells[2 * f]]++;
+        else s->count[p->face_cells[2 * f]]++;
     }
     int64_t head = 0, tail = 0;
     for (int64_t c = 0; c < N; ++c) {
@@ -199,11 +255,15 @@ static int sweep_one(dir_sweep* s, int solve) {
                      * transpose, the partner's lambda of the previous pass across the outflow side */
                     if (s->prev) {
                         int32_t up = other_cell(p, f, sign);
-                        for (int g = 0; g < G; ++g) acc[g] += a * s->prev[(int64_t)up * G + g];
+                        double w = face_weight(p, s->chosen, s->share, f, fabs(tout), up,
+                                               p->face_side[2 * f + (sign > 0 ? 1 : 0)]);
+                        for (int g = 0; g < G; ++g) acc[g] += w * s->prev[(int64_t)up * G + g];
                     }
                 } else {
                     int32_t up = other_cell(p, f, sign);
-                    for (int g = 0; g < G; ++g) acc[g] += a * s->out[(int64_t)up * G + g];
+                    double w = face_weight(p, s->chosen, s->share, f, fabs(tout), up,
+                                           p->face_side[2 * f + (sign > 0 ? 1 : 0)]);
+                    for (int g = 0; g < G; ++g) acc[g] += w * s->out[(int64_t)up * G + g];
                 }
             }
             for (int g = 0; g < G; ++g) {
@@ -231,6 +291,7 @@ static int sweep_one(dir_sweep* s, int solve) {
         for (int64_t k = p->side_start[c]; k < p->side_start[c + 1]; ++k) {
             int64_t f = p->side_face[k];
             if (p->flags[f] & (OR_FACE_BOUNDARY | OR_FACE_PERIODIC)) continue;
+            if (s->chosen && !s->chosen[k]) continue;
             int sign = p->side_sign[k];
             double tout = sign > 0 ? s->t[f] : -s->t[f];
             if (s->reverse) tout = -tout;
@@ -273,10 +334,14 @@ static void* run_job(void* arg) {
     int32_t* count = (int32_t*)malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
     int64_t* queue = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
     int32_t* lev = (int32_t*)malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+    int64_t S = p->side_start[N];
+    uint8_t* chosen = p->dc_n > 0 ? (uint8_t*)malloc((size_t)(S > 0 ? S : 1)) : NULL;
+    double* share = p->dc_n > 0 ? (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1)) : NULL;
     j->status = OR_OK;
-    if (!t || !count || !queue || !lev) { j->status = OR_ERR_MEM; goto done; }
+    if (!t || !count || !queue || !lev || (p->dc_n > 0 && (!chosen || !share))) { j->status = OR_ERR_MEM; goto done; }
     for (int32_t d = j->d0; d < j->d1; ++d) {
         classify(p, d, t);
+        if (chosen) dc_choose(p, t, chosen, share);
         dir_sweep s;
         s.p = p;
         s.t = t;
@@ -285,6 +350,8 @@ static void* run_job(void* arg) {
         s.prev = j->prev ? j->prev + (int64_t)d * N * G : NULL;
         s.out = j->out ? j->out + (int64_t)d * N * G : NULL;
         s.mean = (p->law == OR_LAW_EXP && !j->reverse && p->mean) ? p->mean + (int64_t)d * N * G : NULL;
+        s.chosen = chosen;
+        s.share = share;
         s.level = j->level ? j->level + (int64_t)d * N : lev;
         s.depth = j->depth ? j->depth + d : NULL;
         s.count = count;
@@ -297,6 +364,8 @@ done:
     free(count);
     free(queue);
     free(lev);
+    free(chosen);
+    free(share);
     return NULL;
 }
 
@@ -348,14 +417,18 @@ static int check_problem(const problem* p) {
 /* --------------------------------------------------------------------------------------------- */
 /* public entry points (loaded with ctypes by the tests) */
 
-/* O1+O2: levels[d][c] and depth[d] for every direction; OR_ERR_CYCLE if a graph is cyclic. */
+/* O1+O2: levels[d][c] and depth[d] for every direction; OR_ERR_CYCLE if a graph is cyclic.
+ * dc_n = 0: the dependency graph of scheme (a) (every interior outflow face); dc_n > 0: that of
+ * direction-conserving transport, only the faces each cell hands flux to (dc_choose). */
 int oracle_levels(int64_t n_cells, int64_t n_faces, const double* volume, const int32_t* face_cells,
                   const double* area, const double* normal, const uint8_t* flags, int32_t n_dir,
-                  const double* omega, int32_t* level, int32_t* depth, int n_threads) {
+                  const double* omega, int dc_n, int32_t* level, int32_t* depth, int n_threads) {
+    if (dc_n < 0) return OR_ERR_ARG;
     problem p;
     memset(&p, 0, sizeof p);
     p.n_cells = n_cells; p.n_faces = n_faces; p.volume = volume; p.face_cells = face_cells;
     p.area = area; p.normal = normal; p.flags = flags; p.n_dir = n_dir; p.omega = omega; p.n_groups = 1;
+    p.dc_n = dc_n;
     int rc = check_problem(&p);
     if (rc != OR_OK) return rc;
     rc = build_sides(&p);
@@ -380,18 +453,49 @@ static void mean_intensity(const problem* p, const double* I, double* J) {
 }
 
 /* j_c: sum_d w_d sum over periodic inflow faces of c of |a_f| I_prev[partner] */
-static void periodic_source(const problem* p, const double* I, double* j) {
+/* per-direction scratch of scheme (b) for the tallies: the chosen sides and shares of direction d
+ * (t: [F] scratch for n . Omega); a no-op in scheme (a) */
+typedef struct {
+    double* t;
+    uint8_t* chosen;
+    double* share;
+} dc_scratch;
+
+static int dc_scratch_init(const problem* p, dc_scratch* x) {
+    memset(x, 0, sizeof *x);
+    if (p->dc_n <= 0) return OR_OK;
+    int64_t S = p->side_start[p->n_cells];
+    x->t = (double*)malloc(sizeof(double) * (size_t)(p->n_faces > 0 ? p->n_faces : 1));
+    x->chosen = (uint8_t*)malloc((size_t)(S > 0 ? S : 1));
+    x->share = (double*)malloc(sizeof(double) * (size_t)(p->n_cells > 0 ? p->n_cells : 1));
+    return (x->t && x->chosen && x->share) ? OR_OK : OR_ERR_MEM;
+}
+
+static void dc_scratch_dir(const problem* p, dc_scratch* x, int32_t d) {
+    if (!x->chosen) return;
+    classify(p, d, x->t);
+    dc_choose(p, x->t, x->chosen, x->share);
+}
+
+static void dc_scratch_free(dc_scratch* x) {
+    free(x->t);
+    free(x->chosen);
+    free(x->share);
+}
+
+static void periodic_source(const problem* p, const double* I, double* j, dc_scratch* x) {
     int64_t N = p->n_cells, G = p->n_groups;
     for (int64_t i = 0; i < N * G; ++i) j[i] = 0.0;
     for (int32_t d = 0; d < p->n_dir; ++d) {
         const double* om = p->omega + 3 * d;
+        dc_scratch_dir(p, x, d);
         for (int64_t f = 0; f < p->n_faces; ++f) {
             if (!(p->flags[f] & OR_FACE_PERIODIC)) continue;
             double t = face_dot(p->normal + 3 * f, om);
             if (t == 0.0) continue;
             int32_t c0 = p->face_cells[2 * f], c1 = p->face_cells[2 * f + 1];
             int32_t down = t > 0.0 ? c1 : c0, up = t > 0.0 ? c0 : c1;
-            double a = p->area[f] * fabs(t);
+            double a = face_weight(p, x->chosen, x->share, f, fabs(t), up, p->face_side[2 * f + (t > 0.0 ? 0 : 1)]);
             for (int g = 0; g < G; ++g)
                 j[(int64_t)down * G + g] += p->weight[d] * a * I[(int64_t)d * N * G + (int64_t)up * G + g];
         }
@@ -403,7 +507,7 @@ static const double* tally_field(const problem* p, const double* I) {
     return p->law == OR_LAW_EXP ? p->mean : I;
 }
 
-static void tallies(const problem* p, const double* I, double* J, double* Gam, oracle_stats* st) {
+static void tallies(const problem* p, const double* I, double* J, double* Gam, oracle_stats* st, dc_scratch* x) {
     int64_t N = p->n_cells, G = p->n_groups;
     mean_intensity(p, tally_field(p, I), J);
     double emitted = 0.0, absorbed = 0.0, escaped = 0.0, injected = 0.0, wsum = 0.0;
@@ -417,13 +521,16 @@ static void tallies(const problem* p, const double* I, double* J, double* Gam, o
         }
     for (int32_t d = 0; d < p->n_dir; ++d) {
         const double* om = p->omega + 3 * d;
+        dc_scratch_dir(p, x, d);
         for (int64_t f = 0; f < p->n_faces; ++f) {
             if (!(p->flags[f] & OR_FACE_BOUNDARY)) continue;
             double t = face_dot(p->normal + 3 * f, om);
             double a = p->area[f] * fabs(t);
             int32_t c = p->face_cells[2 * f];
+            /* scheme (b): a cell's outflow leaves through a vacuum face only if it is a chosen side */
+            double aout = t > 0.0 ? face_weight(p, x->chosen, x->share, f, fabs(t), c, p->face_side[2 * f]) : 0.0;
             for (int g = 0; g < G; ++g) {
-                if (t > 0.0) escaped += p->weight[d] * a * I[(int64_t)d * N * G + (int64_t)c * G + g];
+                if (t > 0.0) escaped += p->weight[d] * aout * I[(int64_t)d * N * G + (int64_t)c * G + g];
                 else if (t < 0.0 && p->bc_inflow) injected += p->weight[d] * a * p->bc_inflow[p->bc_index[f] * G + g];
             }
         }
@@ -453,6 +560,9 @@ static double scat_residual(int64_t n, const double* Jnew, const double* Jold) {
 /*
  * Full solve (O3-O7). Outputs J, Gamma [N][G]; optionally every intensity I_out [D][N][G]
  * (final sweep). prev_init [D][N][G] seeds the periodic inflow (warm start) or NULL.
+ * dc_n: 0 for transport scheme (a) of Sec. 2.6 (outflow split over the outflow faces by A n.Omega),
+ * n > 0 for direction-conserving transport, scheme (b) (dc_choose: equal parts to the n faces most
+ * nearly along Omega; the paper's n is the number of dimensions, 3).
  * law: OR_LAW_BALANCE (O3) or OR_LAW_EXP, the exponential reading of Sec. 2.6's "non-absorbed
  * inflow plus source": with tau = kappa_t V / P_c, the outgoing intensity is
  * (exp(-tau) F_in + q) / P_c and J is formed from the cell-mean intensity (F_in / P_c)(1 - exp(-tau))/tau,
@@ -465,8 +575,10 @@ int oracle_solve(int64_t n_cells, int64_t n_faces, const double* volume, const i
                  const double* omega, const double* weight, int32_t n_groups, const double* kappa_abs,
                  const double* kappa_scat, const double* emissivity, const double* bc_inflow, double tol_scat,
                  int32_t max_it_scat, double tol_pbc, int32_t max_it_pbc, const double* prev_init,
-                 int fused, int law, int n_threads, double* J, double* Gam, double* I_out, oracle_stats* st) {
+                 int fused, int law, int dc_n, int n_threads, double* J, double* Gam, double* I_out,
+                 oracle_stats* st) {
     if (law != OR_LAW_BALANCE && law != OR_LAW_EXP) return OR_ERR_ARG;
+    if (dc_n < 0) return OR_ERR_ARG;
     problem p;
     memset(&p, 0, sizeof p);
     p.n_cells = n_cells; p.n_faces = n_faces; p.volume = volume; p.face_cells = face_cells;
@@ -486,9 +598,12 @@ int oracle_solve(int64_t n_cells, int64_t n_faces, const double* volume, const i
     for (int64_t f = 0; f < n_faces; ++f)
         if (flags[f] & OR_FACE_PERIODIC) { has_pbc = 1; break; }
     p.law = law;
+    p.dc_n = dc_n;
+    dc_scratch x;
+    if (dc_scratch_init(&p, &x) != OR_OK) { dc_scratch_free(&x); free_sides(&p); return OR_ERR_MEM; }
     if (law == OR_LAW_EXP) {
         p.mean = (double*)calloc((size_t)(D * NG > 0 ? D * NG : 1), sizeof(double));
-        if (!p.mean) { free_sides(&p); return OR_ERR_MEM; }
+        if (!p.mean) { dc_scratch_free(&x); free_sides(&p); return OR_ERR_MEM; }
     }
     double* I = (double*)calloc((size_t)(D * NG > 0 ? D * NG : 1), sizeof(double));
     double* Iprev = (double*)calloc((size_t)(D * NG > 0 ? D * NG : 1), sizeof(double));
@@ -498,7 +613,7 @@ int oracle_solve(int64_t n_cells, int64_t n_faces, const double* volume, const i
     double* jn1 = (double*)calloc((size_t)(NG > 0 ? NG : 1), sizeof(double));
     if (!I || !Iprev || !q || !Jold || !jn || !jn1) { rc = OR_ERR_MEM; goto out; }
     if (has_pbc && prev_init) memcpy(Iprev, prev_init, sizeof(double) * (size_t)(D * NG));
-    if (has_pbc) periodic_source(&p, Iprev, jn);
+    if (has_pbc) periodic_source(&p, Iprev, jn, &x);
     int conv_pbc = !has_pbc, conv_scat = !has_scat;
     int it_pbc = 0, it_scat_total = 0;
     double res_pbc = 0.0, res_pbc_mean = 0.0, res_scat = 0.0;
@@ -519,7 +634,7 @@ int oracle_solve(int64_t n_cells, int64_t n_faces, const double* volume, const i
             mean_intensity(&p, tally_field(&p, I), J);
             res_scat = scat_residual(NG, J, Jold);
             memcpy(Jold, J, sizeof(double) * (size_t)NG);
-            periodic_source(&p, I, jn1);
+            periodic_source(&p, I, jn1, &x);
             double emax = 0.0, esum = 0.0;
             for (int64_t i = 0; i < NG; ++i) {
                 double s = jn1[i] + jn[i];
@@ -561,7 +676,7 @@ int oracle_solve(int64_t n_cells, int64_t n_faces, const double* volume, const i
         ++it_pbc;
         if (!has_pbc) break;
         /* O6: sources for the next sweep and their relative change */
-        periodic_source(&p, I, jn1);
+        periodic_source(&p, I, jn1, &x);
         double emax = 0.0, esum = 0.0;
         for (int64_t i = 0; i < NG; ++i) {
             double s = jn1[i] + jn[i];
@@ -576,7 +691,7 @@ int oracle_solve(int64_t n_cells, int64_t n_faces, const double* volume, const i
         if (res_pbc < tol_pbc) { conv_pbc = 1; break; }
         if (it_pbc >= max_it_pbc) { conv_pbc = 0; break; }
     }
-    tallies(&p, I, J, Gam, st);
+    tallies(&p, I, J, Gam, st, &x);
     st->it_scat = it_scat_total;
     st->it_pbc = it_pbc;
     st->res_scat = res_scat;
@@ -586,6 +701,7 @@ int oracle_solve(int64_t n_cells, int64_t n_faces, const double* volume, const i
     rc = (conv_pbc && conv_scat) ? OR_OK : OR_NOT_CONVERGED;
 out:
     free(I); free(Iprev); free(q); free(Jold); free(jn); free(jn1); free(p.mean);
+    dc_scratch_free(&x);
     free_sides(&p);
     return rc;
 }
@@ -650,7 +766,7 @@ int oracle_adjoint(int64_t n_cells, int64_t n_faces, const double* volume, const
     /* forward: the converged state, every intensity of the final sweep */
     rc = oracle_solve(n_cells, n_faces, volume, face_cells, area, normal, flags, n_dir, omega, weight, n_groups,
                       kappa_abs, kappa_scat, emissivity, bc_inflow, tol_scat, max_it_scat, tol_pbc, max_it_pbc,
-                      NULL, 0, OR_LAW_BALANCE, n_threads, J, Gam, I, &fst);
+                      NULL, 0, OR_LAW_BALANCE, 0, n_threads, J, Gam, I, &fst);
     if (rc == OR_NOT_CONVERGED) conv_fwd = 0;
     else if (rc != OR_OK) goto out;
     rc = build_sides(&p);

@@ -537,3 +537,93 @@ def test_exp_and_balance_agree_when_thin_away_from_sources():
     b = oracle.solve(p.mesh, p.omega, p.weight, thin, p.emissivity, law="exp")
     assert rel(a["J"][free], b["J"][free]) <= 1e-5
 
+
+# ---- (i) direction-conserving transport, scheme (b) of Sec. 2.6 ---------------------------------
+def test_dc_equals_scheme_a_on_the_lattice_diagonal():
+    # along a body diagonal every cube has three outflow faces with the same area and n . Omega:
+    # both schemes split the outflow in equal thirds, and choose the same faces
+    m = lattice_mesh(7)
+    om = np.array([[s1, s2, s3] for s1 in (1, -1) for s2 in (1, -1) for s3 in (1, -1)], float) / math.sqrt(3.0)
+    assert np.all(om[:, 0] ** 2 == om[:, 1] ** 2) and np.all(om[:, 1] ** 2 == om[:, 2] ** 2)
+    w = np.full(len(om), 4 * math.pi / len(om))
+    rng = np.random.default_rng(10)
+    ka = rng.random((m.n_cells, 1)) * 5
+    em = rng.random((m.n_cells, 1))
+    a = oracle.solve(m, om, w, ka, em, want_intensity=True)
+    b = oracle.solve(m, om, w, ka, em, want_intensity=True, dc_n=3)
+    assert rel(a["I"], b["I"]) <= 1e-14
+    assert np.array_equal(oracle.levels(m, om)[1], oracle.levels(m, om, dc_n=3)[1])
+
+
+@pytest.mark.parametrize("n_dc", [1, 3])
+@pytest.mark.parametrize("box,albedo", [(False, 0.0), (False, 0.5), (True, 0.0), (True, 0.5)])
+def test_dc_dense_and_conservation(n_dc, box, albedo):
+    p = configs.voronoi_small(150, periodic_box=box, n_dir=6, n_groups=2, seed=51, scatter_albedo=albedo,
+                              bc_inflow=not box)
+    ks = p.kappa_scat if albedo else None
+    r = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, kappa_scat=ks,
+                     bc_inflow=p.boundary_inflow, tol_scat=1e-15, max_it_scat=5000, tol_pbc=1e-15, max_it_pbc=5000,
+                     want_intensity=True, dc_n=n_dc)
+    assert r["rc"] == 0
+    I, J, Gam = dense.solve_coupled_dc(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, n_dc, ks,
+                                       p.boundary_inflow)
+    assert rel(r["I"], I) <= 1e-11
+    assert rel(r["J"], J) <= 1e-11 and rel(r["Gamma"], Gam) <= 1e-11
+    assert abs(r["stats"]["defect"]) <= 1e-12
+
+
+def test_dc_thins_the_dependency_graph():
+    # Sec. 2.6: direction-conserving transport to 3 neighbours cuts the downwind dependencies per cell
+    # from about 15.54 / 2 to 3; its wavefront levels are the longest paths of the thinner graph, so
+    # no cell sits deeper than under scheme (a)
+    p = configs.voronoi_small(400, n_dir=4, n_groups=1, seed=53)
+    m = p.mesh
+    na = nd = 0
+    rc_a, lev_a, _ = oracle.levels(m, p.omega)
+    rc_b, lev_b, _ = oracle.levels(m, p.omega, dc_n=3)
+    assert rc_a == rc_b == 0
+    for d in range(p.n_dir):
+        _, _, deps = dense.dc_operator(m, p.omega[d], p.kappa_abs, 3)
+        _, _, deps_a = dense.dc_operator(m, p.omega[d], p.kappa_abs, 10 ** 6)
+        nd += sum(len(v) for v in deps.values())
+        na += sum(len(v) for v in deps_a.values())
+        # brute-force longest paths of the scheme (b) graph
+        lev = np.zeros(m.n_cells, np.int64)
+        for _ in range(m.n_cells):
+            changed = False
+            for u, vs in deps.items():
+                for v in vs:
+                    if lev[v] < lev[u] + 1:
+                        lev[v] = lev[u] + 1
+                        changed = True
+            if not changed:
+                break
+        assert np.array_equal(lev_b[d], lev)
+        assert np.all(lev_b[d] <= lev_a[d])
+    assert nd / (p.n_dir * m.n_cells) <= 3.0 < na / (p.n_dir * m.n_cells)
+
+
+def test_dc_downwind_counts_match_the_paper():
+    # in a periodic Voronoi box (no boundary) each cell has 15.54 neighbours on average, half of them
+    # downwind under scheme (a); scheme (b) hands flux to exactly 3 of them (Sec. 2.6,
+    # tests/golden/paper_values.json)
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")) as f:
+        gold = json.load(f)
+    p = configs.voronoi_small(2000, periodic_box=True, n_dir=4, n_groups=1, seed=53)
+    m = p.mesh
+    assert (m.face_cells[:, 1] >= 0).all()
+    down_a = down_b = 0
+    for d in range(p.n_dir):
+        L, _, _ = dense.dc_operator(m, p.omega[d], p.kappa_abs, 3)
+        La, _, _ = dense.dc_operator(m, p.omega[d], p.kappa_abs, 10 ** 6)
+        off = ~np.eye(m.n_cells, dtype=bool)
+        down_b += int(((L != 0) & off).sum())  # one entry per (chosen face) downwind pair
+        down_a += int(((La != 0) & off).sum())
+    per_b = down_b / (p.n_dir * m.n_cells)
+    per_a = down_a / (p.n_dir * m.n_cells)
+    g = gold["scheme_a_downwind_per_cell"]
+    assert abs(per_a - g["value"]) <= g["abs_tol"]
+    assert abs(per_b - gold["dc_downwind_per_cell"]["value"]) <= 0.01
+
