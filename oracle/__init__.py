@@ -10,10 +10,15 @@ periodic iteration; ``dense.py`` is an independent second oracle that assembles
 and solves the same linear systems directly on small meshes.
 
 Parity status per function (what pins it; see tests/test_oracle_pins.py):
-  oracle_levels  -- pinned: brute-force longest paths, the Voronoi ordering invariant (Appendix A)
+  oracle_levels  -- pinned: brute-force longest paths, the Voronoi ordering invariant (Appendix A);
+                    with dc_n > 0 brute-force longest paths of the thinner scheme (b) graph and the
+                    paper's dependency counts
   oracle_solve   -- pinned: 1-D column closed form, photon conservation, dense LU solves
                     (plain, scattering, periodic, both at once for the nested and the fused
-                    loops), uniform periodic fixed point, linearity, pure streaming
+                    loops), uniform periodic fixed point, linearity, pure streaming; law="exp":
+                    the exact transport solution along a column and dense solves of the EXP
+                    system; dc_n > 0: scheme (a) where the faces tie and dense solves of the
+                    scheme (b) system
   oracle_adjoint -- pinned: central finite differences of oracle_solve (also in kappa_scat, through
                     the source iteration, and through the periodic iteration), dense transposed
                     solve (also of the coupled system, with scattering and periodic faces),
