@@ -234,6 +234,19 @@ sweep_status ensure_partial(sweep_ctx* c, int nblk) {
 
 int nblocks256(int64_t n) { return (int)((n + 255) / 256 > 0 ? (n + 255) / 256 : 1); }
 
+// A timing event that is destroyed when it goes out of scope, also on the error returns. Destroying an
+// event that the device has not reached yet is allowed: its resources are freed once it completes.
+struct ScopedEvent {
+    cudaEvent_t e = nullptr;
+    ScopedEvent() { cudaEventCreate(&e); }
+    ~ScopedEvent() {
+        if (e) cudaEventDestroy(e);
+    }
+    ScopedEvent(const ScopedEvent&) = delete;
+    ScopedEvent& operator=(const ScopedEvent&) = delete;
+    operator cudaEvent_t() const { return e; }
+};
+
 SweepArgs make_args(sweep_ctx* c, const Levels& L, int precision, const void* cm, void* I, const void* Iprev,
                     int G, int parity, int reverse, int level_sync, const sweep_opts* o) {
     SweepArgs a;
@@ -280,9 +293,7 @@ sweep_status run_sweep(sweep_ctx* c, const Levels& L, int precision, int schedul
                        SweepArgs a, const float* bc32, float* ms) {
     if (precision == 32) a.bc = a.reverse ? nullptr : bc32;
     a.lanes = lanes;
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    ScopedEvent e0, e1;
     CK(cudaMemsetAsync(c->bar, 0, sizeof(GridBar), c->st), "reset barrier");
     CK(cudaMemsetAsync(c->derr, 0, sizeof(int), c->st), "reset error word");
     cudaEventRecord(e0, c->st);
@@ -310,8 +321,6 @@ sweep_status run_sweep(sweep_ctx* c, const Levels& L, int precision, int schedul
     CK(cudaStreamSynchronize(c->st), "sweep");
     float t = 0;
     cudaEventElapsedTime(&t, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if (ms) *ms += t;
     if (herr != DEV_OK) {
         c->err = "sweep: a bounded device wait gave up";
@@ -831,9 +840,7 @@ sweep_status assemble_operator(sweep_ctx* c, Levels& L, float* t_ms) {
         }
         L.op_bytes = bytes;
     }
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    ScopedEvent e0, e1;
     cudaEventRecord(e0, c->st);
     CKL(build_operator(c->mesh, L, c->om64, c->om32, c->om32lo, c->st), "assemble operator");
     cudaEventRecord(e1, c->st);
@@ -841,8 +848,6 @@ sweep_status assemble_operator(sweep_ctx* c, Levels& L, float* t_ms) {
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
     if (t_ms) *t_ms = ms;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     L.op_valid = true;
     return SWEEP_OK;
 }
@@ -993,9 +998,7 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     sweep_stats S;
     memset(&S, 0, sizeof S);
     const int64_t launches0 = c->launches;
-    cudaEvent_t t0, t1;
-    cudaEventCreate(&t0);
-    cudaEventCreate(&t1);
+    ScopedEvent t0, t1;
     cudaEventRecord(t0, c->st);
     float tc = 0, tl = 0, top = 0;
     sweep_status s = ensure_levels(c, &o, &tc, &tl, &top);
@@ -1079,9 +1082,7 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     double res_pbc = 0.0, res_pbc_mean = 0.0, res_scat = 0.0;
     float t_sweep = 0.f;
     int cur = has_pbc ? (prev == 0 ? 1 : 0) : 0;
-    cudaEvent_t u0, u1;
-    cudaEventCreate(&u0);
-    cudaEventCreate(&u1);
+    ScopedEvent u0, u1;
     float t_other = 0.f;
     bool graphed = false;
     // Sec. 2.7's fused loops: one source-iteration sweep per periodic iteration, J carried over
@@ -1200,7 +1201,6 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     CK(cudaStreamSynchronize(c->st), "solve");
     float ttot = 0;
     cudaEventElapsedTime(&ttot, t0, t1);
-    cudaEventDestroy(t0); cudaEventDestroy(t1); cudaEventDestroy(u0); cudaEventDestroy(u1);
     S.absorbed = hr[0];
     S.emitted = hr[1];
     S.escaped = hr[2];
@@ -1262,9 +1262,7 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
     sweep_stats S;
     memset(&S, 0, sizeof S);
     const int64_t launches0 = c->launches;
-    cudaEvent_t t0, t1;
-    cudaEventCreate(&t0);
-    cudaEventCreate(&t1);
+    ScopedEvent t0, t1;
     cudaEventRecord(t0, c->st);
     // device copies of the loss gradients and FP64 gradient accumulators
     DevBuf<double> b_dlj, b_dlg, b_gk, b_ge;
@@ -1411,8 +1409,6 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
     CK(cudaStreamSynchronize(c->st), "adjoint");
     float ttot = 0;
     cudaEventElapsedTime(&ttot, t0, t1);
-    cudaEventDestroy(t0);
-    cudaEventDestroy(t1);
     S.n_sweeps = n_sweeps;
     S.it_scat = it_fwd;
     S.it_pbc = it_adj;
