@@ -125,10 +125,16 @@ def adjoint_direction(mesh, om, kappa_abs, g_src):
 
 
 # ---- the EXP law: outgoing (exp(-tau) F_in + q) / P, cell mean (F_in / P)(1 - exp(-tau)) / tau ----
-def inflow_operator(mesh, om, bc_inflow=None, group=0):
+def inflow_operator(mesh, om, bc_inflow=None, group=0, dc_n=0):
     """For one direction: M (N x N) and b (N) with the inflow flux F_in = M I + b of every cell, and
-    the projected outflow area P (N). Periodic faces couple to the partner cell."""
+    the projected outflow area P (N). Periodic faces couple to the partner cell. dc_n > 0: the flux
+    of scheme (b) (dc_operator) instead of A |n . Omega| per face."""
     N = mesh.n_cells
+    if dc_n > 0:
+        L, b, _ = dc_operator(mesh, om, np.zeros((N, group + 1)), dc_n, bc_inflow, group)
+        P = np.diag(L).copy()
+        M = -(L - np.diag(np.diag(L)))
+        return M, b, P
     M = np.zeros((N, N))
     b = np.zeros(N)
     P = np.zeros(N)
@@ -157,9 +163,9 @@ def _exp_factors(kt_V, P):
     return np.exp(-tau), f
 
 
-def solve_coupled_exp(mesh, omega, weight, kappa_abs, emissivity, kappa_scat=None, bc_inflow=None):
+def solve_coupled_exp(mesh, omega, weight, kappa_abs, emissivity, kappa_scat=None, bc_inflow=None, dc_n=0):
     """EXP law, all directions with isotropic scattering through the cell-mean J; returns the outgoing
-    I[D,N,G], the cell mean Ibar[D,N,G], J[N,G] and Gamma[N,G]."""
+    I[D,N,G], the cell mean Ibar[D,N,G], J[N,G] and Gamma[N,G]. dc_n > 0: scheme (b) transport."""
     D, N = omega.shape[0], mesh.n_cells
     G = kappa_abs.shape[1]
     ks = np.zeros_like(kappa_abs) if kappa_scat is None else kappa_scat
@@ -167,7 +173,7 @@ def solve_coupled_exp(mesh, omega, weight, kappa_abs, emissivity, kappa_scat=Non
     Ibar = np.zeros((D, N, G))
     for g in range(G):
         ktV = (kappa_abs[:, g] + ks[:, g]) * mesh.volume
-        ops = [inflow_operator(mesh, omega[d], bc_inflow, g) for d in range(D)]
+        ops = [inflow_operator(mesh, omega[d], bc_inflow, g, dc_n) for d in range(D)]
         assert all((P > 0).all() for _, _, P in ops)
         A = np.zeros((D * N, D * N))
         rhs = np.zeros(D * N)

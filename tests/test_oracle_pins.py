@@ -627,3 +627,19 @@ def test_dc_downwind_counts_match_the_paper():
     assert abs(per_a - g["value"]) <= g["abs_tol"]
     assert abs(per_b - gold["dc_downwind_per_cell"]["value"]) <= 0.01
 
+
+@pytest.mark.parametrize("box,albedo", [(False, 0.5), (True, 0.5)])
+def test_dc_with_the_exp_law(box, albedo):
+    # the two options combine: scheme (b) decides where the outflow goes, the EXP law how much of
+    # the inflow crosses the cell
+    p = configs.voronoi_small(150, periodic_box=box, n_dir=6, n_groups=1, seed=51, scatter_albedo=albedo,
+                              bc_inflow=not box)
+    r = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, kappa_scat=p.kappa_scat,
+                     bc_inflow=p.boundary_inflow, tol_scat=1e-15, max_it_scat=5000, tol_pbc=1e-15, max_it_pbc=5000,
+                     want_intensity=True, law="exp", dc_n=3)
+    assert r["rc"] == 0
+    I, _, J, Gam = dense.solve_coupled_exp(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, p.kappa_scat,
+                                           p.boundary_inflow, dc_n=3)
+    assert rel(r["I"], I) <= 1e-11 and rel(r["J"], J) <= 1e-11
+    assert abs(r["stats"]["defect"]) <= 1e-12
+
