@@ -213,23 +213,23 @@ def step_text(p, fused: int) -> str:
     return "classify + levelise + " + (it or "one sweep")
 
 
-def bytes_per_update(p) -> float:
+def bytes_per_update(p, law: str = "balance") -> float:
     """Algorithmic DRAM bytes per (cell, direction, group) update.
 
     Per task (cell, direction): the row bounds (8 B) and every face-side record of the cell
     (16 B each: neighbour + A n_out in FP32), F_bar = face sides / cells. Per group: the
-    source/denominator pair (8 B, FP32) and the intensity write (4 B); the upwind re-reads
-    hit L2 (the wavefront is on chip) and are not counted.
+    source/denominator pair (8 B, FP32) and the intensity write (4 B), and under the EXP law the
+    cell-mean write (4 B); the upwind re-reads hit L2 (the wavefront is on chip) and are not counted.
     """
     m = p.mesh
     S = 2 * m.n_faces - int((m.face_cells[:, 1] < 0).sum())
     fbar = S / m.n_cells
     G = p.n_groups
-    return (8.0 + 16.0 * fbar) / G + 12.0, fbar
+    return (8.0 + 16.0 * fbar) / G + 12.0 + (4.0 if law == "exp" else 0.0), fbar
 
 
 # ---------------------------------------------------------------------------------------------
-def cpu_baseline(p, seconds_target: float = 15.0) -> dict:
+def cpu_baseline(p, seconds_target: float = 15.0, law: str = "balance") -> dict:
     """The FP64 oracle as it stands, on a bounded sample: one sweep of a subset of directions."""
     import numpy as np
 
@@ -238,7 +238,8 @@ def cpu_baseline(p, seconds_target: float = 15.0) -> dict:
     N, G = p.mesh.n_cells, p.n_groups
     # calibrate on one direction, then size the sample to ~seconds_target of CPU work
     t0 = time.perf_counter()
-    oracle.solve(p.mesh, p.omega[:1], np.full(1, 4 * math.pi), p.kappa_abs, p.emissivity, max_it_pbc=1, threads=1)
+    oracle.solve(p.mesh, p.omega[:1], np.full(1, 4 * math.pi), p.kappa_abs, p.emissivity, max_it_pbc=1, threads=1,
+                 law=law)
     t1 = time.perf_counter() - t0
     nd = int(max(cores, min(p.n_dir, round(seconds_target / max(t1, 1e-3)))))
     nd = min(nd, p.n_dir)
@@ -247,7 +248,7 @@ def cpu_baseline(p, seconds_target: float = 15.0) -> dict:
     om = p.omega[:nd]
     w = np.full(nd, 4 * math.pi / nd)
     t0 = time.perf_counter()
-    oracle.solve(p.mesh, om, w, p.kappa_abs, p.emissivity, max_it_pbc=1, threads=min(cores, nd))
+    oracle.solve(p.mesh, om, w, p.kappa_abs, p.emissivity, max_it_pbc=1, threads=min(cores, nd), law=law)
     dt = time.perf_counter() - t0
     ups = N * nd * G / dt
     return {"value": ups, "unit": "updates/s", "cores": min(cores, nd), "kind": "oracle",
@@ -268,10 +269,10 @@ def run_reference(args, dist: Dist):
     om, w = p.omega[:nd], np.full(nd, 4 * math.pi / nd)
     N, G = p.mesh.n_cells, p.n_groups
     for _ in range(args.warmup):
-        oracle.solve(p.mesh, om, w, p.kappa_abs, p.emissivity, max_it_pbc=1, threads=nd)
+        oracle.solve(p.mesh, om, w, p.kappa_abs, p.emissivity, max_it_pbc=1, threads=nd, law=args.law)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.solve(p.mesh, om, w, p.kappa_abs, p.emissivity, max_it_pbc=1, threads=nd)
+        oracle.solve(p.mesh, om, w, p.kappa_abs, p.emissivity, max_it_pbc=1, threads=nd, law=args.law)
     dt = time.perf_counter() - t0
     v = N * nd * G * args.steps / dt
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "updates/s", "n_gpus": args.gpus,
@@ -310,7 +311,7 @@ def run_ours(args, dist: Dist):
     J = torch.empty((N, G), dtype=torch.float64, device="cuda")
     Gm = torch.empty_like(J)
     opts = default_opts(precision=32, relevel=1, tol_pbc=1e-6, max_it_pbc=200, tol_scat=1e-6, max_it_scat=200,
-                        fused_loops=args.fused_loops)
+                        fused_loops=args.fused_loops, law=args.law)
     for _ in range(args.warmup):
         ctx.solve_dev(J, Gm, opts)
     torch.cuda.synchronize()
@@ -345,7 +346,7 @@ def run_ours(args, dist: Dist):
     value, tmax = aggregate(dist, elapsed, agg["updates"])
 
     # roofline of the dominant kernel (the batched sweep), CUDA events around each launch
-    bpu, fbar = bytes_per_update(p)
+    bpu, fbar = bytes_per_update(p, args.law)
     avg_launch_s = agg["sweep_ms"] / max(1, agg["sweeps"]) / 1e3
     alg_bytes = bpu * N * D * G
     peaks = measured_peaks()
@@ -355,7 +356,9 @@ def run_ours(args, dist: Dist):
                 KERNELS.get(last.get("kernel_used", 0), "?"), {1: "level", 2: "dataflow"}.get(last["schedule_used"], "?"),
                 last["lanes_used"]),
             "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-            "peak_source": peaks["source"], "traffic": profiled_traffic(args.workload),
+            "peak_source": peaks["source"],
+            # the recorded DRAM traffic is that of the BALANCE law's kernel on the periodic box
+            "traffic": profiled_traffic(args.workload) if args.law == "balance" else None,
             "bytes_per_update": bpu, "face_sides_per_cell": fbar, "updates_per_launch": N * D * G,
             "avg_launch_ms": avg_launch_s * 1e3}
 
@@ -389,7 +392,7 @@ def run_ours(args, dist: Dist):
         d2h = 2 * N * G * 8
         ctx2 = Context(dist.local, stream.cuda_stream)
         o = default_opts(precision=32, tol_pbc=1e-6, max_it_pbc=200, tol_scat=1e-6, max_it_scat=200,
-                         fused_loops=args.fused_loops)
+                         fused_loops=args.fused_loops, law=args.law)
 
         def e2e_step():
             ctx2.set_mesh(volume=hv, face_cells=hfc, area=har, normal=hnr, flags=hfl)
@@ -416,7 +419,7 @@ def run_ours(args, dist: Dist):
 
     cpu = None
     if dist.rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline(p)
+        cpu = cpu_baseline(p, law=args.law)
     ctx.close()
     if dist.rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": dist.world, "steps": args.steps,
@@ -426,6 +429,7 @@ def run_ours(args, dist: Dist):
                           "face_sides_per_cell": round(fbar, 3), "precision": "FP32 intensities, FP64 tallies",
                           "l2": "no flush: >10 GB resident working set, 78x the 129 MB L2",
                           "step": step_text(p, args.fused_loops), "fused_loops": args.fused_loops,
+                          "law": args.law,
                           "parallelism": "one independent box per GPU" if dist.world > 1 else "1 GPU"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": agg["launches"],
                "clocks": clk,
@@ -545,6 +549,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the plain-FP64 comparison sweep")
+    ap.add_argument("--law", default="balance", choices=["balance", "exp"],
+                    help="absorption law of the cell update (exp: transmission exp(-tau) across the mean chord)")
     ap.add_argument("--fused-loops", type=int, default=0, choices=[0, 1],
                     help="with scattering and periodic faces: one sweep per periodic iteration (Sec. 2.7)")
     ap.add_argument("--profile-case", action="store_true", help="small fixed solve for ncu captures")

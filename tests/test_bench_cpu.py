@@ -27,6 +27,7 @@ def test_bytes_per_update_on_a_lattice(periodic, G):
     sides = 6 * n ** 3
     assert fbar == pytest.approx(sides / n ** 3)
     assert bpu == pytest.approx((8.0 + 16.0 * fbar) / G + 12.0)
+    assert bench.bytes_per_update(p, "exp")[0] == pytest.approx(bpu + 4.0)  # the cell-mean write
 
 
 def test_traffic_figure_follows_the_kernel_sources(tmp_path, monkeypatch):
