@@ -243,12 +243,14 @@ def test_uniform_periodic_fixed_point():
     assert np.max(np.abs(r2["J"] - C / (4 * math.pi))) <= 1e-11 * C
 
 
-def test_linearity_in_sources():
+@pytest.mark.parametrize("law,dc_n", [("balance", 0), ("exp", 0), ("balance", 3), ("exp", 3)])
+def test_linearity_in_sources(law, dc_n):
+    # every law and scheme is a linear system in the sources
     p = configs.voronoi_small(250, n_dir=8, n_groups=2, seed=29, scatter_albedo=0.3)
     rng = np.random.default_rng(1)
     e1 = rng.random(p.emissivity.shape) * (rng.random(p.emissivity.shape) < 0.1)
     e2 = rng.random(p.emissivity.shape) * (rng.random(p.emissivity.shape) < 0.1)
-    kw = dict(kappa_scat=p.kappa_scat, tol_scat=1e-15, max_it_scat=4000)
+    kw = dict(kappa_scat=p.kappa_scat, tol_scat=1e-15, max_it_scat=4000, law=law, dc_n=dc_n)
     J1 = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, e1, **kw)["J"]
     J2 = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, e2, **kw)["J"]
     J12 = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, e1 + e2, **kw)["J"]
