@@ -66,7 +66,9 @@ enum {
  *   EXP:     P I = exp(-tau) F_in + q (the source leaves unattenuated), and J is formed from the
  *            cell-mean intensity (F_in / P)(1 - exp(-tau)) / tau, so that kappa_t V times it is the
  *            removed flux; with kappa_a = 0 the scattered fraction is 1 - exp(-kappa_s V / P), the
- *            scattering law of Sec. 3.3. Forward solves only (the adjoint takes BALANCE). */
+ *            scattering law of Sec. 3.3. Forward solves only (the adjoint takes BALANCE). EXP runs in
+ *            the kernels that read the mesh rows (not the assembled operator), on the DATAFLOW schedule
+ *            when the schedule is AUTO (no autotuning), and keeps one more [D][N][G] array. */
 enum { SWEEP_LAW_BALANCE = 0, SWEEP_LAW_EXP = 1 };
 
 typedef struct {
