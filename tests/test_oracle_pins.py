@@ -645,3 +645,31 @@ def test_dc_with_the_exp_law(box, albedo):
     assert rel(r["I"], I) <= 1e-11 and rel(r["J"], J) <= 1e-11
     assert abs(r["stats"]["defect"]) <= 1e-12
 
+
+# (small periodic boxes only for seeds whose tessellation closes)
+@pytest.mark.parametrize("seed,box", [(s, False) for s in range(61, 73)] + [(s, True) for s in (52, 56, 62, 67, 71)])
+def test_every_option_against_its_dense_solve(seed, box):
+    # several small meshes, every combination of law, transport scheme and scattering, against the
+    # dense solve of the same system; conservation throughout
+    p = configs.voronoi_small(150 if box else 90, periodic_box=box, n_dir=4, n_groups=1, seed=seed,
+                              scatter_albedo=0.4, bc_inflow=not box)
+    kw = dict(bc_inflow=p.boundary_inflow, tol_scat=1e-15, max_it_scat=5000, tol_pbc=1e-15, max_it_pbc=5000,
+              want_intensity=True)
+    for law in ("balance", "exp"):
+        for dc_n in (0, 2, 3):
+            for ks in (None, p.kappa_scat):
+                r = oracle.solve(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, kappa_scat=ks, law=law,
+                                 dc_n=dc_n, **kw)
+                assert r["rc"] == 0
+                if law == "exp":
+                    I = dense.solve_coupled_exp(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, ks,
+                                                p.boundary_inflow, dc_n=dc_n)[0]
+                elif dc_n:
+                    I = dense.solve_coupled_dc(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, dc_n, ks,
+                                               p.boundary_inflow)[0]
+                else:
+                    I = dense.solve_coupled(p.mesh, p.omega, p.weight, p.kappa_abs, p.emissivity, ks,
+                                            p.boundary_inflow)[0]
+                assert rel(r["I"], I) <= 1e-11, (law, dc_n, ks is not None)
+                assert abs(r["stats"]["defect"]) <= 1e-12
+
