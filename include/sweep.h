@@ -98,7 +98,19 @@ typedef struct {
                                iterations, stop when both changes are below tol_scat and tol_pbc (at most max_it_pbc
                                sweeps). Same fixed point as the nested loops (0, default), far fewer sweeps.
                                Ignored unless both loops are on. */
+    int32_t op_format;      /* SWEEP_OP_*: form of the assembled operator of the FP32 forward sweep */
+    int32_t packets_per_step; /* packed operator: packets a warp takes per step, 1 or 2 (0 = autotuned) */
 } sweep_opts;
+
+/* Forms of the assembled transport operator (the rows of L_Omega, Sec. 2.3, built once per
+ * levelisation and streamed by every FP32 forward BALANCE sweep of the solve):
+ *   AUTO:    PACKETS where they apply (1, 2 or 4 groups, n_cells x n_dir <= 2^31, lanes_per_task 0),
+ *            else LINES;
+ *   LINES:   one 128-byte line per task (header + 14 entry slots), lanes_per_task lanes per task;
+ *   PACKETS: tasks packed back to back, within a wavefront level, into 512-byte warp packets (two
+ *            8-byte slots per lane: the task's inflow entries, then its header), so that no entry slot
+ *            of a warp step is empty and every lane gathers; falls back to LINES where it does not apply. */
+enum { SWEEP_OP_AUTO = 0, SWEEP_OP_LINES = 1, SWEEP_OP_PACKETS = 2 };
 
 typedef struct {
     int32_t it_scat, it_pbc;   /* sweeps done in the source iteration (total) and periodic iterations */
@@ -116,7 +128,7 @@ typedef struct {
     int32_t sweep_launches;    /* batched-sweep kernel launches timed in t_ms[2] */
     int32_t schedule_used;     /* SWEEP_SCHED_* that ran */
     int32_t kernel_launches;   /* all kernels this call launched (including the autotuner's) */
-    int32_t lanes_used;        /* lanes per task of the batched sweep that ran */
+    int32_t lanes_used;        /* lanes per task of the batched sweep that ran (packed operator: 32 x packets per step) */
     int32_t threads_used;      /* threads per block of the batched sweep that ran */
     int32_t blocks_per_sm_used;/* resident blocks per SM it was launched with (0 = maximum) */
     int32_t kernel_used;       /* SWEEP_KERNEL_* form of the batched sweep that ran last */
@@ -131,7 +143,8 @@ enum {
     SWEEP_KERNEL_RECORDS = 3,        /* FP32 forward, lane groups over task records and mesh rows */
     SWEEP_KERNEL_OPERATOR = 4,       /* FP32 forward over the assembled operator, lane groups */
     SWEEP_KERNEL_OPERATOR_LEAN = 5,  /* the same, one group and 8 lanes per task, dataflow schedule */
-    SWEEP_KERNEL_OPERATOR_PAIR = 6   /* the same with two tasks per 8-lane group per step */
+    SWEEP_KERNEL_OPERATOR_PAIR = 6,  /* the same with two tasks per 8-lane group per step */
+    SWEEP_KERNEL_PACKED = 7          /* FP32 forward over the packed operator (whole warps per packet of tasks) */
 };
 
 /* Fill *opts with defaults: precision 32, AUTO schedule, tolerances 1e-6, 100 iterations. */

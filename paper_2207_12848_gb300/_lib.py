@@ -25,7 +25,9 @@ SWEEP_SCHED_AUTO, SWEEP_SCHED_LEVEL, SWEEP_SCHED_DATAFLOW, SWEEP_SCHED_PLAIN = 0
 SCHEDULES = {"auto": 0, "level": 1, "dataflow": 2, "plain": 3}
 LAWS = {"balance": 0, "exp": 1}
 # forms of the batched sweep kernel (sweep_stats.kernel_used)
-KERNELS = {0: "none", 1: "k_plain", 2: "k_sweep", 3: "k_sweep_rec", 4: "k_sweep_op", 5: "k_sweep_op1", 6: "k_sweep_op2"}
+KERNELS = {0: "none", 1: "k_plain", 2: "k_sweep", 3: "k_sweep_rec", 4: "k_sweep_op", 5: "k_sweep_op1", 6: "k_sweep_op2",
+           7: "k_sweep_pk"}
+OP_FORMATS = {"auto": 0, "lines": 1, "packets": 2}
 
 # every entry point include/sweep.h declares
 EXPORTS = ("sweep_default_opts", "sweep_create", "sweep_destroy", "sweep_set_mesh", "sweep_set_directions",
@@ -41,7 +43,8 @@ class sweep_opts(ctypes.Structure):
                 ("relevel", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("spin_budget", ctypes.c_int64), ("debug_stall", ctypes.c_int32),
                 ("lanes_per_task", ctypes.c_int32), ("geometry_only", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("fused_loops", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("fused_loops", ctypes.c_int32),
+                ("op_format", ctypes.c_int32), ("packets_per_step", ctypes.c_int32)]
 
 
 class sweep_stats(ctypes.Structure):
@@ -119,6 +122,8 @@ def default_opts(**kw) -> sweep_opts:
             v = SCHEDULES[v]
         if k == "law" and isinstance(v, str):
             v = LAWS[v]
+        if k == "op_format" and isinstance(v, str):
+            v = OP_FORMATS[v]
         if not hasattr(o, k):
             raise KeyError(k)
         setattr(o, k, v)

@@ -71,7 +71,7 @@ struct sweep_ctx {
     void* Imean = nullptr;
     size_t imean_bytes = 0;
     // autotuner: schedule and block size per (precision, G)
-    int tuned[2][9][2][4] = {};  // [precision][groups][operator mode] -> schedule, threads, lanes, blocks/SM
+    int tuned[2][9][3][4] = {};  // [precision][groups][operator form OPF_*] -> schedule, threads, lanes, blocks/SM
     int64_t launches = 0;  // kernels launched by this context
     PeriodicTable ptab;          // periodic-inflow weights, rebuilt at the start of each periodic solve
     cudaStream_t gst = nullptr;  // capture/replay stream of the iteration graphs
@@ -113,6 +113,8 @@ void dfree(T*& p) {
 void free_levels(Levels& L) {
     dfree(L.raw); dfree(L.task); dfree(L.trec); dfree(L.info); dfree(L.level); dfree(L.lvl_cnt); dfree(L.pad_off);
     dfree(L.lev_chunk); dfree(L.seg_off); dfree(L.op); dfree(L.dlev);
+    dfree(L.pk); dfree(L.pk_meta); dfree(L.lev_pk); dfree(L.pk_grp); dfree(L.pk_cnt); dfree(L.pk_off); dfree(L.pk_scan);
+    dfree(L.pk_flag);
     L = Levels();
 }
 
@@ -256,7 +258,12 @@ SweepArgs make_args(sweep_ctx* c, const Levels& L, int precision, const void* cm
     // the EXP law runs in the generic and plain kernels; the adjoint takes BALANCE
     a.law = (!reverse && o) ? o->law : SWEEP_LAW_BALANCE;
     a.Imean = a.law ? c->Imean : nullptr;
-    a.op = (precision == 32 && !reverse && !a.law && L.op_valid && !(o && o->geometry_only)) ? L.op : nullptr;
+    const bool opr = precision == 32 && !reverse && !a.law && L.op_valid && !(o && o->geometry_only);
+    a.op = opr && L.op_format == OPF_LINES ? L.op : nullptr;
+    a.pk = opr && L.op_format == OPF_PACKETS ? L.pk : nullptr;
+    a.pk_meta = L.pk_meta;
+    a.n_pk = L.n_pk;
+    a.lev_pk = L.lev_pk;
     a.n_chunks = L.h_lev_chunk.empty() ? 0 : L.h_lev_chunk.back();
     a.lev_chunk = L.lev_chunk;
     a.n_levels = L.n_levels;
@@ -309,7 +316,8 @@ sweep_status run_sweep(sweep_ctx* c, const Levels& L, int precision, int schedul
         }
     } else {
         // the EXP law runs in the generic kernel, whose occupancy the reverse query gives
-        int per_sm = sweep_occupancy(precision, a.G, threads, L.nd, lanes, a.reverse || a.law, a.op != nullptr);
+        const int fmt = a.pk ? OPF_PACKETS : (a.op ? OPF_LINES : OPF_NONE);
+        int per_sm = sweep_occupancy(precision, a.G, threads, L.nd, lanes, a.reverse || a.law, fmt);
         if (per_sm < 1) return bad(c, "sweep kernel does not fit on an SM");
         if (bpsm > 0 && bpsm < per_sm) per_sm = bpsm;
         a.level_sync = schedule == SWEEP_SCHED_LEVEL ? 1 : 0;
@@ -417,8 +425,8 @@ sweep_status graph_loop(sweep_ctx* c, const sweep_opts& o, int prec, const void*
     if (s != SWEEP_OK) return s;
     cudaStream_t gs = c->gst;
     IterHost* hp = reinterpret_cast<IterHost*>(c->hpin);
-    int per_sm = sweep_occupancy(prec, G, threads, c->lev.nd, lanes, o.law ? 1 : 0,
-                                 prec == 32 && !o.law && c->lev.op_valid && !o.geometry_only);
+    const int fmt = (prec == 32 && !o.law && c->lev.op_valid && !o.geometry_only) ? c->lev.op_format : OPF_NONE;
+    int per_sm = sweep_occupancy(prec, G, threads, c->lev.nd, lanes, o.law ? 1 : 0, fmt);
     if (per_sm < 1) return bad(c, "sweep kernel does not fit on an SM");
     if (bpsm > 0 && bpsm < per_sm) per_sm = bpsm;
     const int period = pbc ? 4 : 2;
@@ -820,43 +828,98 @@ sweep_status sweep_set_material_dev(sweep_ctx* c, int32_t G, const double* ka, c
 // ---------------------------------------------------------------------------------------------
 namespace {
 
-// Assembles the transport operator of the levelised directions (one 128-byte line per task) when
-// device memory allows; otherwise the FP32 sweep reads the mesh geometry directly.
-sweep_status assemble_operator(sweep_ctx* c, Levels& L, float* t_ms) {
+// Form of the assembled operator a solve with these options sweeps over (OPF_NONE: it reads the mesh).
+int wanted_format(sweep_ctx* c, const Levels& L, const sweep_opts* o, int prec) {
+    if (prec != 32 || !o || o->law != SWEEP_LAW_BALANCE || o->geometry_only || o->schedule == SWEEP_SCHED_PLAIN)
+        return OPF_NONE;
+    const int G = c->G;
+    const bool pk_ok = (G == 1 || G == 2 || G == 4) && (uint64_t)c->mesh.N * (uint64_t)L.nd <= (1ull << 31);
+    if (pk_ok && (o->op_format == SWEEP_OP_PACKETS || (o->op_format == SWEEP_OP_AUTO && o->lanes_per_task == 0)))
+        return OPF_PACKETS;
+    return OPF_LINES;
+}
+
+// device memory for an operator of `bytes`, keeping a margin for the solve buffers allocated later
+bool op_fits(size_t bytes) {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    return bytes + (size_t)(2ull << 30) <= free_b;
+}
+
+// Assembles the transport operator of the levelised directions in the form the solve sweeps over
+// (128-byte lines or packets), when device memory allows; otherwise the FP32 sweep reads the mesh
+// geometry directly. Built once per levelisation and kept while the form stays the same.
+sweep_status ensure_operator(sweep_ctx* c, Levels& L, const sweep_opts* o, int prec, float* t_ms) {
+    int want = wanted_format(c, L, o, prec);
+    if (want == OPF_NONE || (L.op_valid && L.op_format == want)) return SWEEP_OK;
     L.op_valid = false;
-    const int64_t tasks = L.h_lev_chunk.empty() ? 0 : L.h_lev_chunk.back() * 32;
-    const size_t bytes = (size_t)tasks * 128;
-    if (bytes > L.op_bytes) {
-        dfree(L.op);
-        L.op_bytes = 0;
-        size_t free_b = 0, total_b = 0;
-        cudaMemGetInfo(&free_b, &total_b);
-        // keep a margin for the solve buffers allocated later
-        if (bytes + (size_t)(2ull << 30) > free_b) return SWEEP_OK;
-        if (cudaMalloc(&L.op, bytes) != cudaSuccess) {
-            cudaGetLastError();
-            L.op = nullptr;
-            return SWEEP_OK;
-        }
-        L.op_bytes = bytes;
-    }
     ScopedEvent e0, e1;
     cudaEventRecord(e0, c->st);
-    CKL(build_operator(c->mesh, L, c->om64, c->om32, c->om32lo, c->st), "assemble operator");
+    if (want == OPF_PACKETS) {
+        dfree(L.op);  // the other form's buffer
+        L.op_bytes = 0;
+        int64_t n_pk = 0;
+        CKL(pack_plan(c->mesh, L, c->om64, c->om32, c->om32lo, c->st, &n_pk), "plan packed operator");
+        bool ok = n_pk >= 0;  // < 0: a task has more inflow sides than a packet holds
+        if (ok && n_pk > L.pk_cap) {
+            dfree(L.pk);
+            dfree(L.pk_meta);
+            L.pk_cap = 0;
+            const int64_t cap = n_pk + n_pk / 16 + 64;
+            ok = op_fits((size_t)cap * 520) && cudaMalloc(&L.pk, (size_t)cap * 512) == cudaSuccess &&
+                 cudaMalloc(&L.pk_meta, (size_t)cap * 8) == cudaSuccess;
+            if (ok) L.pk_cap = cap;
+            else {
+                cudaGetLastError();
+                dfree(L.pk);
+                dfree(L.pk_meta);
+            }
+        }
+        if (ok) {
+            CKL(pack_write(c->mesh, L, c->om64, c->om32, c->om32lo, c->st), "write packed operator");
+            c->launches += 1;  // the level table
+            L.n_pk = n_pk;
+            L.op_format = OPF_PACKETS;
+            L.op_valid = true;
+        } else {
+            want = OPF_LINES;
+        }
+    }
+    if (want == OPF_LINES) {
+        dfree(L.pk);
+        dfree(L.pk_meta);
+        L.pk_cap = 0;
+        const int64_t tasks = L.h_lev_chunk.empty() ? 0 : L.h_lev_chunk.back() * 32;
+        const size_t bytes = (size_t)tasks * 128;
+        bool ok = true;
+        if (bytes > L.op_bytes) {
+            dfree(L.op);
+            L.op_bytes = 0;
+            ok = op_fits(bytes) && cudaMalloc(&L.op, bytes) == cudaSuccess;
+            if (ok) L.op_bytes = bytes;
+            else {
+                cudaGetLastError();
+                L.op = nullptr;
+            }
+        }
+        if (ok) {
+            CKL(build_operator(c->mesh, L, c->om64, c->om32, c->om32lo, c->st), "assemble operator");
+            L.op_format = OPF_LINES;
+            L.op_valid = true;
+        }
+    }
     cudaEventRecord(e1, c->st);
     CK(cudaEventSynchronize(e1), "assemble operator");
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
     if (t_ms) *t_ms = ms;
-    L.op_valid = true;
     return SWEEP_OK;
 }
 
-sweep_status ensure_levels(sweep_ctx* c, const sweep_opts* o, float* t1, float* t2, float* t3 = nullptr) {
+sweep_status ensure_levels(sweep_ctx* c, const sweep_opts* o, float* t1, float* t2) {
     if (c->lev.valid && !(o && o->relevel) && c->lev.nd == c->D && c->lev.d0 == 0) return SWEEP_OK;
-    sweep_status s = run_levelise(c, c->lev, 0, c->D, budget_of(o), t1, t2);
-    if (s != SWEEP_OK) return s;
-    return assemble_operator(c, c->lev, t3);
+    c->lev.op_valid = false;
+    return run_levelise(c, c->lev, 0, c->D, budget_of(o), t1, t2);
 }
 
 sweep_status ensure_solution(sweep_ctx* c, int prec, bool two) {
@@ -909,14 +972,19 @@ struct LaunchCfg {
 
 // choose the batched-sweep configuration: time one sweep per candidate (results are identical for all)
 sweep_status autotune(sweep_ctx* c, int prec, const void* cm, const float* bc32, const sweep_opts* o, LaunchCfg* out) {
-    const bool op = prec == 32 && c->lev.op_valid && !(o && o->geometry_only);
-    int* t4 = c->tuned[prec == 64][c->G][op ? 1 : 0];
+    const int fmt = (prec == 32 && c->lev.op_valid && !(o && o->geometry_only)) ? c->lev.op_format : OPF_NONE;
+    int* t4 = c->tuned[prec == 64][c->G][fmt];
     if (t4[0]) {
         *out = LaunchCfg{t4[0], t4[1], t4[2], t4[3]};
         return SWEEP_OK;
     }
     std::vector<LaunchCfg> cand;
-    if (op) {
+    if (fmt == OPF_PACKETS) {
+        // packets per warp step: one (lanes 32) or two (lanes 64); the level-synchronous form with two
+        cand.push_back({SWEEP_SCHED_DATAFLOW, 256, 64, 0});
+        cand.push_back({SWEEP_SCHED_DATAFLOW, 256, 32, 0});
+        cand.push_back({SWEEP_SCHED_LEVEL, 256, 64, 0});
+    } else if (fmt == OPF_LINES) {
         // 8 lanes per task (4 tasks per warp step) and 4 lanes per task (8 tasks per step)
         cand.push_back({SWEEP_SCHED_DATAFLOW, 256, 8, 0});
         cand.push_back({SWEEP_SCHED_DATAFLOW, 256, 16, 0});
@@ -1000,8 +1068,12 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     const int64_t launches0 = c->launches;
     ScopedEvent t0, t1;
     cudaEventRecord(t0, c->st);
+    if (o.op_format < SWEEP_OP_AUTO || o.op_format > SWEEP_OP_PACKETS) return bad(c, "op_format must be 0, 1 or 2");
+    if (o.packets_per_step < 0 || o.packets_per_step > 2) return bad(c, "packets_per_step must be 0, 1 or 2");
     float tc = 0, tl = 0, top = 0;
-    sweep_status s = ensure_levels(c, &o, &tc, &tl, &top);
+    sweep_status s = ensure_levels(c, &o, &tc, &tl);
+    if (s != SWEEP_OK) return s;
+    s = ensure_operator(c, c->lev, &o, prec, &top);
     if (s != SWEEP_OK) return s;
     S.t_ms[0] = tc;
     S.t_ms[1] = tl;
@@ -1052,6 +1124,12 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
         if (s != SWEEP_OK) return s;
         if (!o.block_threads) threads = tt;
         if (!o.lanes_per_task) lanes = tl;
+    }
+    // the packed operator's kernel has whole warps per packet: lanes = 32 x packets per warp step
+    const bool packed = prec == 32 && !o.law && !o.geometry_only && c->lev.op_valid && c->lev.op_format == OPF_PACKETS;
+    if (!plain && packed) {
+        if (o.packets_per_step) lanes = 32 * o.packets_per_step;
+        else if (lanes < 32) lanes = 64;
     }
     // the periodic inflow of the first sweep: the previous solve's intensities or zeros
     int prev = -1;
@@ -1341,6 +1419,7 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
         float a1 = 0, a2 = 0;
         if (nb == D) {
             s = ensure_levels(c, &o, &a1, &a2);
+            if (s == SWEEP_OK) s = ensure_operator(c, c->lev, &o, prec, nullptr);
             L = &c->lev;
         } else {
             s = run_levelise(c, c->adj_lev, d0, nb, budget_of(&o), &a1, &a2);

@@ -29,6 +29,12 @@ constexpr double FOURPI = 4.0 * 3.14159265358979323846;
 constexpr float BAND_REL = 1.0e-6f;
 // inflow sides held in a 128-byte operator line; tasks with more take the geometry path
 constexpr int OP_MAX = 14;
+// Packed operator: a packet is 32 lanes x 16 bytes (two 8-byte slots per lane); a task holds its
+// inflow entries, then its header in the odd slot of its last lane, so at most PK_MAX_IN entries.
+constexpr int PK_MAX_IN = 63;
+constexpr uint32_t PK_BOUNDARY = 0x80000000u;  // source-index bit of a boundary-face entry
+// forms of the assembled operator
+enum { OPF_NONE = 0, OPF_LINES = 1, OPF_PACKETS = 2 };
 
 struct GridBar {
     unsigned count;
@@ -88,6 +94,26 @@ __device__ __forceinline__ float ld_relaxed_hint(const float* p, uint64_t pol) {
 }
 __device__ __forceinline__ void st_relaxed_hint(float* p, float v, uint64_t pol) {
     asm volatile("st.relaxed.gpu.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol));
+}
+__device__ __forceinline__ float2 ld_relaxed_hint_v2(const float* p, uint64_t pol) {
+    float2 v;
+    asm volatile("ld.relaxed.gpu.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+                 : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float4 ld_relaxed_hint_v4(const float* p, uint64_t pol) {
+    float4 v;
+    asm volatile("ld.relaxed.gpu.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_hint_v2(float* p, float2 v, uint64_t pol) {
+    asm volatile("st.relaxed.gpu.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y),
+                 "l"(pol));
+}
+__device__ __forceinline__ void st_relaxed_hint_v4(float* p, float4 v, uint64_t pol) {
+    asm volatile("st.relaxed.gpu.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x),
+                 "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol));
 }
 __device__ __forceinline__ void st_relaxed(float* p, float v) {
     asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v));
@@ -255,6 +281,21 @@ struct Levels {
     int4* op = nullptr;          // assembled operator: headers then entries (see build_operator), or null
     size_t op_bytes = 0;
     bool op_valid = false;
+    int op_format = OPF_NONE;    // form of the assembled operator when op_valid
+    // packed operator (OPF_PACKETS): packets of 32 int4, their {head mask, overflow mask}, the first
+    // packet of each level; packing groups (runs of up to 32 chunks of one level) and their counts
+    int4* pk = nullptr;
+    uint2* pk_meta = nullptr;
+    int64_t pk_cap = 0;          // packets allocated
+    int64_t n_pk = 0;            // packets of the current operator (even within every level)
+    int64_t* lev_pk = nullptr;   // device [n_levels+1]
+    int32_t* pk_grp = nullptr;   // device [ng+1] first chunk of each packing group, then [n_levels+1] first group
+    int32_t* pk_cnt = nullptr;   // device [ng] packets per group
+    int64_t* pk_off = nullptr;   // device [ng+1] first packet of each group
+    int64_t* pk_scan = nullptr;  // scan scratch
+    int64_t pk_grp_cap = 0;      // groups (and levels + 1) the tables above hold
+    int64_t pk_ng = 0;
+    int32_t* pk_flag = nullptr;  // device word: a task has more than PK_MAX_IN inflow sides
     int32_t* level = nullptr;    // [nd][N] (during levelisation: minus the upwind cells still unsolved)
     int32_t* lvl_cnt = nullptr;  // [N+2]
     uint32_t* pad_off = nullptr; // [N+2] start of each level in the padded list
@@ -276,6 +317,10 @@ struct SweepArgs {
     const uint32_t* task;
     const int4* trec;     // task records (FP32 forward sweep)
     const int4* op;       // assembled operator headers (one int4 per task), or null (FP32 forward sweep)
+    const int4* pk;       // packed operator (FP32 forward sweep), or null
+    const uint2* pk_meta; // [n_pk] {head mask, long-task flag} of each packet
+    int64_t n_pk;
+    const int64_t* lev_pk;  // [n_levels+1] first packet of each level
     int64_t n_chunks;
     const int64_t* lev_chunk;
     int n_levels;
@@ -320,11 +365,18 @@ cudaError_t launch_validate_mesh(int64_t N, int64_t F, const double* vol, const 
 
 cudaError_t build_operator(const DevMesh& m, const Levels& L, const double* om64_all, const float4* om32_all,
                            const float4* om32lo_all, cudaStream_t st);
+// packed operator: plan (groups, packet counts; *n_pk = packets needed, or -1 when a task has more
+// inflow sides than a packet holds) then write into L.pk / L.pk_meta
+cudaError_t pack_plan(const DevMesh& m, Levels& L, const double* om64_all, const float4* om32_all,
+                      const float4* om32lo_all, cudaStream_t st, int64_t* n_pk);
+cudaError_t pack_write(const DevMesh& m, Levels& L, const double* om64_all, const float4* om32_all,
+                       const float4* om32lo_all, cudaStream_t st);
 cudaError_t levelise(const DevMesh& m, Levels& L, const double* om64_all, const float4* om32_all,
                      const float4* om32lo_all, int dev_sms, GridBar* bar, int* err, long long budget,
                      int64_t* d_scratch, cudaStream_t st, float* t_classify, float* t_levelise, std::string* msg);
 
-int sweep_occupancy(int precision, int G, int threads, int nd, int lanes, int reverse, bool op);
+// fmt: OPF_* form of the assembled operator the launch reads (OPF_NONE: the mesh rows)
+int sweep_occupancy(int precision, int G, int threads, int nd, int lanes, int reverse, int fmt);
 cudaError_t launch_sweep(const SweepArgs& a, int precision, int blocks, int threads, cudaStream_t st,
                          int* kernel = nullptr);
 cudaError_t launch_plain_level(const SweepArgs& a, uint32_t begin, uint32_t end, cudaStream_t st);

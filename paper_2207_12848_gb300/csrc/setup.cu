@@ -892,6 +892,284 @@ cudaError_t build_operator(const DevMesh& m, const Levels& L, const double* om64
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------------
+// Packed operator: the rows of L_Omega (Sec. 2.3: row t = task (c, Omega), its inflow entries in
+// row order and its diagonal P_c) packed back to back into 512-byte packets, so that a warp step
+// streams no empty entry slots and every lane gathers. A packet is 32 lanes x 16 bytes; lane l holds
+// slots 2l and 2l+1 (int2 {source, weight}):
+//   a task with n inflow entries takes ceil((n + 1) / 2) consecutive lanes: entries 0..n-1 in the
+//   first slots, then (n even) one empty slot {0, 0}, then its header {task entry, P_c} in the odd
+//   slot of its last lane (its "head" lane);
+//   entry {dl*N + nb, +w}: interior upwind cell, this sweep's intensities; {dl*N + partner, -w}:
+//   periodic partner, the previous iteration's intensities; {b | PK_BOUNDARY, -w}: boundary face b,
+//   the boundary inflow; w = |A_f n_f.Omega| in FP32 (the same weight as the 128-byte line);
+//   the inflow sides of a row longer than 32 sides are completed by classifying the sides past 32.
+// Per packet, meta = {head mask (bit l: lane l is a head lane), 1 if a task spans more than 16 lanes}.
+// Tasks are packed in sweep order, next-fit, within packing groups of up to 32 chunks (1024 tasks)
+// of one level; a group's packet count is rounded up to even with an empty packet, so that two
+// consecutive packets of a warp step always belong to one level (independent tasks).
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+constexpr int PK_GROUP_CHUNKS = 32;
+
+struct PackArgs {
+    const int4* trec;
+    const int32_t* grp;  // [ng+1] first chunk of each group
+    int64_t ng;
+    const uint32_t* rowptr;
+    const int4* side;
+    const d4* side64;
+    const float4* side_lo;
+    const float4* om32;
+    const float4* om32lo;
+    const double* om64;
+    uint32_t cmask;
+    int cshift;
+    uint32_t N;
+    int32_t* cnt;        // count pass: packets per group
+    int32_t* flag;       // count pass: set when a task has more than PK_MAX_IN inflow sides
+    const int64_t* off;  // write pass: first packet of each group
+    int4* pk;
+    uint2* meta;
+};
+
+// inflow sides of a row past its first 32 (rows longer than 32 sides; their sign as in k_classify)
+__device__ int pk_inflow_past32(const PackArgs& a, const int4 tr, int stop_at, uint32_t* side_out) {
+    const uint32_t e = (uint32_t)tr.x, c = e & a.cmask, dl = e >> a.cshift;
+    const float4 om = a.om32[dl];
+    const double* o64 = a.om64 + 3 * dl;
+    const uint32_t r0 = (uint32_t)tr.y, r1 = a.rowptr[c + 1];
+    int k = 0;
+    for (uint32_t s = r0 + 32; s < r1; ++s) {
+        const int4 r = a.side[s];
+        const float ax = __int_as_float(r.y), ay = __int_as_float(r.z), az = __int_as_float(r.w);
+        if (classify_side(dot32(ax, ay, az, om), ax, ay, az, a.side64, s, o64) >= 0) continue;
+        if (k == stop_at) {
+            *side_out = s;
+            return k;
+        }
+        ++k;
+    }
+    return k;
+}
+
+// inflow entries of a task
+__device__ __forceinline__ int pk_task_inflow(const PackArgs& a, const int4 tr) {
+    int n = __popc((uint32_t)tr.w);
+    if (tr.z < 0) {
+        uint32_t dummy;
+        n += pk_inflow_past32(a, tr, -1, &dummy);
+    }
+    return n;
+}
+
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int j) {
+    for (int q = 0; q < j; ++q) m &= m - 1;
+    return __ffs(m) - 1;
+}
+
+// entry j of a task: its j-th inflow side in row order
+__device__ int2 pk_entry(const PackArgs& a, const int4 tr, int j, uint32_t slab, const float4& om, const float4& oml) {
+    const uint32_t inm = (uint32_t)tr.w;
+    const int nm = __popc(inm);
+    uint32_t s = 0;
+    if (j < nm) s = (uint32_t)tr.y + (uint32_t)nth_set_bit(inm, j);
+    else pk_inflow_past32(a, tr, j - nm, &s);
+    const int4 r = a.side[s];
+    const float w = side_weight(r, a.side_lo[s], om, oml);
+    if (r.x >= 0 && !(r.x & NBR_PERIODIC)) return make_int2((int)(slab + (uint32_t)r.x), __float_as_int(w));
+    if (r.x >= 0) return make_int2((int)(slab + (uint32_t)(r.x & NBR_MASK)), __float_as_int(-w));
+    return make_int2((int)((uint32_t)(-1 - r.x) | PK_BOUNDARY), __float_as_int(-w));
+}
+
+// One warp per packing group. The tasks of the group are read 32 at a time (lane i: task i); a
+// warp prefix sum of their lane counts places them next-fit: every round closes at most one packet.
+// The count pass only counts packets; the write pass repeats the same placement, hands each packet
+// lane its task by shuffles, and writes the packet (16 bytes per lane, one coalesced store).
+template <bool WRITE>
+__global__ void __launch_bounds__(256) k_pack(PackArgs a) {
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (g >= a.ng) return;  // whole warps
+    const int lane = threadIdx.x & 31;
+    const int64_t t_begin = (int64_t)a.grp[g] * 32, t_end = (int64_t)a.grp[g + 1] * 32;
+    int64_t pkt = WRITE ? a.off[g] : 0;
+    int64_t npk = 0;
+    int fill = 0;  // lanes taken in the open packet
+    // the task of this lane of the open packet: record, rank of this lane in the task, its entries
+    int4 my_tr = make_int4((int)TASK_PAD, 0, 0, 0);
+    int my_j = 0, my_n = 0;
+    auto flush = [&]() {
+        if (WRITE) {
+            const bool valid = (uint32_t)my_tr.x != TASK_PAD;
+            const int lanes = (my_n + 2) >> 1;
+            const bool head = valid && my_j == lanes - 1;
+            int4 out = make_int4(0, 0, 0, 0);
+            if (valid) {
+                const uint32_t dl = (uint32_t)my_tr.x >> a.cshift;
+                const uint32_t slab = dl * a.N;
+                const float4 om = a.om32[dl], oml = a.om32lo[dl];
+                const int j0 = 2 * my_j;
+                const int2 s0 = j0 < my_n ? pk_entry(a, my_tr, j0, slab, om, oml) : make_int2(0, 0);
+                const int2 s1 = head ? make_int2(my_tr.x, my_tr.z & 0x7fffffff)
+                                     : (j0 + 1 < my_n ? pk_entry(a, my_tr, j0 + 1, slab, om, oml) : make_int2(0, 0));
+                out = make_int4(s0.x, s0.y, s1.x, s1.y);
+            }
+            const unsigned hm = __ballot_sync(0xffffffffu, head);
+            const unsigned lng = __ballot_sync(0xffffffffu, head && lanes > 16);
+            a.pk[pkt * 32 + lane] = out;
+            if (lane == 0) a.meta[pkt] = make_uint2(hm, lng ? 1u : 0u);
+            ++pkt;
+            my_tr = make_int4((int)TASK_PAD, 0, 0, 0);
+        }
+        ++npk;
+        fill = 0;
+    };
+    for (int64_t t0 = t_begin; t0 < t_end; t0 += 32) {
+        const int4 tr = a.trec[t0 + lane];
+        const bool valid = (uint32_t)tr.x != TASK_PAD;
+        int n = valid ? pk_task_inflow(a, tr) : 0;
+        if (n > PK_MAX_IN) {
+            if (!WRITE) atomicOr(a.flag, 1);
+            n = PK_MAX_IN;  // the plan is discarded
+        }
+        const int sz = valid ? (n + 2) >> 1 : 0;
+        int incl = sz;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        const int excl = incl - sz;
+        int base = 0;  // lanes of this batch's tasks placed so far
+        unsigned todo = __ballot_sync(0xffffffffu, sz > 0);
+        while (todo) {
+            const bool mine = (todo >> lane) & 1u;
+            const unsigned fit = __ballot_sync(0xffffffffu, mine && incl - base <= 32 - fill);
+            if (fit == 0) {  // the next task does not fit: close the packet
+                flush();
+                continue;
+            }
+            const int lo = __ffs(fit) - 1, hi = 31 - __clz(fit);
+            const int used = __shfl_sync(0xffffffffu, incl, hi) - base;
+            if (WRITE) {
+                const int start = fill + excl - base;  // first packet lane of a fitting task
+                const unsigned smask = __reduce_or_sync(0xffffffffu, ((fit >> lane) & 1u) ? (1u << start) : 0u);
+                const bool take = lane >= fill && lane < fill + used;
+                const int k = __popc(smask & ((2u << lane) - 1u)) - 1;  // rank of this lane's task among the fitting
+                const int src = take ? lo + k : lane;
+                const int4 r = make_int4(__shfl_sync(0xffffffffu, tr.x, src), __shfl_sync(0xffffffffu, tr.y, src),
+                                         __shfl_sync(0xffffffffu, tr.z, src), __shfl_sync(0xffffffffu, tr.w, src));
+                const int s_start = __shfl_sync(0xffffffffu, start, src);
+                const int s_n = __shfl_sync(0xffffffffu, n, src);
+                if (take) {
+                    my_tr = r;
+                    my_j = lane - s_start;
+                    my_n = s_n;
+                }
+            }
+            fill += used;
+            base += used;
+            todo &= ~fit;
+            if (fill == 32) flush();
+        }
+    }
+    if (fill > 0) flush();
+    if (npk & 1) flush();  // an empty packet: every group holds an even number
+    if (!WRITE && lane == 0) a.cnt[g] = (int32_t)npk;
+}
+
+__global__ void k_lev_pk(const int32_t* lev_grp, const int64_t* off, int n, int64_t* lev_pk) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= n) lev_pk[i] = off[lev_grp[i]];
+}
+
+PackArgs pack_args(const DevMesh& m, const Levels& L, const double* om64_all, const float4* om32_all,
+                   const float4* om32lo_all) {
+    PackArgs a;
+    a.trec = L.trec;
+    a.grp = L.pk_grp;
+    a.ng = L.pk_ng;
+    a.rowptr = m.rowptr;
+    a.side = m.side;
+    a.side64 = m.side64;
+    a.side_lo = m.side_lo;
+    a.om32 = om32_all + L.d0;
+    a.om32lo = om32lo_all + L.d0;
+    a.om64 = om64_all + 3 * (int64_t)L.d0;
+    a.cmask = L.cmask;
+    a.cshift = L.cshift;
+    a.N = (uint32_t)m.N;
+    a.cnt = L.pk_cnt;
+    a.flag = L.pk_flag;
+    a.off = L.pk_off;
+    a.pk = L.pk;
+    a.meta = L.pk_meta;
+    return a;
+}
+
+}  // namespace
+
+cudaError_t pack_plan(const DevMesh& m, Levels& L, const double* om64_all, const float4* om32_all,
+                      const float4* om32lo_all, cudaStream_t st, int64_t* n_pk) {
+    // packing groups: runs of up to PK_GROUP_CHUNKS chunks of one level (levels are padded to chunks)
+    const int nlev = L.n_levels;
+    std::vector<int32_t> grp, lev_grp(nlev + 1);
+    for (int l = 0; l < nlev; ++l) {
+        lev_grp[l] = (int32_t)grp.size();
+        for (int64_t c = L.h_lev_chunk[l]; c < L.h_lev_chunk[l + 1]; c += PK_GROUP_CHUNKS) grp.push_back((int32_t)c);
+    }
+    const int64_t ng = (int64_t)grp.size();
+    lev_grp[nlev] = (int32_t)ng;
+    grp.push_back(nlev > 0 ? (int32_t)L.h_lev_chunk[nlev] : 0);
+    grp.insert(grp.end(), lev_grp.begin(), lev_grp.end());
+    const int64_t want = ng + nlev + 2;
+    cudaError_t e;
+    if (want > L.pk_grp_cap || !L.pk_flag) {
+        for (void* p : {(void*)L.pk_grp, (void*)L.pk_cnt, (void*)L.pk_off, (void*)L.pk_scan, (void*)L.lev_pk,
+                        (void*)L.pk_flag})
+            if (p) cudaFree(p);
+        L.pk_grp = nullptr; L.pk_cnt = nullptr; L.pk_off = nullptr; L.pk_scan = nullptr; L.lev_pk = nullptr;
+        L.pk_flag = nullptr;
+        L.pk_grp_cap = 0;
+        const int64_t cap = want + want / 4;
+        if ((e = cudaMalloc(&L.pk_grp, sizeof(int32_t) * cap))) return e;
+        if ((e = cudaMalloc(&L.pk_cnt, sizeof(int32_t) * cap))) return e;
+        if ((e = cudaMalloc(&L.pk_off, sizeof(int64_t) * cap))) return e;
+        if ((e = cudaMalloc(&L.pk_scan, sizeof(int64_t) * (cap / (SCAN_BLOCK * SCAN_ITEMS) + 2)))) return e;
+        if ((e = cudaMalloc(&L.lev_pk, sizeof(int64_t) * cap))) return e;
+        if ((e = cudaMalloc(&L.pk_flag, sizeof(int32_t)))) return e;
+        L.pk_grp_cap = cap;
+    }
+    L.pk_ng = ng;
+    if ((e = cudaMemcpyAsync(L.pk_grp, grp.data(), sizeof(int32_t) * grp.size(), cudaMemcpyHostToDevice, st)))
+        return e;
+    if ((e = cudaMemsetAsync(L.pk_flag, 0, sizeof(int32_t), st))) return e;
+    if (ng > 0) {
+        PackArgs a = pack_args(m, L, om64_all, om32_all, om32lo_all);
+        k_pack<false><<<(unsigned)((ng * 32 + 255) / 256), 256, 0, st>>>(a);
+        if ((e = scan_i32(L.pk_cnt, ng, L.pk_off, L.pk_scan, L.pk_off + ng, st))) return e;
+    } else if ((e = cudaMemsetAsync(L.pk_off, 0, sizeof(int64_t), st))) {
+        return e;
+    }
+    int64_t total = 0;
+    int32_t flag = 0;
+    if ((e = cudaMemcpyAsync(&total, L.pk_off + ng, sizeof total, cudaMemcpyDeviceToHost, st))) return e;
+    if ((e = cudaMemcpyAsync(&flag, L.pk_flag, sizeof flag, cudaMemcpyDeviceToHost, st))) return e;
+    if ((e = cudaStreamSynchronize(st))) return e;
+    *n_pk = flag ? -1 : total;
+    return cudaSuccess;
+}
+
+cudaError_t pack_write(const DevMesh& m, Levels& L, const double* om64_all, const float4* om32_all,
+                       const float4* om32lo_all, cudaStream_t st) {
+    PackArgs a = pack_args(m, L, om64_all, om32_all, om32lo_all);
+    if (L.pk_ng > 0) k_pack<true><<<(unsigned)((L.pk_ng * 32 + 255) / 256), 256, 0, st>>>(a);
+    const int nlev = L.n_levels;
+    k_lev_pk<<<(nlev + 1 + 255) / 256, 256, 0, st>>>(L.pk_grp + L.pk_ng + 1, L.pk_off, nlev, L.lev_pk);
+    return cudaGetLastError();
+}
+
 namespace {
 
 cudaError_t classify(const DevMesh& m, Levels& L, const float4* om32, const float4* om32lo, const double* om64,

@@ -986,6 +986,264 @@ __global__ void __launch_bounds__(256, SWEEP_REC_MINB) k_sweep_op2(SweepArgs a) 
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// FP32 forward sweep over the packed operator (see pack_plan / k_pack): one warp per packet of 32
+// lanes x two entry slots, PK packets per warp step. Every lane decodes its own slots and gathers its
+// upwind values (interior: this sweep's intensities, with the readiness test on the sign bit;
+// periodic: the previous iteration's; boundary: the inflow array) with no branch on the entry kind;
+// a segmented shuffle scan (segments = tasks; 4 steps, a 5th in packets holding a task of more than 16
+// lanes) sums each task's inflow into its head lane, which solves the cell balance
+// (P_c + kappa_t V) I = q + sum |a| I_up and stores it. Only a wait for a value not yet written leaves
+// the straight line.
+// ---------------------------------------------------------------------------------------------
+template <int GC>
+__device__ __forceinline__ void pk_gather(const float* p, bool has, uint64_t pol, float* x) {
+    if constexpr (GC == 4) {
+        const float4 v = has ? ld_relaxed_hint_v4(p, pol) : make_float4(0.f, 0.f, 0.f, 0.f);
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    } else if constexpr (GC == 2) {
+        const float2 v = has ? ld_relaxed_hint_v2(p, pol) : make_float2(0.f, 0.f);
+        x[0] = v.x; x[1] = v.y;
+    } else {
+        x[0] = has ? ld_relaxed_hint(p, pol) : 0.f;
+    }
+}
+
+// one packet's decoded state between the gather and the solve
+template <int GC>
+struct PkLane {
+    int4 s;           // this lane's two slots
+    bool h0, h1;      // slot holds an entry whose source exists
+    bool in0, in1;    // interior entry (readiness tested)
+    bool head;
+    bool lng;         // the packet holds a task of more than 16 lanes
+    int pos;          // rank of this lane within its task
+    float x0[GC], x1[GC];
+    float q[2 * GC];  // head lane: {q, kappa_t V} per group
+};
+
+// source of a slot: this sweep's intensities, the previous iteration's (periodic) or the boundary inflow
+__device__ __forceinline__ const float* pk_base(const SweepArgs& a, int idx, int w) {
+    return w >= 0 ? reinterpret_cast<const float*>(a.I)
+                  : ((uint32_t)idx & PK_BOUNDARY ? reinterpret_cast<const float*>(a.bc)
+                                                 : reinterpret_cast<const float*>(a.Iprev));
+}
+
+template <int GC>
+__device__ __forceinline__ void pk_decode(const SweepArgs& a, const int4 s, const uint2 m, int lane, uint64_t keep,
+                                          PkLane<GC>& t) {
+    t.s = s;
+    t.head = (m.x >> lane) & 1u;
+    t.lng = m.y != 0u;
+    const unsigned hb = m.x & ((1u << lane) - 1u);
+    t.pos = lane - (hb ? 32 - __clz(hb) : 0);
+    t.in0 = s.y >= 0;
+    t.in1 = s.w >= 0 && !t.head;
+    const float* b0 = pk_base(a, s.x, s.y);
+    const float* b1 = pk_base(a, s.z, s.w);
+    t.h0 = ((uint32_t)s.y << 1) != 0u && b0 != nullptr;
+    t.h1 = !t.head && ((uint32_t)s.w << 1) != 0u && b1 != nullptr;
+    pk_gather<GC>(b0 + (size_t)((uint32_t)s.x & ~PK_BOUNDARY) * GC, t.h0, keep, t.x0);
+    pk_gather<GC>(b1 + (size_t)((uint32_t)s.z & ~PK_BOUNDARY) * GC, t.h1, keep, t.x1);
+    if (t.head) {  // the cell's source and kappa_t V, loaded beside the gathers
+        const uint32_t c = (uint32_t)s.z & a.cmask;
+        if constexpr (GC == 1) {
+            const float2 v = reinterpret_cast<const float2*>(a.cm)[c];
+            t.q[0] = v.x; t.q[1] = v.y;
+        } else {
+            const float4* cm = reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(a.cm) + (size_t)c * GC);
+#pragma unroll
+            for (int h = 0; h < GC / 2; ++h) {
+                const float4 v = cm[h];
+                t.q[4 * h] = v.x; t.q[4 * h + 1] = v.y; t.q[4 * h + 2] = v.z; t.q[4 * h + 3] = v.w;
+            }
+        }
+    }
+}
+
+// sign bit of any gathered interior value differs from this sweep's parity: not written yet
+template <int GC>
+__device__ __forceinline__ bool pk_unready(const PkLane<GC>& t, uint32_t par) {
+    bool nr = false;
+#pragma unroll
+    for (int g = 0; g < GC; ++g) {
+        nr |= t.h0 && t.in0 && ((__float_as_uint(t.x0[g]) ^ par) >> 31);
+        nr |= t.h1 && t.in1 && ((__float_as_uint(t.x1[g]) ^ par) >> 31);
+    }
+    return nr;
+}
+
+// Bounded wait until *p carries this sweep's parity (rare; inline, since a call would make the
+// compiler save the step's registers); the magnitude, or -1 after giving up (the error word is then set).
+__device__ __forceinline__ float pk_wait_value(const float* p, uint32_t par, long long budget, int* err) {
+    for (long long n = 0;; ++n) {
+        const uint32_t u = __float_as_uint(ld_relaxed(p));
+        if ((u & 0x80000000u) == par) return __uint_as_float(u & 0x7fffffffu);
+        if (n >= budget || ((n & 63) == 63 && ld_volatile_i32(err) != DEV_OK)) {
+            atomicCAS(err, DEV_OK, DEV_TIMEOUT);
+            return -1.f;
+        }
+        __nanosleep(20);
+    }
+}
+
+template <int GC>
+__device__ __forceinline__ void pk_wait(const SweepArgs& a, PkLane<GC>& t, uint32_t par, bool& fail) {
+    const float* I = reinterpret_cast<const float*>(a.I);
+#pragma unroll
+    for (int g = 0; g < GC; ++g) {
+        if (t.h0 && t.in0 && ((__float_as_uint(t.x0[g]) ^ par) >> 31)) {
+            const float v = pk_wait_value(I + (size_t)(uint32_t)t.s.x * GC + g, par, a.spin_budget, a.err);
+            fail |= v < 0.f;
+            t.x0[g] = fmaxf(v, 0.f);
+        }
+        if (t.h1 && t.in1 && ((__float_as_uint(t.x1[g]) ^ par) >> 31)) {
+            const float v = pk_wait_value(I + (size_t)(uint32_t)t.s.z * GC + g, par, a.spin_budget, a.err);
+            fail |= v < 0.f;
+            t.x1[g] = fmaxf(v, 0.f);
+        }
+    }
+}
+
+// segmented sum over each task's lanes, then the head lane solves and stores the cell
+template <int GC>
+__device__ __forceinline__ void pk_solve(const SweepArgs& a, const PkLane<GC>& t, uint32_t par, uint64_t keep,
+                                         bool fail) {
+    const float w0 = fabsf(__int_as_float(t.s.y)), w1 = fabsf(__int_as_float(t.s.w));
+    float acc[GC];
+#pragma unroll
+    for (int g = 0; g < GC; ++g) acc[g] = fmaf(w1, fabsf(t.x1[g]), w0 * fabsf(t.x0[g]));
+#pragma unroll
+    for (int off = 1; off < 16; off <<= 1) {
+#pragma unroll
+        for (int g = 0; g < GC; ++g) {
+            const float y = __shfl_up_sync(0xffffffffu, acc[g], off);
+            if (t.pos >= off) acc[g] += y;
+        }
+    }
+    if (t.lng) {  // warp-uniform: a task spans more than 16 lanes
+#pragma unroll
+        for (int g = 0; g < GC; ++g) {
+            const float y = __shfl_up_sync(0xffffffffu, acc[g], 16);
+            if (t.pos >= 16) acc[g] += y;
+        }
+    }
+    if (t.head && !fail) {
+        const uint32_t e = (uint32_t)t.s.z;
+        const uint32_t dst = (e >> a.cshift) * (uint32_t)a.N + (e & a.cmask);
+        const float P = __int_as_float(t.s.w);
+        float v[GC];
+#pragma unroll
+        for (int g = 0; g < GC; ++g)
+            v[g] = __uint_as_float(__float_as_uint(__fdividef(t.q[2 * g] + acc[g], P + t.q[2 * g + 1])) ^ par);
+        float* out = reinterpret_cast<float*>(a.I) + (size_t)dst * GC;
+        if constexpr (GC == 4) st_relaxed_hint_v4(out, make_float4(v[0], v[1], v[2], v[3]), keep);
+        else if constexpr (GC == 2) st_relaxed_hint_v2(out, make_float2(v[0], v[1]), keep);
+        else st_relaxed_hint(out, v[0], keep);
+    }
+}
+
+// Steps [k0, k1) of PK packets, warp w taking k0 + w, k0 + w + W, ...; the packets of the next step
+// are loaded one step ahead into registers and those three steps ahead prefetched into L2.
+template <int GC, int PK>
+__device__ __forceinline__ bool pk_steps(const SweepArgs& a, int64_t k0, int64_t k1, int64_t warp, int64_t nwarps) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t pol = policy_evict_first();
+    const uint64_t keep = policy_evict_last();  // intensities: each is read again by ~8 downwind tasks
+    const uint32_t par = a.parity ? 0x80000000u : 0u;
+    const int4 zero = make_int4(0, 0, 0, 0);
+    int64_t k = k0 + warp;
+    int4 cur[PK];
+    uint2 cm_[PK];
+    auto load = [&](int64_t kk, int4* s, uint2* m) {
+        const bool ok = kk < k1;
+#pragma unroll
+        for (int p = 0; p < PK; ++p) {
+            s[p] = ok ? ld_stream_int4(a.pk + (kk * PK + p) * 32 + lane, pol) : zero;
+            m[p] = ok ? __ldg(a.pk_meta + kk * PK + p) : make_uint2(0u, 0u);
+        }
+    };
+    load(k, cur, cm_);
+    if (lane == 0)
+        for (int j = 1; j <= 2; ++j)
+            if (k + j * nwarps < k1)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.pk + (k + j * nwarps) * PK * 32),
+                             "r"(PK * 512u));
+    for (int64_t i = 0; k < k1; ++i, k += nwarps) {
+        if ((i & 15) == 0 && __any_sync(0xffffffffu, ld_volatile_i32(a.err) != DEV_OK)) return false;
+        int4 nxt[PK];
+        uint2 nm[PK];
+        load(k + nwarps, nxt, nm);
+        if (lane == 0 && k + 3 * nwarps < k1)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.pk + (k + 3 * nwarps) * PK * 32),
+                         "r"(PK * 512u));
+        PkLane<GC> t[PK];
+#pragma unroll
+        for (int p = 0; p < PK; ++p) pk_decode<GC>(a, cur[p], cm_[p], lane, keep, t[p]);
+        bool fail = false;
+        bool nr = false;
+#pragma unroll
+        for (int p = 0; p < PK; ++p) nr |= pk_unready<GC>(t[p], par);
+        if (__any_sync(0xffffffffu, nr)) {
+#pragma unroll
+            for (int p = 0; p < PK; ++p) pk_wait<GC>(a, t[p], par, fail);
+        }
+#pragma unroll
+        for (int p = 0; p < PK; ++p) pk_solve<GC>(a, t[p], par, keep, fail);
+#pragma unroll
+        for (int p = 0; p < PK; ++p) {
+            cur[p] = nxt[p];
+            cm_[p] = nm[p];
+        }
+    }
+    return true;
+}
+
+// resident 256-thread blocks per SM the packed kernel is compiled for (64 registers; 3 with four groups
+// and two packets per step, whose state needs more)
+template <int GC, int PK>
+struct PkMinBlocks {
+    static constexpr int value = (GC == 4 && PK == 2) ? 3 : 4;
+};
+
+template <int GC, int PK>
+__global__ void __launch_bounds__(256, (PkMinBlocks<GC, PK>::value)) k_sweep_pk(const __grid_constant__ SweepArgs a) {
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    if (a.debug_stall && warp == 0 && (threadIdx.x & 31) == 0) {  // test hook: a wait on a word nothing writes
+        float dummy;
+        wait_value(reinterpret_cast<const float*>(a.stall_word), 1, a, dummy);
+    }
+    if (a.level_sync) {
+        for (int li = 0; li < a.n_levels; ++li) {
+            pk_steps<GC, PK>(a, a.lev_pk[li] / PK, a.lev_pk[li + 1] / PK, warp, nwarps);
+            if (!grid_sync(a.bar, gridDim.x, a.spin_budget, a.err)) return;
+        }
+    } else {
+        pk_steps<GC, PK>(a, 0, a.n_pk / PK, warp, nwarps);
+    }
+}
+
+template <int PK>
+cudaError_t launch_pk(const SweepArgs& a, const cudaLaunchConfig_t& cfg) {
+    switch (a.G) {
+        case 1: return cudaLaunchKernelEx(&cfg, k_sweep_pk<1, PK>, a);
+        case 2: return cudaLaunchKernelEx(&cfg, k_sweep_pk<2, PK>, a);
+        default: return cudaLaunchKernelEx(&cfg, k_sweep_pk<4, PK>, a);
+    }
+}
+
+template <int PK>
+int occupancy_pk(int G, int threads, size_t smem) {
+    int n = 0;
+    switch (G) {
+        case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_pk<1, PK>, threads, smem); break;
+        case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_pk<2, PK>, threads, smem); break;
+        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_pk<4, PK>, threads, smem); break;
+    }
+    return n;
+}
+
 template <int LP>
 cudaError_t launch_op_lanes(const SweepArgs& a, const cudaLaunchConfig_t& cfg) {
     if (LP == 8 && a.G == 1 && !a.level_sync) return cudaLaunchKernelEx(&cfg, k_sweep_op1, a);
@@ -1120,6 +1378,10 @@ cudaError_t launch_typed(const SweepArgs& a, int blocks, int threads, cudaStream
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (sizeof(real) == 4 && !a.reverse && a.pk) {  // FP32 forward over the packed operator
+        *kid = SWEEP_KERNEL_PACKED;
+        return a.lanes >= 64 ? launch_pk<2>(a, cfg) : launch_pk<1>(a, cfg);
+    }
     if (sizeof(real) == 4 && !a.reverse && a.op) {  // FP32 forward over the assembled operator
         if (a.lanes == 16 && a.G == 1 && !a.level_sync) {
             *kid = SWEEP_KERNEL_OPERATOR_PAIR;
@@ -1159,9 +1421,11 @@ int occupancy_lanes(int G, int threads, size_t smem) {
 
 }  // namespace
 
-int sweep_occupancy(int precision, int G, int threads, int nd, int lanes, int reverse, bool op) {
+int sweep_occupancy(int precision, int G, int threads, int nd, int lanes, int reverse, int fmt) {
     size_t smem = sizeof(float4) * (size_t)nd;
-    if (precision == 32 && !reverse && op) {
+    if (precision == 32 && !reverse && fmt == OPF_PACKETS)
+        return lanes >= 64 ? occupancy_pk<2>(G, threads, smem) : occupancy_pk<1>(G, threads, smem);
+    if (precision == 32 && !reverse && fmt == OPF_LINES) {
         if (lanes == 16 && G == 1) {
             int n = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_op2, threads, smem);
