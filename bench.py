@@ -528,13 +528,15 @@ def run_profile_case(args):
     ctx.set_directions(p.omega, p.weight)
     ctx.set_material(p.kappa_abs, p.emissivity)
     o = default_opts(precision=32, schedule=args.schedule, lanes_per_task=args.lanes,
-                     block_threads=128 if args.lanes == 1 else 256, blocks_per_sm=args.bpsm, max_it_pbc=2, tol_pbc=0.0)
+                     block_threads=128 if args.lanes == 1 else 256, blocks_per_sm=args.bpsm, max_it_pbc=2, tol_pbc=0.0,
+                     op_format=args.op_format, packets_per_step=args.pps)
     ctx.solve(o)  # warm-up: module loading, first-touch of buffers
     J, G, st, s = ctx.solve(o)
     ctx.close()
     print(json.dumps({"profile_case": args.workload, "n_cells": p.mesh.n_cells, "sweeps": st["n_sweeps"],
                       "sweep_ms_per_launch": st["t_sweep_ms"] / max(1, st["n_sweeps"]),
-                      "levelise_ms": st["t_levelise_ms"], "depth_max": st["depth_max"]}))
+                      "levelise_ms": st["t_levelise_ms"], "assemble_ms": st["t_assemble_ms"],
+                      "depth_max": st["depth_max"], "kernel": st["kernel_used"], "lanes": st["lanes_used"]}))
 
 
 def main():
@@ -555,7 +557,10 @@ def main():
                     help="with scattering and periodic faces: one sweep per periodic iteration (Sec. 2.7)")
     ap.add_argument("--profile-case", action="store_true", help="small fixed solve for ncu captures")
     ap.add_argument("--schedule", default="dataflow", choices=["level", "dataflow"])
-    ap.add_argument("--lanes", type=int, default=8, choices=[1, 2, 4, 8, 16])
+    ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4, 8, 16],
+                    help="profiling case: lanes per task over 128-byte lines (0 = the packed operator)")
+    ap.add_argument("--op-format", default="auto", choices=["auto", "lines", "packets"])
+    ap.add_argument("--pps", type=int, default=0, choices=[0, 1, 2], help="packets per warp step (0 = autotuned)")
     ap.add_argument("--bpsm", type=int, default=0, help="resident blocks per SM (profiling case)")
     args = ap.parse_args()
     if args.profile_case:

@@ -249,7 +249,9 @@ sweep_status sweep_adjoint_dev(sweep_ctx* ctx, const sweep_opts* opts, const dou
  * exhausted by another component, where cudaMalloc would fail or stall the device).
  *   device, cuda_stream    the GPU and stream to run on (NULL stream = legacy default stream)
  *   face_cells[n_faces][2], normal[n_faces][3], flags[n_faces]
- *                          DEVICE pointers, the mesh faces as for sweep_set_mesh (not validated)
+ *                          DEVICE pointers, the mesh faces as for sweep_set_mesh (the cell indices of
+ *                          interior faces are checked on the device: INVALID_ARG, nothing out of range
+ *                          is touched; normals and flags are not validated)
  *   omega[3]               HOST pointer, the direction
  *   level[n_cells]         DEVICE output: level of every cell (as sweep_levels)
  *   depth                  HOST output: 1 + the largest level
@@ -257,10 +259,11 @@ sweep_status sweep_adjoint_dev(sweep_ctx* ctx, const sweep_opts* opts, const dou
  * GPU work. The working memory is one static device array (65536 counters plus a control block,
  * 256 KB) that every GPU loading the library holds until exit; every call shares it and clears
  * what must start at zero, so calls whose GPU work overlaps (other host threads, other streams)
- * race and give wrong results. The first call on a device looks up the array's device address
- * (a one-time set-up); make that first call before any stream capture. The call returns after
- * the result is on the device (it synchronizes the stream). Errors: INVALID_ARG (sizes, null
- * pointers, device), CYCLE, TIMEOUT (a bounded wait gave up), CUDA. */
+ * race and give wrong results. Every call looks up the array's device address (the first call on a
+ * device also loads the library's device code there, a one-time set-up; make that first call before
+ * any stream capture); the lookup allocates nothing. The call returns after the result is on the
+ * device (it synchronizes the stream). Errors: INVALID_ARG (sizes, null pointers, device, a face
+ * cell index outside [0, n_cells)), CYCLE, TIMEOUT (a bounded wait gave up), CUDA. */
 sweep_status sweep_levels_noalloc(int device, void* cuda_stream, int64_t n_cells, int64_t n_faces,
                                   const int32_t* face_cells, const double* normal, const uint8_t* flags,
                                   const double* omega, int32_t* level, int32_t* depth);

@@ -115,6 +115,59 @@ __device__ __forceinline__ void st_relaxed_hint_v4(float* p, float4 v, uint64_t 
     asm volatile("st.relaxed.gpu.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x),
                  "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol));
 }
+// Predicated forms (the access is issued only where `on` is set; a load leaves 0 elsewhere): one
+// predicated instruction instead of a branch around an asm statement, so lanes of a warp that skip
+// the access do not diverge.
+__device__ __forceinline__ float ld_relaxed_hint_if(const float* p, uint64_t pol, bool on) {
+    float v = 0.f;
+    asm volatile("{ .reg .pred q; setp.ne.u32 q, %3, 0; @q ld.relaxed.gpu.global.L2::cache_hint.f32 %0, [%1], %2; }"
+                 : "+f"(v) : "l"(p), "l"(pol), "r"((unsigned)on));
+    return v;
+}
+__device__ __forceinline__ float2 ld_relaxed_hint_v2_if(const float* p, uint64_t pol, bool on) {
+    float2 v = make_float2(0.f, 0.f);
+    asm volatile("{ .reg .pred q; setp.ne.u32 q, %4, 0; @q ld.relaxed.gpu.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3; }"
+                 : "+f"(v.x), "+f"(v.y) : "l"(p), "l"(pol), "r"((unsigned)on));
+    return v;
+}
+__device__ __forceinline__ float4 ld_relaxed_hint_v4_if(const float* p, uint64_t pol, bool on) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    asm volatile("{ .reg .pred q; setp.ne.u32 q, %6, 0; @q ld.relaxed.gpu.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5; }"
+                 : "+f"(v.x), "+f"(v.y), "+f"(v.z), "+f"(v.w) : "l"(p), "l"(pol), "r"((unsigned)on));
+    return v;
+}
+// predicated re-read that keeps the previous value where `on` is clear
+__device__ __forceinline__ float ld_relaxed_keep_if(const float* p, bool on, float old) {
+    float v = old;
+    asm volatile("{ .reg .pred q; setp.ne.u32 q, %2, 0; @q ld.relaxed.gpu.global.f32 %0, [%1]; }"
+                 : "+f"(v) : "l"(p), "r"((unsigned)on));
+    return v;
+}
+// read-only data of the launch (not written by the kernel itself)
+__device__ __forceinline__ float4 ld_nc_v4_if(const void* p, bool on) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    asm volatile("{ .reg .pred q; setp.ne.u32 q, %5, 0; @q ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4]; }"
+                 : "+f"(v.x), "+f"(v.y), "+f"(v.z), "+f"(v.w) : "l"(p), "r"((unsigned)on));
+    return v;
+}
+__device__ __forceinline__ float2 ld_nc_v2_if(const void* p, bool on) {
+    float2 v = make_float2(0.f, 0.f);
+    asm volatile("{ .reg .pred q; setp.ne.u32 q, %3, 0; @q ld.global.nc.v2.f32 {%0, %1}, [%2]; }"
+                 : "+f"(v.x), "+f"(v.y) : "l"(p), "r"((unsigned)on));
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_hint_if(float* p, float v, uint64_t pol, bool on) {
+    asm volatile("{ .reg .pred q; setp.ne.u32 q, %3, 0; @q st.relaxed.gpu.global.L2::cache_hint.f32 [%0], %1, %2; }"
+                 ::"l"(p), "f"(v), "l"(pol), "r"((unsigned)on));
+}
+__device__ __forceinline__ void st_relaxed_hint_v2_if(float* p, float2 v, uint64_t pol, bool on) {
+    asm volatile("{ .reg .pred q; setp.ne.u32 q, %4, 0; @q st.relaxed.gpu.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3; }"
+                 ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol), "r"((unsigned)on));
+}
+__device__ __forceinline__ void st_relaxed_hint_v4_if(float* p, float4 v, uint64_t pol, bool on) {
+    asm volatile("{ .reg .pred q; setp.ne.u32 q, %6, 0; @q st.relaxed.gpu.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5; }"
+                 ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol), "r"((unsigned)on));
+}
 __device__ __forceinline__ void st_relaxed(float* p, float v) {
     asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v));
 }

@@ -7,8 +7,6 @@
 // buffers and keeps its working memory (upwind counters and a small control block) in one
 // file-scope device array, reserved when the library's module is loaded and held by every GPU that
 // loads it until the process exits.
-#include <mutex>
-
 #include "common.cuh"
 
 namespace {
@@ -22,9 +20,8 @@ constexpr int NOALLOC_CTRL_WORDS = 16;
 //   (one per level modulo 3), +7 cells never reached
 static __device__ __align__(256) int32_t g_noalloc_scratch[NOALLOC_MAX_CELLS + NOALLOC_CTRL_WORDS];
 
-constexpr int MAX_DEVICES = 64;
-int32_t* g_scratch_ptr[MAX_DEVICES];  // device address of the scratch array, per device
-std::mutex g_scratch_mu;
+// error word value of a face whose cell index is outside [0, n_cells) (after sw::DEV_TIMEOUT, DEV_OVERFLOW)
+constexpr int DEV_BAD_INDEX = 3;
 
 // Classification value t = ((nx*Ox) + (ny*Oy)) + (nz*Oz) with separately rounded products and sums.
 __device__ __forceinline__ double face_t(const double* n, double ox, double oy, double oz) {
@@ -47,10 +44,16 @@ __global__ void k_levels_noalloc(int64_t N, int64_t F, const int32_t* fc, const 
     if (!sw::grid_sync(bar, gridDim.x, budget, err)) return;
     for (int64_t f = tid; f < F; f += nth) {
         if (flags[f] & (SWEEP_FACE_BOUNDARY | SWEEP_FACE_PERIODIC)) continue;
+        const int32_t c0 = fc[2 * f], c1 = fc[2 * f + 1];
+        if (c0 < 0 || c0 >= N || c1 < 0 || c1 >= N) {  // the faces are not validated: refuse, touch nothing
+            atomicCAS(err, sw::DEV_OK, DEV_BAD_INDEX);
+            continue;
+        }
         const double t = face_t(normal + 3 * f, ox, oy, oz);
-        if (t > 0.0) atomicAdd(&count[fc[2 * f + 1]], 1);
-        else if (t < 0.0) atomicAdd(&count[fc[2 * f]], 1);
+        if (t > 0.0) atomicAdd(&count[c1], 1);
+        else if (t < 0.0) atomicAdd(&count[c0], 1);
     }
+    // every face the wavefront rounds read was checked above; a bad one ends the launch here
     if (!sw::grid_sync(bar, gridDim.x, budget, err)) return;
     for (int64_t c = tid; c < N; c += nth) level[c] = count[c] == 0 ? 0 : -1;
     if (!sw::grid_sync(bar, gridDim.x, budget, err)) return;
@@ -84,7 +87,7 @@ extern "C" sweep_status sweep_levels_noalloc(int device, void* cuda_stream, int6
                                              const double* omega, int32_t* level, int32_t* depth) {
     if (n_cells < 1 || n_cells > NOALLOC_MAX_CELLS || n_faces < 0) return SWEEP_ERR_INVALID_ARG;
     if (!omega || !level || !depth || (n_faces > 0 && (!face_cells || !normal || !flags))) return SWEEP_ERR_INVALID_ARG;
-    if (device < 0 || device >= MAX_DEVICES) return SWEEP_ERR_INVALID_ARG;
+    if (device < 0) return SWEEP_ERR_INVALID_ARG;
     int prev = 0;
     if (cudaGetDevice(&prev) != cudaSuccess) return SWEEP_ERR_CUDA;
     if (cudaSetDevice(device) != cudaSuccess) {
@@ -93,22 +96,17 @@ extern "C" sweep_status sweep_levels_noalloc(int device, void* cuda_stream, int6
     }
     sweep_status rc = SWEEP_OK;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    int32_t* scratch = nullptr;
-    {
-        // first call on this device: look up the device address of the scratch array (the name
-        // itself is only a host-side stand-in)
-        std::lock_guard<std::mutex> lock(g_scratch_mu);
-        if (!g_scratch_ptr[device]) {
-            void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-                cudaGetLastError();
-                cudaSetDevice(prev);
-                return SWEEP_ERR_CUDA;
-            }
-            g_scratch_ptr[device] = static_cast<int32_t*>(p);
-        }
-        scratch = g_scratch_ptr[device];
+    // The device address of the scratch array on this device (its name is only a host-side stand-in).
+    // The first call on a device loads the library's device code and looks the address up; later calls
+    // look it up again, which allocates nothing and is cheap, so that the address stays right if the
+    // device's primary context was destroyed and created again (cudaDeviceReset) in between.
+    void* sp = nullptr;
+    if (cudaGetSymbolAddress(&sp, g_noalloc_scratch) != cudaSuccess || !sp) {
+        cudaGetLastError();
+        cudaSetDevice(prev);
+        return SWEEP_ERR_CUDA;
     }
+    int32_t* scratch = static_cast<int32_t*>(sp);
     int32_t* ctrl = scratch + NOALLOC_MAX_CELLS;
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
@@ -137,6 +135,8 @@ extern "C" sweep_status sweep_levels_noalloc(int device, void* cuda_stream, int6
     if (e != cudaSuccess) {
         cudaGetLastError();
         rc = SWEEP_ERR_CUDA;
+    } else if (h[2] == DEV_BAD_INDEX) {
+        rc = SWEEP_ERR_INVALID_ARG;
     } else if (h[2] != sw::DEV_OK) {
         rc = SWEEP_ERR_TIMEOUT;
     } else if (h[7] > 0) {

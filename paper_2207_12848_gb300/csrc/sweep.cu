@@ -999,13 +999,13 @@ __global__ void __launch_bounds__(256, SWEEP_REC_MINB) k_sweep_op2(SweepArgs a) 
 template <int GC>
 __device__ __forceinline__ void pk_gather(const float* p, bool has, uint64_t pol, float* x) {
     if constexpr (GC == 4) {
-        const float4 v = has ? ld_relaxed_hint_v4(p, pol) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 v = ld_relaxed_hint_v4_if(p, pol, has);
         x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
     } else if constexpr (GC == 2) {
-        const float2 v = has ? ld_relaxed_hint_v2(p, pol) : make_float2(0.f, 0.f);
+        const float2 v = ld_relaxed_hint_v2_if(p, pol, has);
         x[0] = v.x; x[1] = v.y;
     } else {
-        x[0] = has ? ld_relaxed_hint(p, pol) : 0.f;
+        x[0] = ld_relaxed_hint_if(p, pol, has);
     }
 }
 
@@ -1045,18 +1045,16 @@ __device__ __forceinline__ void pk_decode(const SweepArgs& a, const int4 s, cons
     t.h1 = !t.head && ((uint32_t)s.w << 1) != 0u && b1 != nullptr;
     pk_gather<GC>(b0 + (size_t)((uint32_t)s.x & ~PK_BOUNDARY) * GC, t.h0, keep, t.x0);
     pk_gather<GC>(b1 + (size_t)((uint32_t)s.z & ~PK_BOUNDARY) * GC, t.h1, keep, t.x1);
-    if (t.head) {  // the cell's source and kappa_t V, loaded beside the gathers
-        const uint32_t c = (uint32_t)s.z & a.cmask;
-        if constexpr (GC == 1) {
-            const float2 v = reinterpret_cast<const float2*>(a.cm)[c];
-            t.q[0] = v.x; t.q[1] = v.y;
-        } else {
-            const float4* cm = reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(a.cm) + (size_t)c * GC);
+    // the cell's source and kappa_t V (head lanes), loaded beside the gathers
+    const float2* cm = reinterpret_cast<const float2*>(a.cm) + (size_t)((uint32_t)s.z & a.cmask) * GC;
+    if constexpr (GC == 1) {
+        const float2 v = ld_nc_v2_if(cm, t.head);
+        t.q[0] = v.x; t.q[1] = v.y;
+    } else {
 #pragma unroll
-            for (int h = 0; h < GC / 2; ++h) {
-                const float4 v = cm[h];
-                t.q[4 * h] = v.x; t.q[4 * h + 1] = v.y; t.q[4 * h + 2] = v.z; t.q[4 * h + 3] = v.w;
-            }
+        for (int h = 0; h < GC / 2; ++h) {
+            const float4 v = ld_nc_v4_if(cm + 2 * h, t.head);
+            t.q[4 * h] = v.x; t.q[4 * h + 1] = v.y; t.q[4 * h + 2] = v.z; t.q[4 * h + 3] = v.w;
         }
     }
 }
@@ -1073,35 +1071,34 @@ __device__ __forceinline__ bool pk_unready(const PkLane<GC>& t, uint32_t par) {
     return nr;
 }
 
-// Bounded wait until *p carries this sweep's parity (rare; inline, since a call would make the
-// compiler save the step's registers); the magnitude, or -1 after giving up (the error word is then set).
-__device__ __forceinline__ float pk_wait_value(const float* p, uint32_t par, long long budget, int* err) {
+// The step's gathered interior values not yet written by this sweep: all of them are re-read together,
+// one round trip per poll, until every one carries this sweep's parity (a serial wait per value would
+// cost a round trip per value after its producer finished). Bounded: after spin_budget polls, or when
+// another warp has set the device error word, the step gives up and the error word is set.
+template <int GC, int PK>
+__device__ __forceinline__ void pk_wait_all(const SweepArgs& a, PkLane<GC> (&t)[PK], uint32_t par, bool& fail) {
+    const float* I = reinterpret_cast<const float*>(a.I);
     for (long long n = 0;; ++n) {
-        const uint32_t u = __float_as_uint(ld_relaxed(p));
-        if ((u & 0x80000000u) == par) return __uint_as_float(u & 0x7fffffffu);
-        if (n >= budget || ((n & 63) == 63 && ld_volatile_i32(err) != DEV_OK)) {
-            atomicCAS(err, DEV_OK, DEV_TIMEOUT);
-            return -1.f;
+        bool nr = false;
+#pragma unroll
+        for (int p = 0; p < PK; ++p) {
+#pragma unroll
+            for (int g = 0; g < GC; ++g) {
+                const bool u0 = t[p].h0 && t[p].in0 && ((__float_as_uint(t[p].x0[g]) ^ par) >> 31);
+                const bool u1 = t[p].h1 && t[p].in1 && ((__float_as_uint(t[p].x1[g]) ^ par) >> 31);
+                t[p].x0[g] = ld_relaxed_keep_if(I + (size_t)(uint32_t)t[p].s.x * GC + g, u0, t[p].x0[g]);
+                t[p].x1[g] = ld_relaxed_keep_if(I + (size_t)(uint32_t)t[p].s.z * GC + g, u1, t[p].x1[g]);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < PK; ++p) nr |= pk_unready<GC>(t[p], par);
+        if (!__any_sync(0xffffffffu, nr)) return;
+        if (n >= a.spin_budget || ((n & 63) == 63 && ld_volatile_i32(a.err) != DEV_OK)) {
+            atomicCAS(a.err, DEV_OK, DEV_TIMEOUT);
+            fail = true;
+            return;
         }
         __nanosleep(20);
-    }
-}
-
-template <int GC>
-__device__ __forceinline__ void pk_wait(const SweepArgs& a, PkLane<GC>& t, uint32_t par, bool& fail) {
-    const float* I = reinterpret_cast<const float*>(a.I);
-#pragma unroll
-    for (int g = 0; g < GC; ++g) {
-        if (t.h0 && t.in0 && ((__float_as_uint(t.x0[g]) ^ par) >> 31)) {
-            const float v = pk_wait_value(I + (size_t)(uint32_t)t.s.x * GC + g, par, a.spin_budget, a.err);
-            fail |= v < 0.f;
-            t.x0[g] = fmaxf(v, 0.f);
-        }
-        if (t.h1 && t.in1 && ((__float_as_uint(t.x1[g]) ^ par) >> 31)) {
-            const float v = pk_wait_value(I + (size_t)(uint32_t)t.s.z * GC + g, par, a.spin_budget, a.err);
-            fail |= v < 0.f;
-            t.x1[g] = fmaxf(v, 0.f);
-        }
     }
 }
 
@@ -1128,19 +1125,19 @@ __device__ __forceinline__ void pk_solve(const SweepArgs& a, const PkLane<GC>& t
             if (t.pos >= 16) acc[g] += y;
         }
     }
-    if (t.head && !fail) {
-        const uint32_t e = (uint32_t)t.s.z;
-        const uint32_t dst = (e >> a.cshift) * (uint32_t)a.N + (e & a.cmask);
-        const float P = __int_as_float(t.s.w);
-        float v[GC];
+    // head lanes solve and store their cell (predicated: no branch, the other lanes skip the store)
+    const bool on = t.head && !fail;
+    const uint32_t e = (uint32_t)t.s.z;
+    const uint32_t dst = (e >> a.cshift) * (uint32_t)a.N + (e & a.cmask);
+    const float P = __int_as_float(t.s.w);
+    float v[GC];
 #pragma unroll
-        for (int g = 0; g < GC; ++g)
-            v[g] = __uint_as_float(__float_as_uint(__fdividef(t.q[2 * g] + acc[g], P + t.q[2 * g + 1])) ^ par);
-        float* out = reinterpret_cast<float*>(a.I) + (size_t)dst * GC;
-        if constexpr (GC == 4) st_relaxed_hint_v4(out, make_float4(v[0], v[1], v[2], v[3]), keep);
-        else if constexpr (GC == 2) st_relaxed_hint_v2(out, make_float2(v[0], v[1]), keep);
-        else st_relaxed_hint(out, v[0], keep);
-    }
+    for (int g = 0; g < GC; ++g)
+        v[g] = __uint_as_float(__float_as_uint(__fdividef(t.q[2 * g] + acc[g], P + t.q[2 * g + 1])) ^ par);
+    float* out = reinterpret_cast<float*>(a.I) + (size_t)dst * GC;
+    if constexpr (GC == 4) st_relaxed_hint_v4_if(out, make_float4(v[0], v[1], v[2], v[3]), keep, on);
+    else if constexpr (GC == 2) st_relaxed_hint_v2_if(out, make_float2(v[0], v[1]), keep, on);
+    else st_relaxed_hint_if(out, v[0], keep, on);
 }
 
 // Steps [k0, k1) of PK packets, warp w taking k0 + w, k0 + w + W, ...; the packets of the next step
@@ -1184,10 +1181,7 @@ __device__ __forceinline__ bool pk_steps(const SweepArgs& a, int64_t k0, int64_t
         bool nr = false;
 #pragma unroll
         for (int p = 0; p < PK; ++p) nr |= pk_unready<GC>(t[p], par);
-        if (__any_sync(0xffffffffu, nr)) {
-#pragma unroll
-            for (int p = 0; p < PK; ++p) pk_wait<GC>(a, t[p], par, fail);
-        }
+        if (__any_sync(0xffffffffu, nr)) pk_wait_all<GC, PK>(a, t, par, fail);
 #pragma unroll
         for (int p = 0; p < PK; ++p) pk_solve<GC>(a, t[p], par, keep, fail);
 #pragma unroll

@@ -11,7 +11,7 @@ import pytest
 
 from synth import configs
 from synth.fields import fibonacci_directions
-from synth.mesh import lattice_mesh
+from synth.mesh import column_mesh, lattice_mesh
 
 pytestmark = pytest.mark.gpu
 
@@ -62,3 +62,31 @@ def test_noalloc_rejects_meshes_over_the_limit(gpu_lib):
     # sizes are checked before any GPU work; the pointers are never touched
     st = gpu_lib.sweep_levels_noalloc(0, None, MAX_CELLS + 1, 10, 8, 8, 8, om.ctypes.data, 8, ctypes.byref(depth))
     assert st == 1
+
+
+def test_noalloc_reports_a_cycle(gpu_lib):
+    # a column whose last cell is joined back to its first by an interior face: along +x every cell
+    # waits on the one before it, so no cell is ever ready; the count of cells never reached reports it
+    torch = pytest.importorskip("torch")
+    m = column_mesh(8, periodic_x=True)
+    m.flags = m.flags & ~np.uint8(2)  # the wrap-around face becomes an ordinary interior face
+    st, lev, depth = _noalloc_levels(gpu_lib, torch, m, np.array([1.0, 0.0, 0.0]), 0)
+    assert st == 2
+
+
+def test_noalloc_rejects_an_out_of_range_cell_index(gpu_lib):
+    # an interior face naming cell n_cells + 1: the device-side check refuses it before any counter is
+    # touched, and the next call on good input is unaffected
+    torch = pytest.importorskip("torch")
+    p = configs.voronoi_small(2000, n_dir=1, seed=78)
+    m = p.mesh
+    bad = m.face_cells.copy()
+    inner = np.flatnonzero(m.face_cells[:, 1] >= 0)
+    bad[inner[len(inner) // 2], 1] = m.n_cells + 1
+    good_fc = m.face_cells
+    m.face_cells = bad
+    st, _, _ = _noalloc_levels(gpu_lib, torch, m, p.omega[0], 0)
+    assert st == 1
+    m.face_cells = good_fc
+    st, lev, depth = _noalloc_levels(gpu_lib, torch, m, p.omega[0], 0)
+    assert st == 0 and depth > 0 and lev.min() == 0
