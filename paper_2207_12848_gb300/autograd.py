@@ -4,9 +4,9 @@ Forward runs ``sweep_solve_dev`` (the batched sweep of every direction, Sec. 2.3
 ``sweep_adjoint_dev``: the transposed sweep in reversed level order, whose solution gives the
 gradients of a loss L(J, Gamma) with respect to the absorption coefficient, the emissivity and, with
 isotropic scattering, the scattering coefficient of every cell. With scattering the forward solve
-is the source iteration of Alg. 1 and the backward pass its transpose (the adjoint covers problems
-without periodic faces). Both directions run in the CUDA library; this module only passes device
-pointers.
+is the source iteration of Alg. 1, with periodic faces the periodic iteration of Sec. 2.7 (or both),
+and the backward pass is the transpose of that coupled system. Both directions run in the CUDA
+library; this module only passes device pointers.
 """
 from __future__ import annotations
 

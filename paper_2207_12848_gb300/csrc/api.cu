@@ -67,6 +67,9 @@ struct sweep_ctx {
     void* adjI = nullptr;
     void* adjL = nullptr;
     size_t adj_bytes_I = 0, adj_bytes_L = 0;
+    // the boundary inflow in FP32 for the FP32 sweeps, converted once per material
+    float* bc32 = nullptr;
+    bool bc32_ready = false;
     // EXP law: cell-mean intensities of the last sweep, [nd][N][G] in the solve precision
     void* Imean = nullptr;
     size_t imean_bytes = 0;
@@ -133,7 +136,8 @@ void free_solution(sweep_ctx* c) {
 }
 
 void free_material(sweep_ctx* c) {
-    dfree(c->ka); dfree(c->ks); dfree(c->em); dfree(c->bc);
+    dfree(c->ka); dfree(c->ks); dfree(c->em); dfree(c->bc); dfree(c->bc32);
+    c->bc32_ready = false;
     c->has_mat = false;
     c->has_scat = false;
 }
@@ -1040,11 +1044,21 @@ struct DevBuf {
         if (p) cudaFree(p);
     }
 };
-using Bc32 = DevBuf<float>;
-
 __global__ void k_bc_to_f32(const double* in, int64_t n, float* out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = (float)in[i];
+}
+
+// the FP32 copy of the boundary inflow, kept in the context from the first FP32 solve after set_material
+sweep_status ensure_bc32(sweep_ctx* c) {
+    if (c->bc32_ready) return SWEEP_OK;
+    const int64_t n = c->mesh.NB * c->G;
+    if (!c->bc32) CK(cudaMalloc(&c->bc32, sizeof(float) * (n > 0 ? n : 1)), "alloc boundary inflow");
+    k_bc_to_f32<<<nblocks256(n), 256, 0, c->st>>>(c->bc, n, c->bc32);
+    ++c->launches;
+    CK(cudaGetLastError(), "boundary inflow");
+    c->bc32_ready = true;
+    return SWEEP_OK;
 }
 
 sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, double* Gam_out, bool dev,
@@ -1099,12 +1113,11 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     if (c->mesh.n_bcells > npart) npart = c->mesh.n_bcells;
     s = ensure_partial(c, (int)npart);
     if (s != SWEEP_OK) return s;
-    Bc32 bc32;
+    const float* bc32 = nullptr;
     if (prec == 32 && c->bc) {
-        int64_t n = c->mesh.NB * G;
-        CK(cudaMalloc(&bc32.p, sizeof(float) * n), "alloc");
-        k_bc_to_f32<<<nblocks256(n), 256, 0, c->st>>>(c->bc, n, bc32.p);
-        ++c->launches;
+        s = ensure_bc32(c);
+        if (s != SWEEP_OK) return s;
+        bc32 = c->bc32;
     }
     SolveBuf& b = c->sb;
     const void* cm = prec == 64 ? (const void*)c->cm64 : (const void*)c->cm32;
@@ -1117,7 +1130,7 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
         CKL(launch_prep_material(N, G, c->mesh.vol, c->ka, c->ks, c->em, nullptr, prec == 32 ? c->cm32 : nullptr,
                                 prec == 64 ? c->cm64 : nullptr, c->st), "prep");
         LaunchCfg best;
-        s = autotune(c, prec, cm, bc32.p, &o, &best);
+        s = autotune(c, prec, cm, bc32, &o, &best);
         sched = best.sched;
         const int tt = best.threads, tl = best.lanes;
         if (!o.blocks_per_sm) bpsm = best.bpsm;
@@ -1177,7 +1190,7 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
         ls.prev = prev;
         ls.conv_pbc = conv_pbc;
         ls.conv_scat = conv_scat;
-        s = graph_loop(c, o, prec, cm, bc32.p, sched, threads, lanes, bpsm, nblk, ls, &graphed);
+        s = graph_loop(c, o, prec, cm, bc32, sched, threads, lanes, bpsm, nblk, ls, &graphed);
         if (s != SWEEP_OK) return s;
         if (graphed) {
             cur = ls.cur;
@@ -1204,7 +1217,7 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
             const int parity = !b.sign[cur];
             SweepArgs a = make_args(c, c->lev, prec, cm, b.I[cur], has_pbc ? b.I[prev] : nullptr, G, parity, 0, 0, &o);
             a.debug_stall = o.debug_stall && n_sweeps == 0;
-            s = run_sweep(c, c->lev, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, lanes, bpsm, a, bc32.p,
+            s = run_sweep(c, c->lev, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, lanes, bpsm, a, bc32,
                           &t_sweep);
             if (s != SWEEP_OK) return s;
             b.sign[cur] = parity;
@@ -1285,7 +1298,7 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     S.injected = hr[3];
     double in = S.emitted + S.injected;
     S.defect = in > 0.0 ? (in - S.absorbed - S.escaped) / in : 0.0;
-    S.it_scat = it_scat_total;
+    S.it_scat = c->has_scat ? it_scat_total : 0;  // sweeps of the source iteration (none without scattering)
     S.it_pbc = it_pbc;
     S.n_sweeps = n_sweeps;
     S.kernel_used = c->last_kernel;
@@ -1402,12 +1415,11 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
     }
     void* lbuf[2] = {c->adjL, b_lam2.p};
     int signI = 0, signL[2] = {0, 0}, kl = 0;
-    Bc32 bc32;
+    const float* bc32 = nullptr;
     if (prec == 32 && c->bc) {
-        int64_t n = c->mesh.NB * G;
-        CK(cudaMalloc(&bc32.p, sizeof(float) * n), "alloc");
-        k_bc_to_f32<<<nblocks256(n), 256, 0, c->st>>>(c->bc, n, bc32.p);
-        ++c->launches;
+        sweep_status sb = ensure_bc32(c);
+        if (sb != SWEEP_OK) return sb;
+        bc32 = c->bc32;
     }
     float t_sweep = 0.f, tcl = 0.f, tlv = 0.f;
     int n_sweeps = it_fwd, it_adj = 0;
@@ -1439,7 +1451,7 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
             int pI = !signI;
             SweepArgs a = make_args(c, *L, prec, cm, c->adjI, nullptr, G, pI, 0, 0, &o);
             a.debug_stall = 0;
-            s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, lanes, 0, a, bc32.p, &t_sweep);
+            s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, lanes, 0, a, bc32, &t_sweep);
             if (s != SWEEP_OK) return s;
             signI = pI;
             ++n_sweeps;

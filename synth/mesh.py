@@ -267,7 +267,7 @@ def voronoi_mesh(points: np.ndarray, periodic: bool = False, threads: int | None
         nfaces[todo[ok]] = sub_nf[ok]
         status[todo] = sub_st
         if np.any(sub_st == 3):
-            margin = min(0.5, 2.0 * margin)
+            margin = min(1.0, 2.0 * margin)  # up to a full periodic image of the box in every shell
         todo = todo[~ok]
         k *= 3
     if todo.size:

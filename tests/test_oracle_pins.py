@@ -646,8 +646,7 @@ def test_dc_with_the_exp_law(box, albedo):
     assert abs(r["stats"]["defect"]) <= 1e-12
 
 
-# (small periodic boxes only for seeds whose tessellation closes)
-@pytest.mark.parametrize("seed,box", [(s, False) for s in range(61, 73)] + [(s, True) for s in (52, 56, 62, 67, 71)])
+@pytest.mark.parametrize("seed,box", [(s, False) for s in range(61, 73)] + [(s, True) for s in range(61, 67)])
 def test_every_option_against_its_dense_solve(seed, box):
     # several small meshes, every combination of law, transport scheme and scattering, against the
     # dense solve of the same system; conservation throughout
