@@ -311,7 +311,7 @@ def run_ours(args, dist: Dist):
     J = torch.empty((N, G), dtype=torch.float64, device="cuda")
     Gm = torch.empty_like(J)
     opts = default_opts(precision=32, relevel=1, tol_pbc=1e-6, max_it_pbc=200, tol_scat=1e-6, max_it_scat=200,
-                        fused_loops=args.fused_loops, law=args.law)
+                        fused_loops=args.fused_loops, law=args.law, transport=args.transport)
     for _ in range(args.warmup):
         ctx.solve_dev(J, Gm, opts)
     torch.cuda.synchronize()
@@ -324,6 +324,7 @@ def run_ours(args, dist: Dist):
     dist.barrier()
     ev0.record(stream)
     agg = {"updates": 0.0, "sweep_ms": 0.0, "sweeps": 0, "launches": 0, "classify_ms": 0.0, "levelise_ms": 0.0,
+           "assemble_ms": 0.0,
            "it_pbc": [], "it_scat": [], "defect": [], "res_pbc": []}
     for _ in range(args.steps):
         st, s = ctx.solve_dev(J, Gm, opts)
@@ -333,6 +334,7 @@ def run_ours(args, dist: Dist):
         agg["launches"] += st["kernel_launches"]
         agg["classify_ms"] += st["t_classify_ms"]
         agg["levelise_ms"] += st["t_levelise_ms"]
+        agg["assemble_ms"] += st["t_assemble_ms"]
         agg["it_pbc"].append(st["it_pbc"])
         agg["it_scat"].append(st["it_scat"])
         agg["defect"].append(st["defect"])
@@ -392,7 +394,7 @@ def run_ours(args, dist: Dist):
         d2h = 2 * N * G * 8
         ctx2 = Context(dist.local, stream.cuda_stream)
         o = default_opts(precision=32, tol_pbc=1e-6, max_it_pbc=200, tol_scat=1e-6, max_it_scat=200,
-                         fused_loops=args.fused_loops, law=args.law)
+                         fused_loops=args.fused_loops, law=args.law, transport=args.transport)
 
         def e2e_step():
             ctx2.set_mesh(volume=hv, face_cells=hfc, area=har, normal=hnr, flags=hfl)
@@ -429,7 +431,8 @@ def run_ours(args, dist: Dist):
                           "face_sides_per_cell": round(fbar, 3), "precision": "FP32 intensities, FP64 tallies",
                           "l2": "no flush: >10 GB resident working set, 78x the 129 MB L2",
                           "step": step_text(p, args.fused_loops), "fused_loops": args.fused_loops,
-                          "law": args.law,
+                          "law": args.law, "transport": "scheme (a)" if args.transport == 0 else
+                          "scheme (b), direction-conserving to %d neighbours" % args.transport,
                           "parallelism": "one independent box per GPU" if dist.world > 1 else "1 GPU"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": agg["launches"],
                "clocks": clk,
@@ -437,6 +440,7 @@ def run_ours(args, dist: Dist):
                          "res_pbc": max(agg["res_pbc"]), "depth_max": last["depth_max"],
                          "depth_mean": last["depth_mean"], "classify_ms": agg["classify_ms"] / args.steps,
                          "levelise_ms": agg["levelise_ms"] / args.steps,
+                         "assemble_ms": agg["assemble_ms"] / args.steps,
                          "sweep_ms_per_launch": avg_launch_s * 1e3,
                          "schedule": {1: "level", 2: "dataflow"}.get(last["schedule_used"], last["schedule_used"]),
                          "lanes_per_task": last["lanes_used"], "threads_per_block": last["threads_used"],
@@ -553,6 +557,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the plain-FP64 comparison sweep")
     ap.add_argument("--law", default="balance", choices=["balance", "exp"],
                     help="absorption law of the cell update (exp: transmission exp(-tau) across the mean chord)")
+    ap.add_argument("--transport", type=int, default=0, choices=range(0, 9),
+                    help="transport scheme of Sec. 2.6: 0 = (a); n = (b), direction-conserving to n neighbours")
     ap.add_argument("--fused-loops", type=int, default=0, choices=[0, 1],
                     help="with scattering and periodic faces: one sweep per periodic iteration (Sec. 2.7)")
     ap.add_argument("--profile-case", action="store_true", help="small fixed solve for ncu captures")

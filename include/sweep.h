@@ -100,6 +100,14 @@ typedef struct {
                                Ignored unless both loops are on. */
     int32_t op_format;      /* SWEEP_OP_*: form of the assembled operator of the FP32 forward sweep */
     int32_t packets_per_step; /* packed operator: packets a warp takes per step, 1 or 2 (0 = autotuned) */
+    int32_t transport;      /* transport scheme of Sec. 2.6: 0 = scheme (a), the outflow split over all outflow faces
+                               in proportion to A_f n_f.Omega; n in 1..8 = scheme (b), direction-conserving transport:
+                               each cell hands its outflow P_c I_c in equal parts to the n outflow faces whose outward
+                               normal is most nearly along Omega (largest n.Omega in FP64, ties to the lower face
+                               index), or to all its outflow faces if it has fewer; the dependency graph keeps only
+                               those faces. Boundary inflow enters as in scheme (a); a chosen vacuum face lets its
+                               part escape, a chosen periodic face passes it to the partner. Rows of at most 64 face
+                               sides; forward solves only (the adjoint takes scheme (a)). */
 } sweep_opts;
 
 /* Forms of the assembled transport operator (the rows of L_Omega, Sec. 2.3, built once per
@@ -205,8 +213,9 @@ sweep_status sweep_solve_dev(sweep_ctx* ctx, const sweep_opts* opts, double* mea
 
 /* Wavefront level of every cell for direction `dir` (0 = no upwind cell, else 1 + the
  * largest level of its upwind cells: the longest dependency path, Sec. 2.3) and the
- * direction's depth (1 + largest level). Classifies and levelises if not cached.
- * level[n_cells] host pointer. Errors: INVALID_ARG, CYCLE. */
+ * direction's depth (1 + largest level), in the dependency graph of the transport scheme the
+ * cached levels were made for (that of the last solve; scheme (a) when nothing is cached).
+ * Classifies and levelises if not cached. level[n_cells] host pointer. Errors: INVALID_ARG, CYCLE. */
 sweep_status sweep_levels(sweep_ctx* ctx, int32_t dir, int32_t* level, int32_t* depth);
 
 /* Intensity of direction `dir` from the last solve's final sweep, as FP64, [n_cells][G]

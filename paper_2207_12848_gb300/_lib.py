@@ -44,7 +44,7 @@ class sweep_opts(ctypes.Structure):
                 ("spin_budget", ctypes.c_int64), ("debug_stall", ctypes.c_int32),
                 ("lanes_per_task", ctypes.c_int32), ("geometry_only", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("fused_loops", ctypes.c_int32),
-                ("op_format", ctypes.c_int32), ("packets_per_step", ctypes.c_int32)]
+                ("op_format", ctypes.c_int32), ("packets_per_step", ctypes.c_int32), ("transport", ctypes.c_int32)]
 
 
 class sweep_stats(ctypes.Structure):

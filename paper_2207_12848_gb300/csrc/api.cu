@@ -118,11 +118,13 @@ void free_levels(Levels& L) {
     dfree(L.lev_chunk); dfree(L.seg_off); dfree(L.op); dfree(L.dlev);
     dfree(L.pk); dfree(L.pk_meta); dfree(L.lev_pk); dfree(L.pk_grp); dfree(L.pk_cnt); dfree(L.pk_off); dfree(L.pk_scan);
     dfree(L.pk_flag);
+    dfree(L.dc_mask); dfree(L.dc_inm); dfree(L.dc_share32); dfree(L.dc_share64);
     L = Levels();
 }
 
 void free_mesh(DevMesh& m) {
-    dfree(m.rowptr); dfree(m.side); dfree(m.side64); dfree(m.side_lo); dfree(m.nbr_rows); dfree(m.vol); dfree(m.pcells); dfree(m.bcells);
+    dfree(m.rowptr); dfree(m.side); dfree(m.side64); dfree(m.side_lo); dfree(m.nbr_rows); dfree(m.twin); dfree(m.vol);
+    dfree(m.pcells); dfree(m.bcells);
     m = DevMesh();
 }
 
@@ -176,9 +178,21 @@ sweep_status alloc_levels(sweep_ctx* c, Levels& L, int d0, int nd) {
     return SWEEP_OK;
 }
 
-sweep_status run_levelise(sweep_ctx* c, Levels& L, int d0, int nd, long long budget, float* t1, float* t2) {
+sweep_status run_levelise(sweep_ctx* c, Levels& L, int d0, int nd, long long budget, float* t1, float* t2,
+                          int transport = 0) {
     sweep_status s = alloc_levels(c, L, d0, nd);
     if (s != SWEEP_OK) return s;
+    // scheme (b) tables, [N][nd] each (freed when scheme (a) is levelised again)
+    if (transport > 0 && !L.dc_mask) {
+        const size_t n = (size_t)c->mesh.N * nd;
+        CK(cudaMalloc(&L.dc_mask, sizeof(uint64_t) * n), "alloc scheme (b) tables");
+        CK(cudaMalloc(&L.dc_inm, sizeof(uint64_t) * n), "alloc scheme (b) tables");
+        CK(cudaMalloc(&L.dc_share32, sizeof(float) * n), "alloc scheme (b) tables");
+        CK(cudaMalloc(&L.dc_share64, sizeof(double) * n), "alloc scheme (b) tables");
+    } else if (transport == 0 && L.dc_mask) {
+        dfree(L.dc_mask); dfree(L.dc_inm); dfree(L.dc_share32); dfree(L.dc_share64);
+    }
+    L.transport = transport;
     CK(cudaMemsetAsync(c->derr, 0, sizeof(int), c->st), "reset error word");
     std::string msg;
     CK(levelise(c->mesh, L, c->om64, c->om32, c->om32lo, c->sms, c->bar, c->derr, budget, c->scratch, c->st, t1, t2, &msg),
@@ -187,6 +201,7 @@ sweep_status run_levelise(sweep_ctx* c, Levels& L, int d0, int nd, long long bud
     if (!L.valid) {
         c->err = msg;
         if (msg.find("cyclic") != std::string::npos) return SWEEP_ERR_CYCLE;
+        if (msg.find("direction-conserving") != std::string::npos) return SWEEP_ERR_INVALID_ARG;
         return SWEEP_ERR_TIMEOUT;
     }
     return SWEEP_OK;
@@ -268,6 +283,12 @@ SweepArgs make_args(sweep_ctx* c, const Levels& L, int precision, const void* cm
     a.pk_meta = L.pk_meta;
     a.n_pk = L.n_pk;
     a.lev_pk = L.lev_pk;
+    if (L.transport > 0 && !reverse) {
+        a.dc_mask = L.dc_mask;
+        a.dc_share32 = L.dc_share32;
+        a.dc_share64 = L.dc_share64;
+        a.twin = c->mesh.twin;
+    }
     a.n_chunks = L.h_lev_chunk.empty() ? 0 : L.h_lev_chunk.back();
     a.lev_chunk = L.lev_chunk;
     a.n_levels = L.n_levels;
@@ -321,7 +342,9 @@ sweep_status run_sweep(sweep_ctx* c, const Levels& L, int precision, int schedul
     } else {
         // the EXP law runs in the generic kernel, whose occupancy the reverse query gives
         const int fmt = a.pk ? OPF_PACKETS : (a.op ? OPF_LINES : OPF_NONE);
-        int per_sm = sweep_occupancy(precision, a.G, threads, L.nd, lanes, a.reverse || a.law, fmt);
+        // the EXP law and scheme (b) without an assembled operator run in the generic kernel
+        const bool generic = a.reverse || a.law || (a.dc_mask && fmt == OPF_NONE);
+        int per_sm = sweep_occupancy(precision, a.G, threads, L.nd, lanes, generic, fmt);
         if (per_sm < 1) return bad(c, "sweep kernel does not fit on an SM");
         if (bpsm > 0 && bpsm < per_sm) per_sm = bpsm;
         a.level_sync = schedule == SWEEP_SCHED_LEVEL ? 1 : 0;
@@ -430,7 +453,8 @@ sweep_status graph_loop(sweep_ctx* c, const sweep_opts& o, int prec, const void*
     cudaStream_t gs = c->gst;
     IterHost* hp = reinterpret_cast<IterHost*>(c->hpin);
     const int fmt = (prec == 32 && !o.law && c->lev.op_valid && !o.geometry_only) ? c->lev.op_format : OPF_NONE;
-    int per_sm = sweep_occupancy(prec, G, threads, c->lev.nd, lanes, o.law ? 1 : 0, fmt);
+    const bool generic = o.law || (c->lev.transport > 0 && fmt == OPF_NONE);
+    int per_sm = sweep_occupancy(prec, G, threads, c->lev.nd, lanes, generic ? 1 : 0, fmt);
     if (per_sm < 1) return bad(c, "sweep kernel does not fit on an SM");
     if (bpsm > 0 && bpsm < per_sm) per_sm = bpsm;
     const int period = pbc ? 4 : 2;
@@ -721,6 +745,7 @@ sweep_status sweep_set_mesh(sweep_ctx* c, int64_t n_cells, const double* volume,
     CKM(cudaMalloc(&m.side64, sizeof(d4) * (S > 0 ? S : 1)), "alloc sides");
     CKM(cudaMalloc(&m.side_lo, sizeof(float4) * (S > 0 ? S : 1)), "alloc sides");
     CKM(cudaMalloc(&m.nbr_rows, sizeof(int2) * (S > 0 ? S : 1)), "alloc sides");
+    CKM(cudaMalloc(&m.twin, sizeof(uint32_t) * (S > 0 ? S : 1)), "alloc sides");
     CKM(launch_build_csr(m, d_fc, d_area, d_normal, d_flags, d_tmp, c->st), "build CSR");
     CKM(cudaStreamSynchronize(c->st), "build CSR");
 #undef CKM
@@ -832,12 +857,25 @@ sweep_status sweep_set_material_dev(sweep_ctx* c, int32_t G, const double* ka, c
 // ---------------------------------------------------------------------------------------------
 namespace {
 
+// scheme (b) tables of the cached levels (empty in scheme (a))
+DcTabs dc_tabs(sweep_ctx* c, const Levels& L) {
+    DcTabs t;
+    if (L.transport > 0) {
+        t.mask = L.dc_mask;
+        t.share64 = L.dc_share64;
+        t.twin = c->mesh.twin;
+    }
+    return t;
+}
+
 // Form of the assembled operator a solve with these options sweeps over (OPF_NONE: it reads the mesh).
 int wanted_format(sweep_ctx* c, const Levels& L, const sweep_opts* o, int prec) {
     if (prec != 32 || !o || o->law != SWEEP_LAW_BALANCE || o->geometry_only || o->schedule == SWEEP_SCHED_PLAIN)
         return OPF_NONE;
     const int G = c->G;
     const bool pk_ok = (G == 1 || G == 2 || G == 4) && (uint64_t)c->mesh.N * (uint64_t)L.nd <= (1ull << 31);
+    if (L.transport > 0)  // scheme (b): its shares live in the packets; otherwise the mesh-row kernel
+        return pk_ok ? OPF_PACKETS : OPF_NONE;
     if (pk_ok && (o->op_format == SWEEP_OP_PACKETS || (o->op_format == SWEEP_OP_AUTO && o->lanes_per_task == 0)))
         return OPF_PACKETS;
     return OPF_LINES;
@@ -920,10 +958,14 @@ sweep_status ensure_operator(sweep_ctx* c, Levels& L, const sweep_opts* o, int p
     return SWEEP_OK;
 }
 
+// Levels of every direction in the dependency graph of the requested transport scheme (without options:
+// whatever scheme is cached, else scheme (a)).
 sweep_status ensure_levels(sweep_ctx* c, const sweep_opts* o, float* t1, float* t2) {
-    if (c->lev.valid && !(o && o->relevel) && c->lev.nd == c->D && c->lev.d0 == 0) return SWEEP_OK;
+    const int tr = o ? o->transport : (c->lev.valid ? c->lev.transport : 0);
+    if (c->lev.valid && !(o && o->relevel) && c->lev.nd == c->D && c->lev.d0 == 0 && c->lev.transport == tr)
+        return SWEEP_OK;
     c->lev.op_valid = false;
-    return run_levelise(c, c->lev, 0, c->D, budget_of(o), t1, t2);
+    return run_levelise(c, c->lev, 0, c->D, budget_of(o), t1, t2, tr);
 }
 
 sweep_status ensure_solution(sweep_ctx* c, int prec, bool two) {
@@ -1084,6 +1126,7 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     cudaEventRecord(t0, c->st);
     if (o.op_format < SWEEP_OP_AUTO || o.op_format > SWEEP_OP_PACKETS) return bad(c, "op_format must be 0, 1 or 2");
     if (o.packets_per_step < 0 || o.packets_per_step > 2) return bad(c, "packets_per_step must be 0, 1 or 2");
+    if (o.transport < 0 || o.transport > 8) return bad(c, "transport must be 0 (scheme (a)) or 1..8 (scheme (b))");
     float tc = 0, tl = 0, top = 0;
     sweep_status s = ensure_levels(c, &o, &tc, &tl);
     if (s != SWEEP_OK) return s;
@@ -1148,7 +1191,8 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     int prev = -1;
     if (has_pbc) {
         c->ptab.ready = false;
-        CK(build_periodic_table(c->mesh, D, c->om64, c->w64, &c->ptab, c->st), "periodic weights");
+        const DcTabs dct = dc_tabs(c, c->lev);
+        CK(build_periodic_table(c->mesh, D, c->om64, c->w64, &c->ptab, c->st, &dct), "periodic weights");
         c->launches += 3;
         if (o.warm_start && b.last >= 0) prev = b.last;
         else {
@@ -1277,7 +1321,9 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
                     c->Gam, c->partial, nblk, c->st), "tally");
     CKL(launch_reduce_sum(c->partial, nblocks256(NG), c->red, c->st), "reduce");
     if (c->mesh.n_bcells > 0) {
-        CKL(launch_boundary_tally(prec, c->mesh, b.I[fin], G, D, 0, c->om64, c->w64, c->bc, c->partial, nblk, c->st),
+        const DcTabs dct = dc_tabs(c, c->lev);
+        CKL(launch_boundary_tally(prec, c->mesh, b.I[fin], G, D, 0, c->om64, c->w64, c->bc, c->partial, nblk, c->st,
+                                  &dct),
            "boundary tally");
         CKL(launch_reduce_sum(c->partial, (int)c->mesh.n_bcells, c->red + 2, c->st), "reduce");
     } else {
@@ -1331,6 +1377,7 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
     if (!c->has_mesh || !c->has_dirs || !c->has_mat) return bad(c, "set mesh, directions and material first");
     if (c->G > 4) return bad(c, "the adjoint supports at most 4 groups");
     if (opts_in && opts_in->law != SWEEP_LAW_BALANCE) return bad(c, "the adjoint takes the BALANCE law");
+    if (opts_in && opts_in->transport != 0) return bad(c, "the adjoint takes transport scheme (a)");
     if (!gk_out || !ge_out) return bad(c, "null gradient output");
     sweep_opts o;
     if (opts_in) o = *opts_in;

@@ -311,6 +311,8 @@ struct DevMesh {
     d4* side64 = nullptr;                  // [S]
     float4* side_lo = nullptr;             // [S] area vector minus its FP32 value in the side record
     int2* nbr_rows = nullptr;              // [S] row bounds of the side's interior neighbour ({0, 0} otherwise)
+    uint32_t* twin = nullptr;              // [S] position of the same face in the neighbour's row (interior and
+                                           //     periodic sides; boundary sides 0xffffffff)
     double* vol = nullptr;                 // [N]
     int32_t* pcells = nullptr;             // cells with periodic sides
     int64_t n_pcells = 0;
@@ -349,6 +351,14 @@ struct Levels {
     int64_t pk_grp_cap = 0;      // groups (and levels + 1) the tables above hold
     int64_t pk_ng = 0;
     int32_t* pk_flag = nullptr;  // device word: a task has more than PK_MAX_IN inflow sides
+    // direction-conserving transport (scheme (b) of Sec. 2.6), [N][nd] like info: the chosen outflow
+    // sides (bit k = row position k), the effective inflow sides (interior and periodic sides the
+    // upwind cell chose, boundary inflow sides), and the share P_c / n_c each chosen side carries
+    int transport = 0;           // 0 = scheme (a); n = scheme (b) to n neighbours
+    uint64_t* dc_mask = nullptr;
+    uint64_t* dc_inm = nullptr;
+    float* dc_share32 = nullptr;
+    double* dc_share64 = nullptr;
     int32_t* level = nullptr;    // [nd][N] (during levelisation: minus the upwind cells still unsolved)
     int32_t* lvl_cnt = nullptr;  // [N+2]
     uint32_t* pad_off = nullptr; // [N+2] start of each level in the padded list
@@ -371,6 +381,11 @@ struct SweepArgs {
     const int4* trec;     // task records (FP32 forward sweep)
     const int4* op;       // assembled operator headers (one int4 per task), or null (FP32 forward sweep)
     const int4* pk;       // packed operator (FP32 forward sweep), or null
+    // scheme (b): per [N][nd] chosen outflow sides and shares, per side the twin's row position (null: scheme (a))
+    const uint64_t* dc_mask;
+    const float* dc_share32;
+    const double* dc_share64;
+    const uint32_t* twin;
     const uint2* pk_meta; // [n_pk] {head mask, long-task flag} of each packet
     int64_t n_pk;
     const int64_t* lev_pk;  // [n_levels+1] first packet of each level
@@ -442,9 +457,16 @@ cudaError_t launch_prep_adjoint_src(int64_t N, int G, const double* vol, const d
 cudaError_t launch_tally(int precision, const void* I, int64_t N, int G, int nd, int d0, const double* w64,
                          double wsum, const double* vol, const double* ka, const double* em, double* J,
                          double* Gam, double* partial, int nblk, cudaStream_t st);
+// scheme (b) tables of a solve ([N][nd] chosen outflow sides and FP64 shares, per side the twin's row
+// position); a null pointer to it, or a null mask, means scheme (a)
+struct DcTabs {
+    const uint64_t* mask = nullptr;
+    const double* share64 = nullptr;
+    const uint32_t* twin = nullptr;
+};
 cudaError_t launch_boundary_tally(int precision, const DevMesh& m, const void* I, int G, int nd, int d0,
                                   const double* om64, const double* w64, const double* bc, double* partial,
-                                  int nblk, cudaStream_t st);
+                                  int nblk, cudaStream_t st, const DcTabs* dc = nullptr);
 cudaError_t launch_scat_residual(int64_t NG, const double* J, double* Jold, unsigned long long* d_max,
                                  cudaStream_t st);
 // FP64 periodic-inflow weights of a solve (periodic sides of the periodic cells x directions)
@@ -456,7 +478,7 @@ struct PeriodicTable {
     bool ready = false;
 };
 cudaError_t build_periodic_table(const DevMesh& m, int nd, const double* om64, const double* w64, PeriodicTable* t,
-                                 cudaStream_t st);
+                                 cudaStream_t st, const DcTabs* dc = nullptr);
 cudaError_t launch_periodic_source(int precision, const DevMesh& m, const void* I, int G, int nd,
                                    const double* om64, const double* w64, double* jn1, const double* jn,
                                    unsigned long long* d_max, double* partial, int nblk, cudaStream_t st,

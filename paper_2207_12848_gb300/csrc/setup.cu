@@ -214,6 +214,29 @@ __global__ void k_fill_sides(int64_t S, const int64_t* key, const int32_t* fc, c
     nbr_rows[s] = nbr >= 0 && !(nbr & NBR_PERIODIC) ? make_int2((int)rowptr[nbr], (int)rowptr[nbr + 1]) : make_int2(0, 0);
 }
 
+// Position of each interior or periodic side's twin (the same face seen from the neighbour) in the
+// neighbour's row: rows are sorted by (face, side), so the twin's key is this key with its side bit
+// flipped, found by binary search. Boundary sides get 0xffffffff.
+__global__ void k_twin(int64_t S, const int64_t* key, const int32_t* fc, const uint8_t* flags, const uint32_t* rowptr,
+                       uint32_t* twin) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const int64_t k = key[s], f = k >> 1;
+    if (flags[f] & SWEEP_FACE_BOUNDARY) {
+        twin[s] = 0xffffffffu;
+        return;
+    }
+    const int32_t u = (k & 1) ? fc[2 * f] : fc[2 * f + 1];
+    const int64_t want = k ^ 1;
+    uint32_t lo = rowptr[u], hi = rowptr[u + 1];  // key[lo..hi) ascending
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (key[mid] <= want) lo = mid;
+        else hi = mid;
+    }
+    twin[s] = lo - rowptr[u];
+}
+
 __global__ void k_cell_kinds(int64_t N, const uint32_t* rowptr, const int4* side, int32_t* isp, int32_t* isb) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
@@ -274,7 +297,7 @@ cudaError_t launch_build_csr(const DevMesh& mc, const int32_t* fc, const double*
     TRY(scan_i32(d_tmp, N + 1, off, scratch, total, st));  // d_tmp[N] = 0 -> off[N] = S
     k_to_u32<<<nblk(N + 1), 256, 0, st>>>(off, N + 1, m.rowptr);
     if (F > 0) k_scatter_sides<<<nblk(F), 256, 0, st>>>(F, fc, m.rowptr, fill, key);
-    if (N > 0) k_sort_rows<<<nblk(N), 128, 0, st>>>(N, m.rowptr, key, maxrow);
+    if (N > 0) k_sort_rows<<<nblk(N, 128), 128, 0, st>>>(N, m.rowptr, key, maxrow);
     // boundary ordinals in face order
     if (F > 0) {
         k_flag_boundary<<<nblk(F), 256, 0, st>>>(F, flags, isb);
@@ -282,6 +305,7 @@ cudaError_t launch_build_csr(const DevMesh& mc, const int32_t* fc, const double*
     }
     if (S > 0) k_fill_sides<<<nblk(S), 256, 0, st>>>(S, key, fc, area, normal, flags, bidx, m.rowptr, m.side,
                                                      m.side64, m.side_lo, m.nbr_rows);
+    if (S > 0) k_twin<<<nblk(S), 256, 0, st>>>(S, key, fc, flags, m.rowptr, m.twin);
     // periodic / boundary cell lists (increasing cell order)
     if (N > 0) {
         k_cell_kinds<<<nblk(N), 256, 0, st>>>(N, m.rowptr, m.side, isp, isb);
@@ -388,6 +412,97 @@ __global__ void k_classify(int64_t N, int nd, const uint32_t* rowptr, const int4
         base = __shfl_sync(0xffffffffu, base, leader);
         if (push) raw[base + __popc(m & ((1u << lane) - 1))] = entry;
     }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Direction-conserving transport (scheme (b) of Sec. 2.6), per task (c, Omega): the cell hands its
+// outflow P_c I_c in equal parts to the n outflow sides whose outward normal is most nearly along
+// Omega -- largest n.Omega in the exact FP64 rounding sequence of the classification, ties to the
+// lower face index (rows are sorted by face) -- or to all its outflow sides if it has fewer. The share
+// of each chosen side is P_c / n_c, P_c summed in FP64 in row order.
+// ---------------------------------------------------------------------------------------------
+constexpr int DC_MAX_N = 8;      // largest n of scheme (b)
+constexpr int DC_MAX_ROW = 64;   // face sides per row (one 64-bit mask)
+
+__global__ void k_dc_choose(int64_t N, int nd, int dcn, const uint32_t* rowptr, const d4* side64, const double* om64,
+                            uint64_t* dc_mask, float* share32, double* share64, int* bad) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N * (int64_t)nd) return;
+    const int64_t c = t / nd;
+    const int dl = (int)(t - c * nd);
+    const uint32_t r0 = rowptr[c], r1 = rowptr[c + 1];
+    if (r1 - r0 > (uint32_t)DC_MAX_ROW) {
+        atomicOr(bad, 1);
+        dc_mask[t] = 0ull;
+        share32[t] = 0.f;
+        share64[t] = 0.0;
+        return;
+    }
+    const double* o = om64 + 3 * dl;
+    double P = 0.0;
+    double bt[DC_MAX_N];
+    int bk[DC_MAX_N];
+    int nb = 0;
+    for (uint32_t s = r0; s < r1; ++s) {
+        const d4 n = side64[s];
+        const double tt = exact_t(n, o);
+        if (!(tt > 0.0)) continue;
+        P = __dadd_rn(P, __dmul_rn(n.w, tt));
+        // kept sorted by (n.Omega descending, row position ascending): a later side displaces a kept one
+        // only with a strictly larger n.Omega
+        if (nb < dcn || tt > bt[dcn - 1]) {
+            int i = nb < dcn ? nb++ : dcn - 1;
+            while (i > 0 && tt > bt[i - 1]) {
+                bt[i] = bt[i - 1];
+                bk[i] = bk[i - 1];
+                --i;
+            }
+            bt[i] = tt;
+            bk[i] = (int)(s - r0);
+        }
+    }
+    uint64_t m = 0ull;
+    for (int i = 0; i < nb; ++i) m |= 1ull << bk[i];
+    const double sh = nb > 0 ? __ddiv_rn(P, (double)nb) : 0.0;
+    dc_mask[t] = m;
+    share64[t] = sh;
+    share32[t] = (float)sh;
+}
+
+// Effective inflow sides of each task under scheme (b) -- interior and periodic sides whose upwind cell
+// chose the face (read through the twin side's position in the upwind row), and boundary inflow sides,
+// which enter as in scheme (a) -- and the upwind count over the chosen interior faces, which seeds the
+// levelisation (level = -count, level-0 lists per direction).
+__global__ void k_dc_count(int64_t N, int nd, const uint32_t* rowptr, const int4* side, const d4* side64,
+                           const float4* om32, const double* om64, const uint32_t* twin, const uint64_t* dc_mask,
+                           uint64_t* dc_inm, int32_t* level, uint32_t* dlist, int32_t* n0) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N * (int64_t)nd) return;
+    const int64_t c = t / nd;
+    const int dl = (int)(t - c * nd);
+    const uint32_t r0 = rowptr[c], r1 = min(rowptr[c + 1], r0 + (uint32_t)DC_MAX_ROW);
+    const float4 om = om32[dl];
+    const double* o64 = om64 + 3 * dl;
+    uint64_t inm = 0ull;
+    int cnt = 0;
+    for (uint32_t s = r0; s < r1; ++s) {
+        const int4 r = side[s];
+        const float ax = __int_as_float(r.y), ay = __int_as_float(r.z), az = __int_as_float(r.w);
+        if (classify_side(dot32(ax, ay, az, om), ax, ay, az, side64, s, o64) >= 0) continue;
+        const uint64_t bit = 1ull << (s - r0);
+        if (r.x < 0) {
+            inm |= bit;
+            continue;
+        }
+        const uint32_t u = (uint32_t)(r.x & NBR_MASK);
+        if ((dc_mask[(int64_t)u * nd + dl] >> twin[s]) & 1ull) {
+            inm |= bit;
+            if (!(r.x & NBR_PERIODIC)) ++cnt;
+        }
+    }
+    dc_inm[t] = inm;
+    level[(size_t)dl * N + c] = -cnt;
+    if (cnt == 0) dlist[(size_t)dl * N + atomicAdd(&n0[dl], 1)] = (uint32_t)c;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -577,6 +692,7 @@ struct DirLevArgs {
     const int2* nbr_rows;    // [S] row bounds of each side's interior neighbour
     const float4* om32;
     const double* om64;
+    const uint64_t* dc_mask; // scheme (b): [N][nd] chosen outflow sides (release only those), or null
     int32_t* level;          // [nd][N]: minus the unsolved upwind cells, then the level
     uint32_t* dlist;         // [nd][N] cells of each direction in level order; level 0 from the classification
     const int32_t* n0;       // [nd] level-0 sizes
@@ -628,15 +744,17 @@ __global__ void __launch_bounds__(LD_THREADS, 1) k_levelise_dir(DirLevArgs a) {
             for (int i0 = 0; i0 < n; i0 += TPR) {
                 const int i = i0 + threadIdx.x / LD_KL;
                 if (i >= n) continue;
-                uint32_t r0, r1;
+                uint32_t r0, r1, cc;
                 if (i < LD_Q) {
+                    cc = q[3 * i];
                     r0 = q[3 * i + 1];
                     r1 = q[3 * i + 2];
                 } else {  // a level wider than the shared list: cells from the global list
-                    const uint32_t c = out[base + i];
-                    r0 = a.rowptr[c];
-                    r1 = a.rowptr[c + 1];
+                    cc = out[base + i];
+                    r0 = a.rowptr[cc];
+                    r1 = a.rowptr[cc + 1];
                 }
+                const uint64_t chosen = a.dc_mask ? a.dc_mask[(int64_t)cc * a.nd + d] : 0ull;
                 for (uint32_t b = r0; b < r1; b += LD_KL * LD_KU) {
                     int4 r[LD_KU];
 #pragma unroll
@@ -654,7 +772,11 @@ __global__ void __launch_bounds__(LD_THREADS, 1) k_levelise_dir(DirLevArgs a) {
                         const uint32_t s = b + gl + k * LD_KL;
                         const float ax = __int_as_float(r[k].y), ay = __int_as_float(r[k].z),
                                     az = __int_as_float(r[k].w);
-                        if (classify_side(dot32(ax, ay, az, om), ax, ay, az, a.side64, s, o64) <= 0) continue;
+                        if (a.dc_mask) {  // scheme (b): the chosen sides only
+                            if (!((chosen >> (s - r0)) & 1ull)) continue;
+                        } else if (classify_side(dot32(ax, ay, az, om), ax, ay, az, a.side64, s, o64) <= 0) {
+                            continue;
+                        }
                         old[k] = atomicAdd(&lv[r[k].x], 1);
                         nr[k] = a.nbr_rows[s];
                     }
@@ -929,6 +1051,9 @@ struct PackArgs {
     uint32_t N;
     int32_t* cnt;        // count pass: packets per group
     int32_t* flag;       // count pass: set when a task has more than PK_MAX_IN inflow sides
+    int nd;
+    const uint64_t* dc_inm;   // scheme (b): [N][nd] effective inflow sides, or null (scheme (a))
+    const float* dc_share32;  // scheme (b): [N][nd] share of each chosen side
     const int64_t* off;  // write pass: first packet of each group
     int4* pk;
     uint2* meta;
@@ -954,8 +1079,14 @@ __device__ int pk_inflow_past32(const PackArgs& a, const int4 tr, int stop_at, u
     return k;
 }
 
+// scheme (b) table index of a task
+__device__ __forceinline__ int64_t pk_dc_index(const PackArgs& a, uint32_t e) {
+    return (int64_t)(e & a.cmask) * a.nd + (e >> a.cshift);
+}
+
 // inflow entries of a task
 __device__ __forceinline__ int pk_task_inflow(const PackArgs& a, const int4 tr) {
+    if (a.dc_inm) return __popcll(a.dc_inm[pk_dc_index(a, (uint32_t)tr.x)]);
     int n = __popc((uint32_t)tr.w);
     if (tr.z < 0) {
         uint32_t dummy;
@@ -969,15 +1100,23 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int j) {
     return __ffs(m) - 1;
 }
 
-// entry j of a task: its j-th inflow side in row order
+// entry j of a task: its j-th inflow side in row order (scheme (b): of its effective inflow sides, the
+// interior and periodic ones weighted by the upwind cell's share)
 __device__ int2 pk_entry(const PackArgs& a, const int4 tr, int j, uint32_t slab, const float4& om, const float4& oml) {
-    const uint32_t inm = (uint32_t)tr.w;
-    const int nm = __popc(inm);
     uint32_t s = 0;
-    if (j < nm) s = (uint32_t)tr.y + (uint32_t)nth_set_bit(inm, j);
-    else pk_inflow_past32(a, tr, j - nm, &s);
+    if (a.dc_inm) {
+        uint64_t m = a.dc_inm[pk_dc_index(a, (uint32_t)tr.x)];
+        for (int q = 0; q < j; ++q) m &= m - 1;
+        s = (uint32_t)tr.y + (uint32_t)(__ffsll((long long)m) - 1);
+    } else {
+        const uint32_t inm = (uint32_t)tr.w;
+        const int nm = __popc(inm);
+        if (j < nm) s = (uint32_t)tr.y + (uint32_t)nth_set_bit(inm, j);
+        else pk_inflow_past32(a, tr, j - nm, &s);
+    }
     const int4 r = a.side[s];
-    const float w = side_weight(r, a.side_lo[s], om, oml);
+    float w = side_weight(r, a.side_lo[s], om, oml);
+    if (a.dc_inm && r.x >= 0) w = a.dc_share32[(int64_t)(r.x & NBR_MASK) * a.nd + ((uint32_t)tr.x >> a.cshift)];
     if (r.x >= 0 && !(r.x & NBR_PERIODIC)) return make_int2((int)(slab + (uint32_t)r.x), __float_as_int(w));
     if (r.x >= 0) return make_int2((int)(slab + (uint32_t)(r.x & NBR_MASK)), __float_as_int(-w));
     return make_int2((int)((uint32_t)(-1 - r.x) | PK_BOUNDARY), __float_as_int(-w));
@@ -1102,6 +1241,9 @@ PackArgs pack_args(const DevMesh& m, const Levels& L, const double* om64_all, co
     a.N = (uint32_t)m.N;
     a.cnt = L.pk_cnt;
     a.flag = L.pk_flag;
+    a.nd = L.nd;
+    a.dc_inm = L.transport > 0 ? L.dc_inm : nullptr;
+    a.dc_share32 = L.transport > 0 ? L.dc_share32 : nullptr;
     a.off = L.pk_off;
     a.pk = L.pk;
     a.meta = L.pk_meta;
@@ -1218,6 +1360,7 @@ cudaError_t levelise_by_direction(const DevMesh& m, Levels& L, const float4* om3
     a.N = m.N; a.nd = nd; a.cap = cap; a.rowptr = m.rowptr; a.side = m.side; a.side64 = m.side64;
     a.nbr_rows = m.nbr_rows; a.om32 = om32; a.om64 = om64; a.level = L.level; a.dlist = L.raw; a.n0 = n0;
     a.dcnt = dcnt; a.dbase = dbase;
+    a.dc_mask = L.transport > 0 ? L.dc_mask : nullptr;
     a.depth = depth; a.overflow = ovf;
     const int blocks = nd < dev_sms ? nd : dev_sms;
     cudaFuncSetAttribute(k_levelise_dir, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LD_SMEM);
@@ -1307,6 +1450,33 @@ cudaError_t levelise(const DevMesh& m, Levels& L, const double* om64_all, const 
     const bool by_dir = L.dlev != nullptr && L.dlev_cap > 0;
     e = classify(m, L, om32, om32lo, om64, by_dir, st);
     if (e != cudaSuccess) return e;
+    if (L.transport > 0) {
+        // scheme (b): the chosen sides and shares, then the counts and level-0 lists of its thinner graph
+        if (!by_dir) {
+            *msg = "direction-conserving transport needs the direction-parallel levelisation";
+            L.valid = false;
+            return cudaSuccess;
+        }
+        int* bad = reinterpret_cast<int*>(d_scratch + 2);
+        int32_t* n0 = L.dlev + (int64_t)nd * 2 * L.dlev_cap;
+        if ((e = cudaMemsetAsync(bad, 0, sizeof(int), st))) return e;
+        if ((e = cudaMemsetAsync(n0, 0, sizeof(int32_t) * nd, st))) return e;
+        const int64_t tot = N * (int64_t)nd;
+        if (tot > 0) {
+            k_dc_choose<<<nblk(tot), 256, 0, st>>>(N, nd, L.transport, m.rowptr, m.side64, om64, L.dc_mask,
+                                                   L.dc_share32, L.dc_share64, bad);
+            k_dc_count<<<nblk(tot), 256, 0, st>>>(N, nd, m.rowptr, m.side, m.side64, om32, om64, m.twin, L.dc_mask,
+                                                  L.dc_inm, L.level, L.raw, n0);
+        }
+        int hbad = 0;
+        if ((e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st))) return e;
+        if ((e = cudaStreamSynchronize(st))) return e;
+        if (hbad) {
+            *msg = "direction-conserving transport: a row has more than 64 face sides";
+            L.valid = false;
+            return cudaSuccess;
+        }
+    }
     cudaEventRecord(ev[1], st);
     int nlev = 0;
     bool done_by_dir = false;
@@ -1315,6 +1485,11 @@ cudaError_t levelise(const DevMesh& m, Levels& L, const double* om64_all, const 
         e = levelise_by_direction(m, L, om32, om64, dev_sms, st, &nlev, &overflow);
         if (e != cudaSuccess) return e;
         done_by_dir = !overflow;
+        if (overflow && L.transport > 0) {
+            *msg = "direction-conserving transport: a direction is deeper than 65536 levels";
+            L.valid = false;
+            return cudaSuccess;
+        }
         if (overflow) {
             e = classify(m, L, om32, om32lo, om64, false, st);
             if (e != cudaSuccess) return e;

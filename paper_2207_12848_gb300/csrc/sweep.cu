@@ -180,6 +180,11 @@ __device__ __forceinline__ bool group_task(const SweepArgs& a, uint32_t entry, u
                     if (nb >= 0 && !(nb & NBR_PERIODIC)) kind[k] = 1;
                     else if (nb >= 0) kind[k] = 2;  // the partner's value of the previous sweep or pass
                     else if (!a.reverse) kind[k] = 3;
+                    if (a.dc_mask && nb >= 0) {  // scheme (b): the upwind cell's share, if it chose this face
+                        const int64_t i = (int64_t)(nb & NBR_MASK) * a.nd + dl;
+                        if ((a.dc_mask[i] >> a.twin[s]) & 1ull) w[k] = F64 ? (real)a.dc_share64[i] : (real)a.dc_share32[i];
+                        else kind[k] = 0;
+                    }
                 }
             }
         }
@@ -1295,6 +1300,12 @@ __device__ __forceinline__ void plain_task(const SweepArgs& a, uint32_t entry) {
         if (t > 0.0) P = __dadd_rn(P, w);
         const bool inflow = a.reverse ? t > 0.0 : t < 0.0;
         if (!inflow) continue;
+        double wi = w;
+        if (a.dc_mask && nb >= 0) {  // scheme (b): the upwind cell's share, if it chose this face
+            const int64_t i = (int64_t)(nb & NBR_MASK) * a.nd + dl;
+            if (!((a.dc_mask[i] >> a.twin[s]) & 1ull)) continue;
+            wi = a.dc_share64[i];
+        }
         const double* src = nullptr;
         if (nb >= 0 && !(nb & NBR_PERIODIC)) src = I + (slab + (uint32_t)nb) * G;
         else if (nb >= 0) src = a.Iprev ? reinterpret_cast<const double*>(a.Iprev) + (slab + (nb & NBR_MASK)) * G
@@ -1303,7 +1314,7 @@ __device__ __forceinline__ void plain_task(const SweepArgs& a, uint32_t entry) {
         else src = a.bc ? reinterpret_cast<const double*>(a.bc) + (size_t)(-1 - nb) * G : nullptr;
         if (!src) continue;
         for (int g = 0; g < GM; ++g)
-            if (g < G) acc[g] = __dadd_rn(acc[g], __dmul_rn(w, fabs(src[g])));
+            if (g < G) acc[g] = __dadd_rn(acc[g], __dmul_rn(wi, fabs(src[g])));
     }
     double* dst = I + (slab + c) * G;
     for (int g = 0; g < GM; ++g) {
@@ -1386,7 +1397,7 @@ cudaError_t launch_typed(const SweepArgs& a, int blocks, int threads, cudaStream
         if (a.lanes == 4) return launch_op_lanes<4>(a, cfg);
         return launch_op_lanes<8>(a, cfg);
     }
-    if (sizeof(real) == 4 && !a.reverse && !a.law) {  // FP32 forward: the record kernel
+    if (sizeof(real) == 4 && !a.reverse && !a.law && !a.dc_mask) {  // FP32 forward, scheme (a): the record kernel
         *kid = SWEEP_KERNEL_RECORDS;
         if (a.lanes == 1) return launch_rec_lanes<1>(a, cfg);
         if (a.lanes == 2) return launch_rec_lanes<2>(a, cfg);

@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_boundary_tally(const int32_t* b
                                                                 const int4* side, const d4* side64, const real* I,
                                                                 int64_t N, int G, int nd, const double* om64,
                                                                 const double* w64, const double* bc,
-                                                                double* partial) {
+                                                                double* partial, DcTabs dc) {
     __shared__ double sh[ROW_THREADS / 32];
     const int64_t k = blockIdx.x;
     const int32_t c = bcells[k];
@@ -135,8 +135,14 @@ __global__ void __launch_bounds__(ROW_THREADS) k_boundary_tally(const int32_t* b
             const d4 n = side64[s];
             const double t = exact_t(n, om64 + 3 * d);
             const double wa = dmul(w, dmul(n.w, fabs(t)));
+            // scheme (b): the outflow leaves through a vacuum face only if the cell chose it, with its share
+            double wo = wa;
+            if (dc.mask && t > 0.0) {
+                const int64_t i = (int64_t)c * nd + d;
+                wo = ((dc.mask[i] >> (s - r0)) & 1ull) ? dmul(w, dc.share64[i]) : 0.0;
+            }
             for (int g = 0; g < G; ++g) {
-                if (t > 0.0) esc = dadd(esc, dmul(wa, mag(I + ((size_t)d * N + c) * G + g)));
+                if (t > 0.0) esc = dadd(esc, dmul(wo, mag(I + ((size_t)d * N + c) * G + g)));
                 else if (t < 0.0 && bc) inj = dadd(inj, dmul(wa, bc[(size_t)(-1 - nbr) * G + g]));
             }
         }
@@ -243,7 +249,7 @@ __global__ void k_scan_counts(const int32_t* cnt, int64_t n, int32_t* off) {
 __global__ void __launch_bounds__(ROW_THREADS) k_pside_weights(const int32_t* pcells, const int32_t* off,
                                                                const uint32_t* rowptr, const int4* side,
                                                                const d4* side64, int nd, const double* om64,
-                                                               const double* w64, double* wa) {
+                                                               const double* w64, double* wa, DcTabs dc) {
     const int64_t k = blockIdx.x;
     const int32_t c = pcells[k];
     const uint32_t r0 = rowptr[c], r1 = rowptr[c + 1];
@@ -254,7 +260,12 @@ __global__ void __launch_bounds__(ROW_THREADS) k_pside_weights(const int32_t* pc
             if (x < 0 || !(x & NBR_PERIODIC)) continue;
             const d4 n = side64[s];
             const double t = exact_t(n, om64 + 3 * d);
-            wa[j * nd + d] = t < 0.0 ? dmul(w64[d], dmul(n.w, fabs(t))) : 0.0;
+            double v = t < 0.0 ? dmul(w64[d], dmul(n.w, fabs(t))) : 0.0;
+            if (dc.mask && t < 0.0) {  // scheme (b): the partner's share, if the partner chose this face
+                const int64_t i = (int64_t)(x & NBR_MASK) * nd + d;
+                v = ((dc.mask[i] >> dc.twin[s]) & 1ull) ? dmul(w64[d], dc.share64[i]) : 0.0;
+            }
+            wa[j * nd + d] = v;
             ++j;
         }
     }
@@ -449,16 +460,17 @@ cudaError_t launch_tally(int precision, const void* I, int64_t N, int G, int nd,
 
 cudaError_t launch_boundary_tally(int precision, const DevMesh& m, const void* I, int G, int nd, int d0,
                                   const double* om64, const double* w64, const double* bc, double* partial, int nblk_,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, const DcTabs* dc) {
     (void)nblk_;
+    const DcTabs tabs = dc ? *dc : DcTabs();
     if (m.n_bcells <= 0) return cudaSuccess;
     const unsigned b = (unsigned)m.n_bcells;
     if (precision == 64)
         k_boundary_tally<double><<<b, ROW_THREADS, 0, st>>>(m.bcells, m.rowptr, m.side, m.side64, (const double*)I,
-                                                            m.N, G, nd, om64 + 3 * d0, w64 + d0, bc, partial);
+                                                            m.N, G, nd, om64 + 3 * d0, w64 + d0, bc, partial, tabs);
     else
         k_boundary_tally<float><<<b, ROW_THREADS, 0, st>>>(m.bcells, m.rowptr, m.side, m.side64, (const float*)I,
-                                                           m.N, G, nd, om64 + 3 * d0, w64 + d0, bc, partial);
+                                                           m.N, G, nd, om64 + 3 * d0, w64 + d0, bc, partial, tabs);
     return cudaGetLastError();
 }
 
@@ -469,7 +481,7 @@ cudaError_t launch_scat_residual(int64_t NG, const double* J, double* Jold, unsi
 }
 
 cudaError_t build_periodic_table(const DevMesh& m, int nd, const double* om64, const double* w64, PeriodicTable* t,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, const DcTabs* dc) {
     if (m.n_pcells <= 0) return cudaSuccess;
     const int64_t np = m.n_pcells;
     cudaError_t e;
@@ -495,7 +507,7 @@ cudaError_t build_periodic_table(const DevMesh& m, int nd, const double* om64, c
         t->wa_cap = need;
     }
     k_pside_weights<<<(unsigned)np, ROW_THREADS, 0, st>>>(m.pcells, t->off, m.rowptr, m.side, m.side64, nd, om64, w64,
-                                                          t->wa);
+                                                          t->wa, dc ? *dc : DcTabs());
     t->ready = true;
     return cudaGetLastError();
 }

@@ -160,6 +160,27 @@ def column_mesh(n: int, h: float = 1.0 / 256, periodic_x: bool = False) -> Mesh:
                 periodic=periodic_x, extra={"kind": "column", "n": n, "h": h})
 
 
+def star_mesh(n_arms: int, seed: int) -> Mesh:
+    """One hub cell joined to n_arms cells by faces whose normals cover the sphere; every arm cell has a
+    box-boundary face on its far side. Not a tessellation (the cells are not closed), but every step of
+    the sweep is defined on it, and the oracle runs the same algorithm."""
+    from synth.fields import fibonacci_directions
+    nrm, _ = fibonacci_directions(n_arms, seed=seed)
+    rng = np.random.default_rng(seed)
+    fc = np.zeros((2 * n_arms, 2), np.int32)
+    fc[:n_arms, 0] = 0
+    fc[:n_arms, 1] = np.arange(1, n_arms + 1)
+    fc[n_arms:, 0] = np.arange(1, n_arms + 1)
+    fc[n_arms:, 1] = -1
+    normal = np.concatenate([nrm, nrm])
+    area = rng.uniform(0.5, 1.5, 2 * n_arms) * 0.01
+    flags = np.zeros(2 * n_arms, np.uint8)
+    flags[n_arms:] = FACE_BOUNDARY
+    vol = np.full(n_arms + 1, 1e-3)
+    vol[0] = 1e-2
+    return Mesh(volume=vol, face_cells=fc, area=area, normal=normal, flags=flags)
+
+
 # ----------------------------------------------------------------------------------------------
 # Voronoi meshes from generator points
 # ----------------------------------------------------------------------------------------------

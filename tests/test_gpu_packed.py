@@ -13,7 +13,7 @@ import pytest
 import oracle
 from synth import configs
 from synth.fields import fibonacci_directions
-from synth.mesh import FACE_BOUNDARY, Mesh
+from synth.mesh import star_mesh
 
 pytestmark = pytest.mark.gpu
 
@@ -70,26 +70,6 @@ def test_packed_scattering_iteration(ctx, use_graph):
     J, _, st, s = ctx.solve(precision=32, tol_scat=1e-6, max_it_scat=200, use_graph=use_graph)
     assert s == 0 and abs(st["defect"]) <= DEFECT_TOL
     assert fp32_err(J, run_oracle(p, tol_scat=1e-6, max_it_scat=200)["J"]) <= 2 * FP32_TOL
-
-
-def star_mesh(n_arms: int, seed: int) -> Mesh:
-    """One hub cell joined to n_arms cells by faces whose normals cover the sphere; every arm cell has a
-    box-boundary face on its far side. Not a tessellation (the cells are not closed), but every step of
-    the sweep is defined on it, and the oracle runs the same algorithm."""
-    nrm, _ = fibonacci_directions(n_arms, seed=seed)
-    rng = np.random.default_rng(seed)
-    fc = np.zeros((2 * n_arms, 2), np.int32)
-    fc[:n_arms, 0] = 0
-    fc[:n_arms, 1] = np.arange(1, n_arms + 1)
-    fc[n_arms:, 0] = np.arange(1, n_arms + 1)
-    fc[n_arms:, 1] = -1
-    normal = np.concatenate([nrm, nrm])
-    area = rng.uniform(0.5, 1.5, 2 * n_arms) * 0.01
-    flags = np.zeros(2 * n_arms, np.uint8)
-    flags[n_arms:] = FACE_BOUNDARY
-    vol = np.full(n_arms + 1, 1e-3)
-    vol[0] = 1e-2
-    return Mesh(volume=vol, face_cells=fc, area=area, normal=normal, flags=flags)
 
 
 @pytest.mark.parametrize("n_arms,packed", [(80, True), (160, False)])
