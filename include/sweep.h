@@ -222,6 +222,25 @@ sweep_status sweep_levels(sweep_ctx* ctx, int32_t dir, int32_t* level, int32_t* 
  * host pointer. Errors: INVALID_ARG (no solve yet or bad dir). */
 sweep_status sweep_intensity(sweep_ctx* ctx, int32_t dir, double* intensity);
 
+/* Rotation of the direction set between substeps (Sec. 2.6, the rotation paragraph): a radiative-
+ * transfer step may be split into N_rot substeps, each with the sources reduced by 1/N_rot, the
+ * directions rotated after every substep to Omega'_i = R Omega_i (R a rotation, e.g. R_z(phi) R_y(theta)
+ * with randomly drawn spherical angles). Angle-dependent state is carried over by
+ *   I(Omega'_i) = sum_j c_ij I(Omega_j),  c_ij = dS_ij / dS_i,
+ * dS_ij the solid angle that the bin of new direction i shares with the bin of old direction j (a bin:
+ * the part of the unit sphere nearer to its direction than to any other of its set; nearest by the
+ * largest ((px Ox) + (py Oy)) + (pz Oz) in FP64, ties to the lower index) and dS_i = sum_j dS_ij,
+ * taken by a quadrature of n_quad equal-weight points of a Fibonacci sphere
+ * (z_m = 1 - (2m+1)/n_quad, phi_m = m pi (3 - sqrt 5)).
+ *   rotation[3][3]  HOST pointer, row-major; orthonormal with determinant +1 (within 1e-12)
+ *   n_quad          quadrature points, 1 .. 2^26 (0 = 2^16)
+ * The context's directions become Omega'_i = ((R_k0 x + R_k1 y) + R_k2 z) (weights unchanged; cached
+ * levels and operators are rebuilt by the next solve), and the intensities of the last solve are
+ * remapped, so that a following solve with warm_start = 1 starts its periodic iteration from them.
+ * The caller scales the sources by 1/N_rot and sums the substeps' J and Gamma.
+ * Errors: INVALID_ARG (no directions, bad rotation or n_quad), OOM, CUDA. */
+sweep_status sweep_rotate_directions(sweep_ctx* ctx, const double* rotation, int64_t n_quad);
+
 /* Adjoint (transpose) of the sweep for a loss L(J, Gamma). For each direction it solves
  * L_Omega^T lambda = g, g_c = w_d (dL/dGamma_c kappa_a,c V_c + dL/dJ_c / 4pi), as a sweep
  * in reversed level order, and accumulates in FP64

@@ -74,6 +74,8 @@ def _lib():
             lib.oracle_solve.argtypes = [I64, I64, P, P, P, P, P, I32, P, P, I32, P, P, P, P, D, I32, D, I32, P,
                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P,
                                          ctypes.POINTER(Stats)]
+            lib.oracle_remap_coeffs.restype = ctypes.c_int
+            lib.oracle_remap_coeffs.argtypes = [I32, P, P, I64, P]
             lib.oracle_adjoint.restype = ctypes.c_int
             lib.oracle_adjoint.argtypes = [I64, I64, P, P, P, P, P, I32, P, P, I32, P, P, P, P, P, P, D, I32, D,
                                            I32, ctypes.c_int, P, P, P, P]
@@ -177,3 +179,36 @@ def adjoint_full(mesh, omega, weight, kappa_abs, emissivity, kappa_scat=None, dl
                                _ptr(ge), _ptr(gs), _ptr(its))
     return {"rc": rc, "grad_kappa_abs": gk, "grad_emissivity": ge, "grad_kappa_scat": gs,
             "it_forward": int(its[0]), "it_adjoint": int(its[1])}
+
+
+def remap_coeffs(omega_old, omega_new, n_quad: int = 1 << 16):
+    """c[i][j] = dS_ij / dS_i between a direction set and its rotation (the rotation paragraph of
+    Sec. 2.6): the solid angle that the bin of new direction i shares with the bin of old direction j,
+    over the solid angle of bin i, by a Fibonacci-sphere quadrature of n_quad points."""
+    a = _c(omega_old, np.float64).reshape(-1, 3)
+    b = _c(omega_new, np.float64).reshape(-1, 3)
+    D = a.shape[0]
+    c = np.zeros((D, D))
+    rc = _lib().oracle_remap_coeffs(D, _ptr(a), _ptr(b), n_quad, _ptr(c))
+    if rc != OK:
+        raise RuntimeError("oracle_remap_coeffs failed: %d" % rc)
+    return c
+
+
+def rotation(theta: float, phi: float) -> np.ndarray:
+    """R(theta, phi) = R_z(phi) R_y(theta): a rotation by theta about y, then by phi about z (the two
+    spherical angles of the rotation paragraph of Sec. 2.6)."""
+    ct, st, cp, sp = np.cos(theta), np.sin(theta), np.cos(phi), np.sin(phi)
+    ry = np.array([[ct, 0.0, st], [0.0, 1.0, 0.0], [-st, 0.0, ct]])
+    rz = np.array([[cp, -sp, 0.0], [sp, cp, 0.0], [0.0, 0.0, 1.0]])
+    return rz @ ry
+
+
+def rotate(omega, R):
+    """Omega'_i = R Omega_i, each component ((R_k0 x + R_k1 y) + R_k2 z) separately rounded."""
+    om = _c(omega, np.float64).reshape(-1, 3)
+    R = np.asarray(R, np.float64)
+    out = np.empty_like(om)
+    for k in range(3):
+        out[:, k] = (R[k, 0] * om[:, 0] + R[k, 1] * om[:, 1]) + R[k, 2] * om[:, 2]
+    return out

@@ -823,3 +823,59 @@ out:
     if (built) free_sides(&p);
     return rc;
 }
+
+/* ------------------------------------------------------------------------------------------------
+ * Remap coefficients between two direction sets (Sec. 2.6, the rotation paragraph): after the
+ * directions are rotated, an angle-dependent quantity is carried over as
+ *   I(Omega'_i) = sum_j c_ij I(Omega_j),  c_ij = dS_ij / dS_i,
+ * dS_ij the solid angle that the bin of the new direction i shares with the bin of the old direction
+ * j, dS_i = sum_j dS_ij the solid angle of bin i (so every row sums to 1). A direction's bin is the part
+ * of the unit sphere nearer to it than to any other direction of its set. The solid angles are taken
+ * by quadrature: n_quad points of a Fibonacci sphere,
+ *   z_m = 1 - (2m + 1)/n_quad,  phi_m = m pi (3 - sqrt 5),
+ * each of equal weight, each in the bin of the direction with the largest p.Omega
+ * (((px Ox) + (py Oy)) + (pz Oz), separately rounded; ties to the lower index); dS_ij is then
+ * proportional to the number of points in both bin i and bin j.
+ * c_out[n_dir][n_dir] row-major, row i = new direction i.
+ * ------------------------------------------------------------------------------------------------ */
+static int32_t nearest_direction(const double* p, int32_t n_dir, const double* omega) {
+    int32_t best = 0;
+    double bd = -2.0;
+    for (int32_t d = 0; d < n_dir; ++d) {
+        double t = ((p[0] * omega[3 * d]) + (p[1] * omega[3 * d + 1])) + (p[2] * omega[3 * d + 2]);
+        if (t > bd) {
+            bd = t;
+            best = d;
+        }
+    }
+    return best;
+}
+
+int oracle_remap_coeffs(int32_t n_dir, const double* omega_old, const double* omega_new, int64_t n_quad,
+                        double* c_out) {
+    if (n_dir < 1 || n_quad < 1 || !omega_old || !omega_new || !c_out) return OR_ERR_ARG;
+    int64_t* cnt = (int64_t*)calloc((size_t)n_dir * (size_t)n_dir, sizeof(int64_t));
+    int64_t* row = (int64_t*)calloc((size_t)n_dir, sizeof(int64_t));
+    if (!cnt || !row) {
+        free(cnt);
+        free(row);
+        return OR_ERR_MEM;
+    }
+    const double golden = M_PI * (3.0 - sqrt(5.0));
+    for (int64_t m = 0; m < n_quad; ++m) {
+        double z = 1.0 - (2.0 * (double)m + 1.0) / (double)n_quad;
+        double r = sqrt(1.0 - z * z);
+        double ph = (double)m * golden;
+        double p[3] = {r * cos(ph), r * sin(ph), z};
+        int32_t i = nearest_direction(p, n_dir, omega_new);
+        int32_t j = nearest_direction(p, n_dir, omega_old);
+        cnt[(int64_t)i * n_dir + j]++;
+        row[i]++;
+    }
+    for (int32_t i = 0; i < n_dir; ++i)
+        for (int32_t j = 0; j < n_dir; ++j)
+            c_out[(int64_t)i * n_dir + j] = row[i] > 0 ? (double)cnt[(int64_t)i * n_dir + j] / (double)row[i] : 0.0;
+    free(cnt);
+    free(row);
+    return OR_OK;
+}

@@ -33,7 +33,7 @@ OP_FORMATS = {"auto": 0, "lines": 1, "packets": 2}
 EXPORTS = ("sweep_default_opts", "sweep_create", "sweep_destroy", "sweep_set_mesh", "sweep_set_directions",
            "sweep_set_material", "sweep_set_material_dev", "sweep_solve", "sweep_solve_dev", "sweep_levels",
            "sweep_intensity", "sweep_adjoint", "sweep_adjoint_dev", "sweep_status_string", "sweep_last_error",
-           "sweep_levels_noalloc")
+           "sweep_levels_noalloc", "sweep_rotate_directions")
 
 
 class sweep_opts(ctypes.Structure):
@@ -99,6 +99,7 @@ def load(path: str | None = None):
         "sweep_status_string": (ctypes.c_char_p, [S]),
         "sweep_last_error": (ctypes.c_char_p, [P]),
         "sweep_levels_noalloc": (S, [ctypes.c_int, P, I64, I64, P, P, P, P, P, ctypes.POINTER(I32)]),
+        "sweep_rotate_directions": (S, [P, P, I64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -245,6 +246,11 @@ class Context:
         s = self._check(self.lib.sweep_solve_dev(self.h, ctypes.byref(o), _dp(J_out), _dp(Gamma_out),
                                                  ctypes.byref(st)), (SWEEP_OK, SWEEP_NOT_CONVERGED))
         return st.as_dict(), s
+
+    def rotate_directions(self, rotation, n_quad: int = 0):
+        """Rotate the direction set by a 3x3 rotation and remap the last solve's intensities onto it."""
+        R = _host(rotation, np.float64).reshape(3, 3)
+        self._check(self.lib.sweep_rotate_directions(self.h, _hp(R), n_quad))
 
     def levels(self, direction: int):
         lev = np.zeros(self.n_cells, np.int32)

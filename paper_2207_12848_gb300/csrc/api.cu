@@ -1610,6 +1610,115 @@ sweep_status sweep_intensity(sweep_ctx* c, int32_t dir, double* out) {
     return cuda_status(c, e, "copy intensity");
 }
 
+// Rotation of the direction set between substeps (Sec. 2.6, the rotation paragraph), with the remap of the
+// intensities the last solve left (the warm start of the next periodic iteration).
+sweep_status sweep_rotate_directions(sweep_ctx* c, const double* R, int64_t n_quad) {
+    if (!c) return SWEEP_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    if (!c->has_dirs) return bad(c, "set the directions first");
+    if (!R) return bad(c, "null rotation");
+    if (n_quad == 0) n_quad = 1 << 16;
+    if (n_quad < 1 || n_quad > (1ll << 26)) return bad(c, "n_quad must be in [1, 2^26] (0 = 2^16)");
+    // a proper rotation: R^T R = 1 and det R = +1, within 1e-12
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += R[3 * k + a] * R[3 * k + b];
+            if (!(std::fabs(s - (a == b ? 1.0 : 0.0)) <= 1e-12)) return bad(c, "rotation is not orthonormal");
+        }
+    const double det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) +
+                       R[2] * (R[3] * R[7] - R[4] * R[6]);
+    if (!(std::fabs(det - 1.0) <= 1e-12)) return bad(c, "rotation must have determinant +1");
+    const int D = c->D;
+    std::vector<double> om_old(3 * (size_t)D), om_new(3 * (size_t)D), w(D);
+    CK(cudaMemcpy(om_old.data(), c->om64, sizeof(double) * 3 * D, cudaMemcpyDeviceToHost), "read directions");
+    CK(cudaMemcpy(w.data(), c->w64, sizeof(double) * D, cudaMemcpyDeviceToHost), "read directions");
+    for (int d = 0; d < D; ++d)
+        for (int k = 0; k < 3; ++k) {
+            // ((R_k0 x + R_k1 y) + R_k2 z), each product and sum rounded on its own
+            volatile double p0 = R[3 * k] * om_old[3 * d], p1 = R[3 * k + 1] * om_old[3 * d + 1],
+                            p2 = R[3 * k + 2] * om_old[3 * d + 2];
+            om_new[3 * d + k] = (p0 + p1) + p2;
+        }
+    SolveBuf& b = c->sb;
+    const bool remap = b.last >= 0 && b.I[b.last] && b.nd == D;
+    if (remap) {
+        // quadrature points z_m = 1 - (2m+1)/M, phi_m = m pi (3 - sqrt 5) on the unit sphere
+        std::vector<double3> pts((size_t)n_quad);
+        const double golden = M_PI * (3.0 - std::sqrt(5.0));
+        for (int64_t m = 0; m < n_quad; ++m) {
+            const double z = 1.0 - (2.0 * (double)m + 1.0) / (double)n_quad;
+            volatile double zz = z * z;
+            const double r = std::sqrt(1.0 - zz);
+            const double ph = (double)m * golden;
+            pts[(size_t)m] = make_double3(r * std::cos(ph), r * std::sin(ph), z);
+        }
+        DevBuf<double3> d_pts;
+        DevBuf<double> d_new;
+        DevBuf<unsigned long long> d_cnt;
+        CK(cudaMalloc(&d_pts.p, sizeof(double3) * (size_t)n_quad), "alloc quadrature");
+        CK(cudaMalloc(&d_new.p, sizeof(double) * 3 * D), "alloc directions");
+        CK(cudaMalloc(&d_cnt.p, sizeof(unsigned long long) * (size_t)D * D), "alloc counts");
+        CK(cudaMemcpyAsync(d_pts.p, pts.data(), sizeof(double3) * (size_t)n_quad, cudaMemcpyHostToDevice, c->st),
+           "upload");
+        CK(cudaMemcpyAsync(d_new.p, om_new.data(), sizeof(double) * 3 * D, cudaMemcpyHostToDevice, c->st), "upload");
+        CK(cudaMemsetAsync(d_cnt.p, 0, sizeof(unsigned long long) * (size_t)D * D, c->st), "init");
+        CKL(launch_remap_count(d_pts.p, n_quad, c->om64, d_new.p, D, d_cnt.p, c->st), "remap coefficients");
+        std::vector<unsigned long long> cnt((size_t)D * D);
+        CK(cudaMemcpyAsync(cnt.data(), d_cnt.p, sizeof(unsigned long long) * (size_t)D * D, cudaMemcpyDeviceToHost,
+                           c->st), "read counts");
+        CK(cudaStreamSynchronize(c->st), "remap coefficients");
+        // c_ij = dS_ij / dS_i as a sparse matrix by rows (new directions)
+        std::vector<int32_t> rp(D + 1, 0), col;
+        std::vector<double> val;
+        for (int i = 0; i < D; ++i) {
+            unsigned long long row = 0;
+            for (int j = 0; j < D; ++j) row += cnt[(size_t)i * D + j];
+            for (int j = 0; j < D; ++j) {
+                const unsigned long long n = cnt[(size_t)i * D + j];
+                if (!n) continue;
+                col.push_back(j);
+                val.push_back((double)n / (double)row);
+            }
+            rp[i + 1] = (int32_t)col.size();
+        }
+        DevBuf<int32_t> d_rp, d_col;
+        DevBuf<double> d_val;
+        const size_t nnz = col.size() > 0 ? col.size() : 1;
+        CK(cudaMalloc(&d_rp.p, sizeof(int32_t) * (D + 1)), "alloc remap");
+        CK(cudaMalloc(&d_col.p, sizeof(int32_t) * nnz), "alloc remap");
+        CK(cudaMalloc(&d_val.p, sizeof(double) * nnz), "alloc remap");
+        CK(cudaMemcpyAsync(d_rp.p, rp.data(), sizeof(int32_t) * (D + 1), cudaMemcpyHostToDevice, c->st), "upload");
+        CK(cudaMemcpyAsync(d_col.p, col.data(), sizeof(int32_t) * col.size(), cudaMemcpyHostToDevice, c->st), "upload");
+        CK(cudaMemcpyAsync(d_val.p, val.data(), sizeof(double) * val.size(), cudaMemcpyHostToDevice, c->st), "upload");
+        // remap the last solve's intensities into the other buffer, which becomes the last one
+        const int src = b.last, dst = 1 - b.last;
+        if (!b.I[dst]) {
+            CK(cudaMalloc(&b.I[dst], b.bytes > 0 ? b.bytes : 4), "alloc intensities");
+            b.sign[dst] = 0;
+        }
+        const int64_t NG = b.N * (int64_t)b.G;
+        CKL(launch_remap(b.prec, b.I[src], b.I[dst], NG, D, d_rp.p, d_col.p, d_val.p, b.sign[dst], c->st), "remap");
+        CK(cudaStreamSynchronize(c->st), "remap");
+        b.last = dst;
+    }
+    // the rotated set replaces the directions (weights unchanged); levels and operators are rebuilt
+    std::vector<float4> o32(D), o32lo(D);
+    for (int d = 0; d < D; ++d) {
+        const double* x = om_new.data() + 3 * d;
+        o32[d] = make_float4((float)x[0], (float)x[1], (float)x[2], (float)w[d]);
+        o32lo[d] = make_float4((float)(x[0] - (double)o32[d].x), (float)(x[1] - (double)o32[d].y),
+                               (float)(x[2] - (double)o32[d].z), 0.f);
+    }
+    CK(cudaMemcpy(c->om64, om_new.data(), sizeof(double) * 3 * D, cudaMemcpyHostToDevice), "upload directions");
+    CK(cudaMemcpy(c->om32, o32.data(), sizeof(float4) * D, cudaMemcpyHostToDevice), "upload directions");
+    CK(cudaMemcpy(c->om32lo, o32lo.data(), sizeof(float4) * D, cudaMemcpyHostToDevice), "upload directions");
+    c->lev.valid = false;
+    c->lev.op_valid = false;
+    c->adj_lev.valid = false;
+    return SWEEP_OK;
+}
+
 sweep_status sweep_adjoint(sweep_ctx* c, const sweep_opts* o, const double* dlj, const double* dlg, double* gk,
                            double* ge, double* gks, sweep_stats* st) {
     return adjoint_impl(c, o, dlj, dlg, gk, ge, gks, false, st);

@@ -488,6 +488,11 @@ cudaError_t launch_grad_accum(int precision, const void* I, const void* lam, int
                               const double* w64, const double* vol, const double* dl_dG, double* gk, double* ge,
                               cudaStream_t st);
 cudaError_t launch_fill_u32(uint32_t* p, uint32_t v, int64_t n, cudaStream_t st);
+// rotation of the direction set: quadrature counts of the shared bins, and the remap of [D][NG] intensities
+cudaError_t launch_remap_count(const double3* pts, int64_t n, const double* om_old, const double* om_new, int n_dir,
+                               unsigned long long* cnt, cudaStream_t st);
+cudaError_t launch_remap(int precision, const void* in, void* out, int64_t NG, int n_dir, const int32_t* rp,
+                         const int32_t* col, const double* val, int par, cudaStream_t st);
 cudaError_t launch_to_f64(int precision, const void* I, int64_t n, double* out, cudaStream_t st);
 
 }  // namespace sw

@@ -588,3 +588,79 @@ cudaError_t launch_to_f64(int precision, const void* I, int64_t n, double* out, 
 }
 
 }  // namespace sw
+
+// ---------------------------------------------------------------------------------------------
+// Rotation of the direction set (the rotation paragraph of Sec. 2.6): the remap coefficients
+// c_ij = dS_ij / dS_i between the bins of the new directions i and the old directions j, by a
+// quadrature of equal-weight points on the unit sphere, and the remap of the stored intensities
+// I(Omega'_i) = sum_j c_ij I(Omega_j).
+// ---------------------------------------------------------------------------------------------
+namespace sw {
+namespace {
+
+// the direction (of n_dir) nearest to p: largest ((px Ox) + (py Oy)) + (pz Oz), ties to the lower index
+__device__ __forceinline__ int nearest_dir(const double3 p, const double* om, int n_dir) {
+    int best = 0;
+    double bd = -2.0;
+    for (int d = 0; d < n_dir; ++d) {
+        const double t = __dadd_rn(__dadd_rn(__dmul_rn(p.x, om[3 * d]), __dmul_rn(p.y, om[3 * d + 1])),
+                                   __dmul_rn(p.z, om[3 * d + 2]));
+        if (t > bd) {
+            bd = t;
+            best = d;
+        }
+    }
+    return best;
+}
+
+__global__ void k_remap_count(const double3* pts, int64_t n, const double* om_old, const double* om_new, int n_dir,
+                              unsigned long long* cnt) {
+    extern __shared__ double s_om[];  // [2][n_dir][3]
+    for (int i = threadIdx.x; i < 6 * n_dir; i += blockDim.x) s_om[i] = i < 3 * n_dir ? om_new[i] : om_old[i - 3 * n_dir];
+    __syncthreads();
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    const double3 p = pts[m];
+    const int i = nearest_dir(p, s_om, n_dir);
+    const int j = nearest_dir(p, s_om + 3 * n_dir, n_dir);
+    atomicAdd(&cnt[(int64_t)i * n_dir + j], 1ull);
+}
+
+// out[i][c][g] = sum over the nonzeros (j, c_ij) of row i of c_ij |in[j][c][g]|, written with the sign
+// bit `par` (the parity the buffer's values carry); one thread per (cell, group) element
+template <typename real>
+__global__ void k_remap(const real* in, real* out, int64_t NG, int n_dir, const int32_t* rp, const int32_t* col,
+                        const double* val, int par) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= NG) return;
+    for (int i = 0; i < n_dir; ++i) {
+        double acc = 0.0;
+        for (int k = rp[i]; k < rp[i + 1]; ++k)
+            acc = __dadd_rn(acc, __dmul_rn(val[k], fabs((double)in[(int64_t)col[k] * NG + e])));
+        const real v = (real)acc;
+        out[(int64_t)i * NG + e] = par ? -v : v;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_remap_count(const double3* pts, int64_t n, const double* om_old, const double* om_new, int n_dir,
+                               unsigned long long* cnt, cudaStream_t st) {
+    if (n > 0)
+        k_remap_count<<<(unsigned)((n + 255) / 256), 256, sizeof(double) * 6 * n_dir, st>>>(pts, n, om_old, om_new,
+                                                                                            n_dir, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_remap(int precision, const void* in, void* out, int64_t NG, int n_dir, const int32_t* rp,
+                         const int32_t* col, const double* val, int par, cudaStream_t st) {
+    if (NG <= 0) return cudaSuccess;
+    const unsigned b = (unsigned)((NG + 255) / 256);
+    if (precision == 64)
+        k_remap<double><<<b, 256, 0, st>>>((const double*)in, (double*)out, NG, n_dir, rp, col, val, par);
+    else
+        k_remap<float><<<b, 256, 0, st>>>((const float*)in, (float*)out, NG, n_dir, rp, col, val, par);
+    return cudaGetLastError();
+}
+
+}  // namespace sw

@@ -672,3 +672,49 @@ def test_every_option_against_its_dense_solve(seed, box):
                 assert rel(r["I"], I) <= 1e-11, (law, dc_n, ks is not None)
                 assert abs(r["stats"]["defect"]) <= 1e-12
 
+
+
+# ---- remap coefficients of a rotated direction set (Sec. 2.6, the rotation paragraph) ---------------------
+def test_remap_identity_and_row_sums():
+    om, _ = fibonacci_directions(24, seed=4)
+    assert np.array_equal(oracle.remap_coeffs(om, om), np.eye(24))
+    c = oracle.remap_coeffs(om, oracle.rotate(om, oracle.rotation(0.7, 2.1)))
+    assert (c >= 0).all()
+    assert np.max(np.abs(c.sum(1) - 1.0)) <= 1e-14
+    assert np.count_nonzero(c) < 24 * 10  # a rotated bin overlaps only a few old bins
+
+
+def test_remap_two_antipodal_directions():
+    # the bins of +z and -z are the hemispheres; a quarter turn about x makes the new bins the hemispheres
+    # of -y and +y, each of which shares exactly half of its solid angle with each old bin
+    om = np.array([[0.0, 0.0, 1.0], [0.0, 0.0, -1.0]])
+    R = np.array([[1.0, 0.0, 0.0], [0.0, 0.0, -1.0], [0.0, 1.0, 0.0]])
+    c = oracle.remap_coeffs(om, oracle.rotate(om, R))
+    assert np.max(np.abs(c - 0.5)) <= 1e-3
+
+
+def test_remap_of_a_symmetry_is_a_permutation():
+    # a quarter turn about z maps the six axis directions onto themselves: the bins coincide
+    om = np.concatenate([np.eye(3), -np.eye(3)])
+    R = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+    new = oracle.rotate(om, R)
+    perm = np.array([int(np.argmax(om @ v)) for v in new])
+    c = oracle.remap_coeffs(om, new)
+    assert np.array_equal(c, np.eye(6)[perm])
+
+
+def test_remap_against_monte_carlo():
+    # brute force with independent code: random points on the sphere, each in the bin of its nearest
+    # direction of either set
+    om, _ = fibonacci_directions(16, seed=2)
+    new = oracle.rotate(om, oracle.rotation(1.1, 4.0))
+    c = oracle.remap_coeffs(om, new, n_quad=1 << 18)
+    rng = np.random.default_rng(3)
+    p = rng.normal(size=(1_000_000, 3))
+    p /= np.linalg.norm(p, axis=1)[:, None]
+    i = np.argmax(p @ new.T, axis=1)
+    j = np.argmax(p @ om.T, axis=1)
+    cnt = np.zeros((16, 16))
+    np.add.at(cnt, (i, j), 1.0)
+    mc = cnt / cnt.sum(1, keepdims=True)
+    assert np.max(np.abs(c - mc)) <= 6e-3
