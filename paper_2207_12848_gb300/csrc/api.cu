@@ -1557,6 +1557,17 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
     S.t_ms[2] = t_sweep;
     S.t_ms[4] = ttot;
     S.updates = (double)N * D * G * (it_fwd + 2.0 * it_adj);  // forward, transposed over 2G split groups
+    {
+        const Levels& Ld = B == D ? c->lev : c->adj_lev;  // depths of the (last) batch levelised
+        int dmaxv = 0;
+        double dsum = 0;
+        for (int d : Ld.depth) {
+            dmaxv = std::max(dmaxv, d);
+            dsum += d;
+        }
+        S.depth_max = dmaxv;
+        S.depth_mean = Ld.depth.empty() ? 0.0 : dsum / Ld.depth.size();
+    }
     S.updates_per_s = ttot > 0 ? S.updates / (ttot * 1e-3) : 0.0;
     S.schedule_used = plain ? SWEEP_SCHED_PLAIN : sched;
     S.kernel_used = c->last_kernel;
