@@ -118,6 +118,7 @@ void free_levels(Levels& L) {
     dfree(L.lev_chunk); dfree(L.seg_off); dfree(L.op); dfree(L.dlev);
     dfree(L.pk); dfree(L.pk_meta); dfree(L.lev_pk); dfree(L.pk_grp); dfree(L.pk_cnt); dfree(L.pk_off); dfree(L.pk_scan);
     dfree(L.pk_flag);
+    dfree(L.lfill);
     dfree(L.dc_mask); dfree(L.dc_inm); dfree(L.dc_share32); dfree(L.dc_share64);
     L = Levels();
 }
@@ -1027,7 +1028,9 @@ sweep_status autotune(sweep_ctx* c, int prec, const void* cm, const float* bc32,
     std::vector<LaunchCfg> cand;
     if (fmt == OPF_PACKETS) {
         // packets per warp step: one (lanes 32) or two (lanes 64); the level-synchronous form with two
+        // (three resident blocks per SM: fewer polling warps compete with the ones that have work)
         cand.push_back({SWEEP_SCHED_DATAFLOW, 256, 64, 0});
+        cand.push_back({SWEEP_SCHED_DATAFLOW, 256, 64, 3});
         cand.push_back({SWEEP_SCHED_DATAFLOW, 256, 32, 0});
         cand.push_back({SWEEP_SCHED_LEVEL, 256, 64, 0});
     } else if (fmt == OPF_LINES) {

@@ -183,6 +183,9 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ int ld_volatile_i32(const int* p) { return *(const volatile int*)p; }
+__device__ __forceinline__ void st_relaxed_i32(int* p, int v) {
+    asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ int ld_relaxed_i32(const int* p) {
     int v;
     asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p));
@@ -373,6 +376,7 @@ struct Levels {
     // in that direction's list, for up to dlev_cap levels; then level-0 sizes, depths, overflow word
     int32_t* dlev = nullptr;     // [nd][2][dlev_cap] + [nd] + [nd] + [1]
     int dlev_cap = 0;
+    int32_t* lfill = nullptr;    // [nd][dlev_cap] positions taken within each level while ordering the lists
 };
 
 // Kernel argument block of the batched sweep.

@@ -705,7 +705,8 @@ struct DirLevArgs {
 // Per level and task: the side records of the cell's row (classified in registers: sign of n.Omega
 // as in the classification) and, for each downwind interior neighbour, one atomic on its counter
 // together with a load of that neighbour's row bounds, so a cell released here enters the next
-// level's list with its row already known: two dependent memory round trips per level.
+// level's list with its row already known (and its row prefetched into L2 by the bulk-copy engine, so
+// the next level's record loads are L2 hits): two dependent memory round trips per level.
 __global__ void __launch_bounds__(LD_THREADS, 1) k_levelise_dir(DirLevArgs a) {
     extern __shared__ uint32_t s_lists[];  // [2][LD_Q][3]
     __shared__ int s_next;
@@ -792,6 +793,10 @@ __global__ void __launch_bounds__(LD_THREADS, 1) k_levelise_dir(DirLevArgs a) {
                             qn[3 * p + 1] = (uint32_t)nr[k].x;
                             qn[3 * p + 2] = (uint32_t)nr[k].y;
                         }
+                        // its side records are read on the next level: start pulling them into L2 now
+                        if (nr[k].y > nr[k].x)
+                            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.side + nr[k].x),
+                                         "r"((uint32_t)(nr[k].y - nr[k].x) * 16u));
                     }
                 }
             }
@@ -805,6 +810,26 @@ __global__ void __launch_bounds__(LD_THREADS, 1) k_levelise_dir(DirLevArgs a) {
         if (threadIdx.x == 0) a.depth[d] = L;
         __syncthreads();
     }
+}
+
+// Each direction's level-ordered list rewritten with the cells of every level in cell order (the mesh's
+// Hilbert order, so the tasks of a level that share upwind cells lie close together in the sweep):
+// threads over (direction, cell) in cell order take the next position of their level.
+__global__ void k_order_levels(int64_t N, int nd, int cap, const int32_t* level, const int32_t* dbase,
+                               int32_t* fill, uint32_t* dlist) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t tot = N * (int64_t)nd;
+    const int64_t d = t < tot ? t / N : -1, c = t - d * N;
+    int L = t < tot ? level[t] : -1;
+    if (L >= cap) L = -1;  // negative: never levelised (a cycle) or past the tables
+    // lanes of one direction and level take consecutive positions with one atomic, in lane (cell) order
+    const int64_t key = L < 0 ? -1 : d * cap + L;
+    const unsigned same = __match_any_sync(0xffffffffu, key);
+    const int lane = threadIdx.x & 31, lead = __ffs(same) - 1;
+    int p = 0;
+    if (lane == lead && key >= 0) p = atomicAdd(&fill[key], __popc(same));
+    p = __shfl_sync(0xffffffffu, p, lead) + __popc(same & ((1u << lane) - 1u));
+    if (key >= 0) dlist[d * N + dbase[key] + p] = (uint32_t)c;
 }
 
 // Cells on each level over all directions (lvl_cnt[L]) for L < n_levels.
@@ -1380,6 +1405,13 @@ cudaError_t levelise_by_direction(const DevMesh& m, Levels& L, const float4* om3
         cudaMemsetAsync(L.pad_off, 0, sizeof(uint32_t), st);
         return cudaMemsetAsync(L.lev_chunk, 0, sizeof(int64_t), st);
     }
+    // the cells of each (direction, level) in cell order
+    if (!L.lfill) {
+        if ((e = cudaMalloc(&L.lfill, sizeof(int32_t) * (size_t)nd * cap))) return e;
+    }
+    if ((e = cudaMemsetAsync(L.lfill, 0, sizeof(int32_t) * (size_t)nd * cap, st))) return e;
+    const int64_t tot = m.N * (int64_t)nd;
+    if (tot > 0) k_order_levels<<<nblk(tot), 256, 0, st>>>(m.N, nd, cap, L.level, dbase, L.lfill, L.raw);
     e = ensure_seg(L, nlev);
     if (e != cudaSuccess) return e;
     k_level_totals<<<nblk(nlev), 256, 0, st>>>(dcnt, depth, nd, cap, nlev, L.lvl_cnt);
