@@ -382,6 +382,27 @@ def run_ours(args, dist: Dist):
             "speedup_fp64_batched_vs_plain": stp["t_sweep_ms"] / st64["t_sweep_ms"],
             "plain_launches": stp["kernel_launches"]}
 
+    if dist.rank == 0 and not args.quick and args.law == "balance" and args.transport == 0:
+        # the same box under the EXP law and under scheme (b) (direction-conserving to 3 neighbours): one
+        # step each as timed above (classify, levelise, assemble, periodic iteration to 1e-6)
+        for key, kw, law in (("exp_law", dict(law="exp"), "exp"), ("scheme_b", dict(transport=3), "balance")):
+            ok = default_opts(precision=32, relevel=1, tol_pbc=1e-6, max_it_pbc=200, tol_scat=1e-6, max_it_scat=200,
+                              **kw)
+            ctx.solve_dev(J, Gm, ok)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sx, _ = ctx.solve_dev(J, Gm, ok)
+            torch.cuda.synchronize()
+            tx = time.perf_counter() - t0
+            swm = sx["t_sweep_ms"] / max(1, sx["sweep_launches"])
+            extra[key] = {"value": sx["updates"] / tx, "unit": "updates/s", "ms_per_step": 1e3 * tx,
+                          "roofline": _roof(p, swm, peaks, KERNELS.get(sx["kernel_used"], "?"), law),
+                          "solve": {"it_pbc": sx["it_pbc"], "n_sweeps": sx["n_sweeps"], "defect": sx["defect"],
+                                    "depth_max": sx["depth_max"], "depth_mean": sx["depth_mean"],
+                                    "depth_max_scheme_a": last["depth_max"], "classify_ms": sx["t_classify_ms"],
+                                    "levelise_ms": sx["t_levelise_ms"], "assemble_ms": sx["t_assemble_ms"],
+                                    "sweep_ms_per_launch": swm}}
+
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -502,13 +523,26 @@ def _timed(stream, fn, steps: int, warmup: int):
     return ev0.elapsed_time(ev1) / 1e3, outs
 
 
-def _roof(p, sweep_ms: float, peaks: dict, kernel: str) -> dict:
-    bpu, fbar = bytes_per_update(p)
+def _roof(p, sweep_ms: float, peaks: dict, kernel: str, law: str = "balance") -> dict:
+    bpu, fbar = bytes_per_update(p, law)
     upd = p.mesh.n_cells * p.n_dir * p.n_groups
     ach = bpu * upd / (sweep_ms / 1e3) / 1e9
     return {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": ach / peaks["hbm_gbs"], "peak_source": peaks["source"], "bytes_per_update": bpu,
             "avg_launch_ms": sweep_ms}
+
+
+def _roof_sweeps(p, sweep_ms_total: float, n_sweeps: int, updates: float, peaks: dict, kernel: str) -> dict:
+    """Roofline over sweeps of different group counts (the adjoint: forward sweeps over G groups, transposed
+    sweeps over 2G split groups): per sweep every task reads its row (8 B + 16 B per face side), per
+    update the source pair and the write (12 B)."""
+    m = p.mesh
+    fbar = (2 * m.n_faces - int((m.face_cells[:, 1] < 0).sum())) / m.n_cells
+    alg = m.n_cells * p.n_dir * (8.0 + 16.0 * fbar) * n_sweeps + 12.0 * updates
+    ach = alg / (sweep_ms_total / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / peaks["hbm_gbs"], "peak_source": peaks["source"], "bytes_per_update": alg / updates,
+            "avg_launch_ms": sweep_ms_total / max(1, n_sweeps)}
 
 
 def _solve_entry(name: str, workload: str, p, ctx, stream, opts, steps: int, warmup: int, peaks: dict) -> dict:
@@ -607,20 +641,36 @@ def adjoint_entry(args, stream, peaks: dict, steps: int, warmup: int, cpu: bool 
         J = torch.empty((N, G), dtype=torch.float64, device="cuda")
         Gm = torch.empty_like(J)
         ctx.solve_dev(J, Gm, default_opts(precision=32))
+        sf, _ = ctx.solve_dev(J, Gm, default_opts(precision=32))  # the forward sweep alone, for comparison
         dg = 2.0 * (Gm - torch.from_numpy(T).cuda())
         gk, ge = torch.empty_like(J), torch.empty_like(J)
         opts = default_opts(precision=32)
         dt, outs = _timed(stream, lambda: ctx.adjoint_dev(gk, ge, None, dg, opts), steps, warmup)
         upd = sum(o["updates"] for o in outs)
         sweeps = sum(o["n_sweeps"] for o in outs)
-        sweep_ms = sum(o["t_sweep_ms"] for o in outs) / max(1, sweeps)
+        t_sw = sum(o["t_sweep_ms"] for o in outs)
         st = outs[-1]
         e = {"config": "5 (differentiation)", "workload": WORKLOADS["adjoint"], "n_cells": N, "n_dir": D,
              "n_groups": G, "steps": steps, "value": upd / dt, "unit": "updates/s", "ms_per_step": 1e3 * dt / steps,
-             "dtype": "f32", "roofline": _roof(p, sweep_ms, peaks, KERNELS.get(st["kernel_used"], "?")),
+             "dtype": "f32", "roofline": _roof_sweeps(p, t_sw, sweeps, upd, peaks, KERNELS.get(st["kernel_used"], "?")),
              "gpu_launches": sum(o["kernel_launches"] for o in outs),
              "solve": {"depth_max": st["depth_max"], "forward_sweeps": st["it_scat"], "transposed_passes": st["it_pbc"],
-                       "sweeps": st["n_sweeps"], "sweep_ms_per_launch": sweep_ms}}
+                       "sweeps": st["n_sweeps"], "sweep_ms_per_launch": t_sw / max(1, sweeps),
+                       "assemble_ms": st["t_assemble_ms"]}}
+        e["forward_roofline"] = _roof(p, sf["t_sweep_ms"] / max(1, sf["sweep_launches"]), peaks,
+                                      KERNELS.get(sf["kernel_used"], "?"))
+        # accuracy of the FP32 gradients against the FP64 adjoint of the same inputs
+        gk64, ge64 = torch.empty_like(J), torch.empty_like(J)
+        ctx.adjoint_dev(gk64, ge64, None, dg, default_opts(precision=64))
+        acc = {}
+        for name, a, b in (("grad_kappa_abs", gk, gk64), ("grad_emissivity", ge, ge64)):
+            a, b = a.cpu().numpy(), b.cpu().numpy()
+            big = np.abs(b) >= 1e-3 * np.abs(b).max()
+            rel = np.abs(a[big] - b[big]) / np.abs(b[big])
+            acc[name] = {"max_abs_err_over_max": float(np.abs(a - b).max() / np.abs(b).max()),
+                         "rel_err_p50": float(np.percentile(rel, 50)), "rel_err_p99": float(np.percentile(rel, 99)),
+                         "rel_err_max": float(rel.max()), "outputs_compared": int(big.sum())}
+        e["fp32_vs_fp64"] = acc
         dgh = dg.cpu().numpy()
         if e2e:
             # through the host-pointer call: the loss gradient in, both gradients out, copies included

@@ -116,8 +116,10 @@ void dfree(T*& p) {
 void free_levels(Levels& L) {
     dfree(L.raw); dfree(L.task); dfree(L.trec); dfree(L.info); dfree(L.level); dfree(L.lvl_cnt); dfree(L.pad_off);
     dfree(L.lev_chunk); dfree(L.seg_off); dfree(L.op); dfree(L.dlev);
-    dfree(L.pk); dfree(L.pk_meta); dfree(L.lev_pk); dfree(L.pk_grp); dfree(L.pk_cnt); dfree(L.pk_off); dfree(L.pk_scan);
-    dfree(L.pk_flag);
+    for (PackedOp* P : {&L.pk, &L.pkt}) {
+        dfree(P->pk); dfree(P->meta); dfree(P->lev_pk); dfree(P->grp); dfree(P->lev_grp); dfree(P->cnt);
+        dfree(P->off); dfree(P->scan); dfree(P->flag);
+    }
     dfree(L.lfill);
     dfree(L.dc_mask); dfree(L.dc_inm); dfree(L.dc_share32); dfree(L.dc_share64);
     L = Levels();
@@ -155,6 +157,8 @@ sweep_status alloc_levels(sweep_ctx* c, Levels& L, int d0, int nd) {
     const int64_t N = c->mesh.N;
     if (L.nd == nd && L.raw && L.d0 == d0) {
         L.valid = false;
+        L.op_valid = false;
+        L.pkt.valid = false;
         return SWEEP_OK;
     }
     free_levels(L);
@@ -269,21 +273,30 @@ struct ScopedEvent {
     operator cudaEvent_t() const { return e; }
 };
 
+// cell update of the packed kernel for these arguments
+int pk_mode(const SweepArgs& a) { return a.reverse ? PK_TRANSPOSED : (a.law ? PK_EXP : PK_BALANCE); }
+
 SweepArgs make_args(sweep_ctx* c, const Levels& L, int precision, const void* cm, void* I, const void* Iprev,
                     int G, int parity, int reverse, int level_sync, const sweep_opts* o) {
     SweepArgs a;
     memset(&a, 0, sizeof a);
     a.task = L.task;
     a.trec = L.trec;
-    // the EXP law runs in the generic and plain kernels; the adjoint takes BALANCE
+    // the EXP law runs in the packed, generic and plain kernels; the adjoint takes BALANCE
     a.law = (!reverse && o) ? o->law : SWEEP_LAW_BALANCE;
     a.Imean = a.law ? c->Imean : nullptr;
-    const bool opr = precision == 32 && !reverse && !a.law && L.op_valid && !(o && o->geometry_only);
-    a.op = opr && L.op_format == OPF_LINES ? L.op : nullptr;
-    a.pk = opr && L.op_format == OPF_PACKETS ? L.pk : nullptr;
-    a.pk_meta = L.pk_meta;
-    a.n_pk = L.n_pk;
-    a.lev_pk = L.lev_pk;
+    const bool opr = precision == 32 && !(o && o->geometry_only);
+    // forward: the assembled operator of the levels; transposed: the packed transposed operator
+    const PackedOp* P = nullptr;
+    if (opr && !reverse && L.op_valid && L.op_format == OPF_PACKETS) P = &L.pk;
+    if (opr && reverse && L.pkt.valid) P = &L.pkt;
+    a.op = opr && !reverse && !a.law && L.op_valid && L.op_format == OPF_LINES ? L.op : nullptr;
+    if (P) {
+        a.pk = P->pk;
+        a.pk_meta = P->meta;
+        a.n_pk = P->n_pk;
+        a.lev_pk = P->lev_pk;
+    }
     if (L.transport > 0 && !reverse) {
         a.dc_mask = L.dc_mask;
         a.dc_share32 = L.dc_share32;
@@ -341,11 +354,10 @@ sweep_status run_sweep(sweep_ctx* c, const Levels& L, int precision, int schedul
             }
         }
     } else {
-        // the EXP law runs in the generic kernel, whose occupancy the reverse query gives
         const int fmt = a.pk ? OPF_PACKETS : (a.op ? OPF_LINES : OPF_NONE);
-        // the EXP law and scheme (b) without an assembled operator run in the generic kernel
-        const bool generic = a.reverse || a.law || (a.dc_mask && fmt == OPF_NONE);
-        int per_sm = sweep_occupancy(precision, a.G, threads, L.nd, lanes, generic, fmt);
+        // without an assembled operator the adjoint, the EXP law and scheme (b) run in the generic kernel
+        const bool generic = fmt == OPF_NONE && (a.reverse || a.law || a.dc_mask);
+        int per_sm = sweep_occupancy(precision, a.G, threads, L.nd, lanes, generic, fmt, pk_mode(a));
         if (per_sm < 1) return bad(c, "sweep kernel does not fit on an SM");
         if (bpsm > 0 && bpsm < per_sm) per_sm = bpsm;
         a.level_sync = schedule == SWEEP_SCHED_LEVEL ? 1 : 0;
@@ -453,9 +465,11 @@ sweep_status graph_loop(sweep_ctx* c, const sweep_opts& o, int prec, const void*
     if (s != SWEEP_OK) return s;
     cudaStream_t gs = c->gst;
     IterHost* hp = reinterpret_cast<IterHost*>(c->hpin);
-    const int fmt = (prec == 32 && !o.law && c->lev.op_valid && !o.geometry_only) ? c->lev.op_format : OPF_NONE;
-    const bool generic = o.law || (c->lev.transport > 0 && fmt == OPF_NONE);
-    int per_sm = sweep_occupancy(prec, G, threads, c->lev.nd, lanes, generic ? 1 : 0, fmt);
+    int fmt = (prec == 32 && c->lev.op_valid && !o.geometry_only) ? c->lev.op_format : OPF_NONE;
+    if (o.law && fmt == OPF_LINES) fmt = OPF_NONE;  // the EXP law: packets or the mesh rows
+    const bool generic = fmt == OPF_NONE && (o.law || c->lev.transport > 0);
+    int per_sm = sweep_occupancy(prec, G, threads, c->lev.nd, lanes, generic ? 1 : 0, fmt,
+                                 o.law ? PK_EXP : PK_BALANCE);
     if (per_sm < 1) return bad(c, "sweep kernel does not fit on an SM");
     if (bpsm > 0 && bpsm < per_sm) per_sm = bpsm;
     const int period = pbc ? 4 : 2;
@@ -871,12 +885,12 @@ DcTabs dc_tabs(sweep_ctx* c, const Levels& L) {
 
 // Form of the assembled operator a solve with these options sweeps over (OPF_NONE: it reads the mesh).
 int wanted_format(sweep_ctx* c, const Levels& L, const sweep_opts* o, int prec) {
-    if (prec != 32 || !o || o->law != SWEEP_LAW_BALANCE || o->geometry_only || o->schedule == SWEEP_SCHED_PLAIN)
-        return OPF_NONE;
+    if (prec != 32 || !o || o->geometry_only || o->schedule == SWEEP_SCHED_PLAIN) return OPF_NONE;
     const int G = c->G;
     const bool pk_ok = (G == 1 || G == 2 || G == 4) && (uint64_t)c->mesh.N * (uint64_t)L.nd <= (1ull << 31);
-    if (L.transport > 0)  // scheme (b): its shares live in the packets; otherwise the mesh-row kernel
-        return pk_ok ? OPF_PACKETS : OPF_NONE;
+    // scheme (b) (its shares live in the packets) and the EXP law have the packed form only; otherwise
+    // the mesh-row kernel
+    if (L.transport > 0 || o->law != SWEEP_LAW_BALANCE) return pk_ok ? OPF_PACKETS : OPF_NONE;
     if (pk_ok && (o->op_format == SWEEP_OP_PACKETS || (o->op_format == SWEEP_OP_AUTO && o->lanes_per_task == 0)))
         return OPF_PACKETS;
     return OPF_LINES;
@@ -887,6 +901,60 @@ bool op_fits(size_t bytes) {
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     return bytes + (size_t)(2ull << 30) <= free_b;
+}
+
+// Plans and writes a packed operator of the levels L (transposed: the adjoint's), growing its buffers
+// when device memory allows; false when it does not fit or a task has more entries than a packet holds.
+bool build_packed(sweep_ctx* c, Levels& L, PackedOp& P, bool transposed) {
+    int64_t n_pk = 0;
+    if (pack_plan(c->mesh, L, P, transposed, c->om64, c->om32, c->om32lo, c->st, &n_pk) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    c->launches += 2;  // count pass, scan
+    bool ok = n_pk >= 0;  // < 0: a task has more entries than a packet holds
+    if (ok && n_pk > P.cap) {
+        dfree(P.pk);
+        dfree(P.meta);
+        P.cap = 0;
+        const int64_t cap = n_pk + n_pk / 16 + 64;
+        ok = op_fits((size_t)cap * 520) && cudaMalloc(&P.pk, (size_t)cap * 512) == cudaSuccess &&
+             cudaMalloc(&P.meta, (size_t)cap * 8) == cudaSuccess;
+        if (ok) P.cap = cap;
+        else {
+            cudaGetLastError();
+            dfree(P.pk);
+            dfree(P.meta);
+        }
+    }
+    if (!ok) return false;
+    if (pack_write(c->mesh, L, P, transposed, c->om64, c->om32, c->om32lo, c->st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    c->launches += 1;  // write pass
+    P.n_pk = n_pk;
+    return true;
+}
+
+// The packed transposed operator of the cached levels for the FP32 adjoint sweep (2G = 2 or 4 split
+// groups, the packed kernel's widths), built once per levelisation; without it (memory, rows longer
+// than a packet, other group counts) the transposed sweep reads the mesh rows.
+sweep_status ensure_transposed(sweep_ctx* c, Levels& L, const sweep_opts* o, int prec, float* t_ms) {
+    const int G2 = 2 * c->G;
+    if (prec != 32 || (o && (o->geometry_only || o->schedule == SWEEP_SCHED_PLAIN)) || (G2 != 2 && G2 != 4) ||
+        (uint64_t)c->mesh.N * (uint64_t)L.nd > (1ull << 31) || L.transport > 0)
+        return SWEEP_OK;
+    if (L.pkt.valid) return SWEEP_OK;
+    ScopedEvent e0, e1;
+    cudaEventRecord(e0, c->st);
+    L.pkt.valid = build_packed(c, L, L.pkt, true);
+    cudaEventRecord(e1, c->st);
+    CK(cudaEventSynchronize(e1), "assemble transposed operator");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (t_ms) *t_ms += ms;
+    return SWEEP_OK;
 }
 
 // Assembles the transport operator of the levelised directions in the form the solve sweeps over
@@ -901,27 +969,8 @@ sweep_status ensure_operator(sweep_ctx* c, Levels& L, const sweep_opts* o, int p
     if (want == OPF_PACKETS) {
         dfree(L.op);  // the other form's buffer
         L.op_bytes = 0;
-        int64_t n_pk = 0;
-        CKL(pack_plan(c->mesh, L, c->om64, c->om32, c->om32lo, c->st, &n_pk), "plan packed operator");
-        bool ok = n_pk >= 0;  // < 0: a task has more inflow sides than a packet holds
-        if (ok && n_pk > L.pk_cap) {
-            dfree(L.pk);
-            dfree(L.pk_meta);
-            L.pk_cap = 0;
-            const int64_t cap = n_pk + n_pk / 16 + 64;
-            ok = op_fits((size_t)cap * 520) && cudaMalloc(&L.pk, (size_t)cap * 512) == cudaSuccess &&
-                 cudaMalloc(&L.pk_meta, (size_t)cap * 8) == cudaSuccess;
-            if (ok) L.pk_cap = cap;
-            else {
-                cudaGetLastError();
-                dfree(L.pk);
-                dfree(L.pk_meta);
-            }
-        }
-        if (ok) {
-            CKL(pack_write(c->mesh, L, c->om64, c->om32, c->om32lo, c->st), "write packed operator");
+        if (build_packed(c, L, L.pk, false)) {
             c->launches += 1;  // the level table
-            L.n_pk = n_pk;
             L.op_format = OPF_PACKETS;
             L.op_valid = true;
         } else {
@@ -929,9 +978,9 @@ sweep_status ensure_operator(sweep_ctx* c, Levels& L, const sweep_opts* o, int p
         }
     }
     if (want == OPF_LINES) {
-        dfree(L.pk);
-        dfree(L.pk_meta);
-        L.pk_cap = 0;
+        dfree(L.pk.pk);
+        dfree(L.pk.meta);
+        L.pk.cap = 0;
         const int64_t tasks = L.h_lev_chunk.empty() ? 0 : L.h_lev_chunk.back() * 32;
         const size_t bytes = (size_t)tasks * 128;
         bool ok = true;
@@ -966,6 +1015,7 @@ sweep_status ensure_levels(sweep_ctx* c, const sweep_opts* o, float* t1, float* 
     if (c->lev.valid && !(o && o->relevel) && c->lev.nd == c->D && c->lev.d0 == 0 && c->lev.transport == tr)
         return SWEEP_OK;
     c->lev.op_valid = false;
+    c->lev.pkt.valid = false;
     return run_levelise(c, c->lev, 0, c->D, budget_of(o), t1, t2, tr);
 }
 
@@ -1170,7 +1220,7 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
     int sched = o.schedule, threads = o.block_threads ? o.block_threads : 256;
     int lanes = o.lanes_per_task ? o.lanes_per_task : 4;
     int bpsm = o.blocks_per_sm;
-    // the EXP law has one kernel form (the generic one): no tuning, the dataflow schedule
+    // the EXP law: no tuning, the dataflow schedule (packets: two per warp step)
     if (!plain && sched == SWEEP_SCHED_AUTO && o.law) sched = SWEEP_SCHED_DATAFLOW;
     if (!plain && sched == SWEEP_SCHED_AUTO) {
         CKL(launch_prep_material(N, G, c->mesh.vol, c->ka, c->ks, c->em, nullptr, prec == 32 ? c->cm32 : nullptr,
@@ -1185,7 +1235,7 @@ sweep_status solve_impl(sweep_ctx* c, const sweep_opts* opts_in, double* J_out, 
         if (!o.lanes_per_task) lanes = tl;
     }
     // the packed operator's kernel has whole warps per packet: lanes = 32 x packets per warp step
-    const bool packed = prec == 32 && !o.law && !o.geometry_only && c->lev.op_valid && c->lev.op_format == OPF_PACKETS;
+    const bool packed = prec == 32 && !o.geometry_only && c->lev.op_valid && c->lev.op_format == OPF_PACKETS;
     if (!plain && packed) {
         if (o.packets_per_step) lanes = 32 * o.packets_per_step;
         else if (lanes < 32) lanes = 64;
@@ -1471,7 +1521,9 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
         if (sb != SWEEP_OK) return sb;
         bc32 = c->bc32;
     }
-    float t_sweep = 0.f, tcl = 0.f, tlv = 0.f;
+    float t_sweep = 0.f, tcl = 0.f, tlv = 0.f, tasm = 0.f;
+    // the packed kernels take whole warps per packet: 32 lanes x packets per warp step
+    const int pk_lanes = 32 * (o.packets_per_step ? o.packets_per_step : 2);
     int n_sweeps = it_fwd, it_adj = 0;
     bool conv_adj = true;
     double res_adj = 0.0;
@@ -1481,7 +1533,8 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
         float a1 = 0, a2 = 0;
         if (nb == D) {
             s = ensure_levels(c, &o, &a1, &a2);
-            if (s == SWEEP_OK) s = ensure_operator(c, c->lev, &o, prec, nullptr);
+            if (s == SWEEP_OK) s = ensure_operator(c, c->lev, &o, prec, &tasm);
+            if (s == SWEEP_OK) s = ensure_transposed(c, c->lev, &o, prec, &tasm);
             L = &c->lev;
         } else {
             s = run_levelise(c, c->adj_lev, d0, nb, budget_of(&o), &a1, &a2);
@@ -1501,7 +1554,8 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
             int pI = !signI;
             SweepArgs a = make_args(c, *L, prec, cm, c->adjI, nullptr, G, pI, 0, 0, &o);
             a.debug_stall = 0;
-            s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, lanes, 0, a, bc32, &t_sweep);
+            s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, a.pk ? pk_lanes : lanes, 0, a,
+                          bc32, &t_sweep);
             if (s != SWEEP_OK) return s;
             signI = pI;
             ++n_sweeps;
@@ -1516,7 +1570,8 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
             int pL = !signL[kl];
             SweepArgs r = make_args(c, *L, prec, cm, lbuf[kl], pbc ? lbuf[1 - kl] : nullptr, 2 * G, pL, 1, 0, &o);
             r.debug_stall = 0;
-            s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, lanes, 0, r, nullptr, &t_sweep);
+            s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, r.pk ? pk_lanes : lanes, 0, r,
+                          nullptr, &t_sweep);
             if (s != SWEEP_OK) return s;
             signL[kl] = pL;
             ++n_sweeps;
@@ -1559,6 +1614,7 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
     S.t_ms[1] = tlv;
     S.t_ms[2] = t_sweep;
     S.t_ms[4] = ttot;
+    S.t_ms[5] = tasm;  // forward and transposed operators
     S.updates = (double)N * D * G * (it_fwd + 2.0 * it_adj);  // forward, transposed over 2G split groups
     {
         const Levels& Ld = B == D ? c->lev : c->adj_lev;  // depths of the (last) batch levelised
@@ -1729,6 +1785,7 @@ sweep_status sweep_rotate_directions(sweep_ctx* c, const double* R, int64_t n_qu
     CK(cudaMemcpy(c->om32lo, o32lo.data(), sizeof(float4) * D, cudaMemcpyHostToDevice), "upload directions");
     c->lev.valid = false;
     c->lev.op_valid = false;
+    c->lev.pkt.valid = false;
     c->adj_lev.valid = false;
     return SWEEP_OK;
 }

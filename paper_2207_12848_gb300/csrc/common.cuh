@@ -33,6 +33,9 @@ constexpr int OP_MAX = 14;
 // inflow entries, then its header in the odd slot of its last lane, so at most PK_MAX_IN entries.
 constexpr int PK_MAX_IN = 63;
 constexpr uint32_t PK_BOUNDARY = 0x80000000u;  // source-index bit of a boundary-face entry
+// cell update the packed kernel applies: the balance of scheme (a) or (b), the EXP law, or the
+// transposed balance of the adjoint sweep (source scaled by the direction weight)
+enum { PK_BALANCE = 0, PK_EXP = 1, PK_TRANSPOSED = 2 };
 // forms of the assembled operator
 enum { OPF_NONE = 0, OPF_LINES = 1, OPF_PACKETS = 2 };
 
@@ -325,6 +328,26 @@ struct DevMesh {
     std::vector<int64_t> mesh_off;
 };
 
+// A packed operator: packets of 32 int4 with their {head mask, long-task flag}, the first packet of
+// each level of its stream, and the packing groups (runs of up to 32 chunks of one level) with their
+// packet counts. The forward operator streams the levels in sweep order, the transposed one in reverse.
+struct PackedOp {
+    int4* pk = nullptr;
+    uint2* meta = nullptr;
+    int64_t cap = 0;             // packets allocated
+    int64_t n_pk = 0;            // packets of the current operator (even within every level)
+    int64_t* lev_pk = nullptr;   // device [n_levels+1] first packet of each level of the stream
+    int2* grp = nullptr;         // device [ng] {first chunk, end chunk} of each packing group
+    int32_t* lev_grp = nullptr;  // device [n_levels+1] first group of each level of the stream
+    int32_t* cnt = nullptr;      // device [ng] packets per group
+    int64_t* off = nullptr;      // device [ng+1] first packet of each group
+    int64_t* scan = nullptr;     // scan scratch
+    int64_t grp_cap = 0;         // groups (and levels + 1) the tables above hold
+    int64_t ng = 0;
+    int32_t* flag = nullptr;     // device word: a task has more entries than a packet holds
+    bool valid = false;          // transposed operator: built for the current levels
+};
+
 struct Levels {
     bool valid = false;
     int d0 = 0, nd = 0;
@@ -340,20 +363,8 @@ struct Levels {
     size_t op_bytes = 0;
     bool op_valid = false;
     int op_format = OPF_NONE;    // form of the assembled operator when op_valid
-    // packed operator (OPF_PACKETS): packets of 32 int4, their {head mask, overflow mask}, the first
-    // packet of each level; packing groups (runs of up to 32 chunks of one level) and their counts
-    int4* pk = nullptr;
-    uint2* pk_meta = nullptr;
-    int64_t pk_cap = 0;          // packets allocated
-    int64_t n_pk = 0;            // packets of the current operator (even within every level)
-    int64_t* lev_pk = nullptr;   // device [n_levels+1]
-    int32_t* pk_grp = nullptr;   // device [ng+1] first chunk of each packing group, then [n_levels+1] first group
-    int32_t* pk_cnt = nullptr;   // device [ng] packets per group
-    int64_t* pk_off = nullptr;   // device [ng+1] first packet of each group
-    int64_t* pk_scan = nullptr;  // scan scratch
-    int64_t pk_grp_cap = 0;      // groups (and levels + 1) the tables above hold
-    int64_t pk_ng = 0;
-    int32_t* pk_flag = nullptr;  // device word: a task has more than PK_MAX_IN inflow sides
+    PackedOp pk;                 // packed operator of the forward sweep (OPF_PACKETS)
+    PackedOp pkt;                // packed transposed operator of the adjoint sweep, built on demand
     // direction-conserving transport (scheme (b) of Sec. 2.6), [N][nd] like info: the chosen outflow
     // sides (bit k = row position k), the effective inflow sides (interior and periodic sides the
     // upwind cell chose, boundary inflow sides), and the share P_c / n_c each chosen side carries
@@ -437,18 +448,20 @@ cudaError_t launch_validate_mesh(int64_t N, int64_t F, const double* vol, const 
 
 cudaError_t build_operator(const DevMesh& m, const Levels& L, const double* om64_all, const float4* om32_all,
                            const float4* om32lo_all, cudaStream_t st);
-// packed operator: plan (groups, packet counts; *n_pk = packets needed, or -1 when a task has more
-// inflow sides than a packet holds) then write into L.pk / L.pk_meta
-cudaError_t pack_plan(const DevMesh& m, Levels& L, const double* om64_all, const float4* om32_all,
-                      const float4* om32lo_all, cudaStream_t st, int64_t* n_pk);
-cudaError_t pack_write(const DevMesh& m, Levels& L, const double* om64_all, const float4* om32_all,
-                       const float4* om32lo_all, cudaStream_t st);
+// packed operator P of the levels L: plan (groups, packet counts; *n_pk = packets needed, or -1 when a
+// task has more entries than a packet holds) then write into P.pk / P.meta. transposed: the adjoint's
+// operator (outflow entries, levels in reverse order)
+cudaError_t pack_plan(const DevMesh& m, const Levels& L, PackedOp& P, bool transposed, const double* om64_all,
+                      const float4* om32_all, const float4* om32lo_all, cudaStream_t st, int64_t* n_pk);
+cudaError_t pack_write(const DevMesh& m, const Levels& L, PackedOp& P, bool transposed, const double* om64_all,
+                       const float4* om32_all, const float4* om32lo_all, cudaStream_t st);
 cudaError_t levelise(const DevMesh& m, Levels& L, const double* om64_all, const float4* om32_all,
                      const float4* om32lo_all, int dev_sms, GridBar* bar, int* err, long long budget,
                      int64_t* d_scratch, cudaStream_t st, float* t_classify, float* t_levelise, std::string* msg);
 
-// fmt: OPF_* form of the assembled operator the launch reads (OPF_NONE: the mesh rows)
-int sweep_occupancy(int precision, int G, int threads, int nd, int lanes, int reverse, int fmt);
+// fmt: OPF_* form of the assembled operator the launch reads (OPF_NONE: the mesh rows); generic: the
+// mesh-row launch is the generic kernel (reverse, EXP, scheme (b)); pk_mode: the packed kernel's PK_*
+int sweep_occupancy(int precision, int G, int threads, int nd, int lanes, int generic, int fmt, int pk_mode);
 cudaError_t launch_sweep(const SweepArgs& a, int precision, int blocks, int threads, cudaStream_t st,
                          int* kernel = nullptr);
 cudaError_t launch_plain_level(const SweepArgs& a, uint32_t begin, uint32_t end, cudaStream_t st);

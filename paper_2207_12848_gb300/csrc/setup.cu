@@ -1055,6 +1055,10 @@ cudaError_t build_operator(const DevMesh& m, const Levels& L, const double* om64
 // Tasks are packed in sweep order, next-fit, within packing groups of up to 32 chunks (1024 tasks)
 // of one level; a group's packet count is rounded up to even with an empty packet, so that two
 // consecutive packets of a warp step always belong to one level (independent tasks).
+// The transposed operator (rows of L_Omega^T, the adjoint sweep) has the same layout: a task's
+// entries are its outflow sides to interior cells {dl*N + nb, +w} and periodic partners
+// {dl*N + partner, -w} (the previous pass of the transposed periodic iteration), its header the same
+// {task entry, P_c}, and the levels are streamed in reverse order (downwind cells first).
 // ---------------------------------------------------------------------------------------------
 namespace {
 
@@ -1062,8 +1066,9 @@ constexpr int PK_GROUP_CHUNKS = 32;
 
 struct PackArgs {
     const int4* trec;
-    const int32_t* grp;  // [ng+1] first chunk of each group
+    const int2* grp;     // [ng] {first chunk, end chunk} of each group
     int64_t ng;
+    int transposed;      // the adjoint's operator: outflow entries (interior and periodic sides)
     const uint32_t* rowptr;
     const int4* side;
     const d4* side64;
@@ -1104,6 +1109,28 @@ __device__ int pk_inflow_past32(const PackArgs& a, const int4 tr, int stop_at, u
     return k;
 }
 
+// outflow sides of a task's row to interior cells or periodic partners, in row order (the transposed
+// operator's entries, their sign as in k_classify): their count, or the stop_at-th in *side_out
+__device__ int pk_outflow(const PackArgs& a, const int4 tr, int stop_at, uint32_t* side_out) {
+    const uint32_t e = (uint32_t)tr.x, c = e & a.cmask, dl = e >> a.cshift;
+    const float4 om = a.om32[dl];
+    const double* o64 = a.om64 + 3 * dl;
+    const uint32_t r0 = (uint32_t)tr.y, r1 = a.rowptr[c + 1];
+    int k = 0;
+    for (uint32_t s = r0; s < r1; ++s) {
+        const int4 r = a.side[s];
+        if (r.x < 0) continue;  // boundary face: nothing flows back in through the transpose
+        const float ax = __int_as_float(r.y), ay = __int_as_float(r.z), az = __int_as_float(r.w);
+        if (classify_side(dot32(ax, ay, az, om), ax, ay, az, a.side64, s, o64) <= 0) continue;
+        if (k == stop_at) {
+            *side_out = s;
+            return k;
+        }
+        ++k;
+    }
+    return k;
+}
+
 // scheme (b) table index of a task
 __device__ __forceinline__ int64_t pk_dc_index(const PackArgs& a, uint32_t e) {
     return (int64_t)(e & a.cmask) * a.nd + (e >> a.cshift);
@@ -1111,6 +1138,10 @@ __device__ __forceinline__ int64_t pk_dc_index(const PackArgs& a, uint32_t e) {
 
 // inflow entries of a task
 __device__ __forceinline__ int pk_task_inflow(const PackArgs& a, const int4 tr) {
+    if (a.transposed) {
+        uint32_t dummy;
+        return pk_outflow(a, tr, -1, &dummy);
+    }
     if (a.dc_inm) return __popcll(a.dc_inm[pk_dc_index(a, (uint32_t)tr.x)]);
     int n = __popc((uint32_t)tr.w);
     if (tr.z < 0) {
@@ -1129,7 +1160,9 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int j) {
 // interior and periodic ones weighted by the upwind cell's share)
 __device__ int2 pk_entry(const PackArgs& a, const int4 tr, int j, uint32_t slab, const float4& om, const float4& oml) {
     uint32_t s = 0;
-    if (a.dc_inm) {
+    if (a.transposed) {
+        pk_outflow(a, tr, j, &s);
+    } else if (a.dc_inm) {
         uint64_t m = a.dc_inm[pk_dc_index(a, (uint32_t)tr.x)];
         for (int q = 0; q < j; ++q) m &= m - 1;
         s = (uint32_t)tr.y + (uint32_t)(__ffsll((long long)m) - 1);
@@ -1156,7 +1189,8 @@ __global__ void __launch_bounds__(256) k_pack(PackArgs a) {
     const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (g >= a.ng) return;  // whole warps
     const int lane = threadIdx.x & 31;
-    const int64_t t_begin = (int64_t)a.grp[g] * 32, t_end = (int64_t)a.grp[g + 1] * 32;
+    const int2 gr = a.grp[g];
+    const int64_t t_begin = (int64_t)gr.x * 32, t_end = (int64_t)gr.y * 32;
     int64_t pkt = WRITE ? a.off[g] : 0;
     int64_t npk = 0;
     int fill = 0;  // lanes taken in the open packet
@@ -1248,12 +1282,13 @@ __global__ void k_lev_pk(const int32_t* lev_grp, const int64_t* off, int n, int6
     if (i <= n) lev_pk[i] = off[lev_grp[i]];
 }
 
-PackArgs pack_args(const DevMesh& m, const Levels& L, const double* om64_all, const float4* om32_all,
-                   const float4* om32lo_all) {
+PackArgs pack_args(const DevMesh& m, const Levels& L, const PackedOp& P, bool transposed, const double* om64_all,
+                   const float4* om32_all, const float4* om32lo_all) {
     PackArgs a;
     a.trec = L.trec;
-    a.grp = L.pk_grp;
-    a.ng = L.pk_ng;
+    a.grp = P.grp;
+    a.ng = P.ng;
+    a.transposed = transposed ? 1 : 0;
     a.rowptr = m.rowptr;
     a.side = m.side;
     a.side64 = m.side64;
@@ -1264,76 +1299,81 @@ PackArgs pack_args(const DevMesh& m, const Levels& L, const double* om64_all, co
     a.cmask = L.cmask;
     a.cshift = L.cshift;
     a.N = (uint32_t)m.N;
-    a.cnt = L.pk_cnt;
-    a.flag = L.pk_flag;
+    a.cnt = P.cnt;
+    a.flag = P.flag;
     a.nd = L.nd;
-    a.dc_inm = L.transport > 0 ? L.dc_inm : nullptr;
-    a.dc_share32 = L.transport > 0 ? L.dc_share32 : nullptr;
-    a.off = L.pk_off;
-    a.pk = L.pk;
-    a.meta = L.pk_meta;
+    a.dc_inm = L.transport > 0 && !transposed ? L.dc_inm : nullptr;
+    a.dc_share32 = L.transport > 0 && !transposed ? L.dc_share32 : nullptr;
+    a.off = P.off;
+    a.pk = P.pk;
+    a.meta = P.meta;
     return a;
 }
 
 }  // namespace
 
-cudaError_t pack_plan(const DevMesh& m, Levels& L, const double* om64_all, const float4* om32_all,
-                      const float4* om32lo_all, cudaStream_t st, int64_t* n_pk) {
-    // packing groups: runs of up to PK_GROUP_CHUNKS chunks of one level (levels are padded to chunks)
+cudaError_t pack_plan(const DevMesh& m, const Levels& L, PackedOp& P, bool transposed, const double* om64_all,
+                      const float4* om32_all, const float4* om32lo_all, cudaStream_t st, int64_t* n_pk) {
+    // packing groups: runs of up to PK_GROUP_CHUNKS chunks of one level (levels are padded to chunks),
+    // the levels in stream order (the transposed operator: last level first)
     const int nlev = L.n_levels;
-    std::vector<int32_t> grp, lev_grp(nlev + 1);
-    for (int l = 0; l < nlev; ++l) {
-        lev_grp[l] = (int32_t)grp.size();
-        for (int64_t c = L.h_lev_chunk[l]; c < L.h_lev_chunk[l + 1]; c += PK_GROUP_CHUNKS) grp.push_back((int32_t)c);
+    std::vector<int2> grp;
+    std::vector<int32_t> lev_grp(nlev + 1);
+    for (int i = 0; i < nlev; ++i) {
+        const int l = transposed ? nlev - 1 - i : i;
+        lev_grp[i] = (int32_t)grp.size();
+        const int64_t c1 = L.h_lev_chunk[l + 1];
+        for (int64_t c = L.h_lev_chunk[l]; c < c1; c += PK_GROUP_CHUNKS)
+            grp.push_back(make_int2((int)c, (int)std::min<int64_t>(c + PK_GROUP_CHUNKS, c1)));
     }
     const int64_t ng = (int64_t)grp.size();
     lev_grp[nlev] = (int32_t)ng;
-    grp.push_back(nlev > 0 ? (int32_t)L.h_lev_chunk[nlev] : 0);
-    grp.insert(grp.end(), lev_grp.begin(), lev_grp.end());
-    const int64_t want = ng + nlev + 2;
+    const int64_t want = std::max<int64_t>(ng, nlev) + 2;
     cudaError_t e;
-    if (want > L.pk_grp_cap || !L.pk_flag) {
-        for (void* p : {(void*)L.pk_grp, (void*)L.pk_cnt, (void*)L.pk_off, (void*)L.pk_scan, (void*)L.lev_pk,
-                        (void*)L.pk_flag})
+    if (want > P.grp_cap || !P.flag) {
+        for (void* p : {(void*)P.grp, (void*)P.lev_grp, (void*)P.cnt, (void*)P.off, (void*)P.scan, (void*)P.lev_pk,
+                        (void*)P.flag})
             if (p) cudaFree(p);
-        L.pk_grp = nullptr; L.pk_cnt = nullptr; L.pk_off = nullptr; L.pk_scan = nullptr; L.lev_pk = nullptr;
-        L.pk_flag = nullptr;
-        L.pk_grp_cap = 0;
+        P.grp = nullptr; P.lev_grp = nullptr; P.cnt = nullptr; P.off = nullptr; P.scan = nullptr;
+        P.lev_pk = nullptr; P.flag = nullptr;
+        P.grp_cap = 0;
         const int64_t cap = want + want / 4;
-        if ((e = cudaMalloc(&L.pk_grp, sizeof(int32_t) * cap))) return e;
-        if ((e = cudaMalloc(&L.pk_cnt, sizeof(int32_t) * cap))) return e;
-        if ((e = cudaMalloc(&L.pk_off, sizeof(int64_t) * cap))) return e;
-        if ((e = cudaMalloc(&L.pk_scan, sizeof(int64_t) * (cap / (SCAN_BLOCK * SCAN_ITEMS) + 2)))) return e;
-        if ((e = cudaMalloc(&L.lev_pk, sizeof(int64_t) * cap))) return e;
-        if ((e = cudaMalloc(&L.pk_flag, sizeof(int32_t)))) return e;
-        L.pk_grp_cap = cap;
+        if ((e = cudaMalloc(&P.grp, sizeof(int2) * cap))) return e;
+        if ((e = cudaMalloc(&P.lev_grp, sizeof(int32_t) * cap))) return e;
+        if ((e = cudaMalloc(&P.cnt, sizeof(int32_t) * cap))) return e;
+        if ((e = cudaMalloc(&P.off, sizeof(int64_t) * cap))) return e;
+        if ((e = cudaMalloc(&P.scan, sizeof(int64_t) * (cap / (SCAN_BLOCK * SCAN_ITEMS) + 2)))) return e;
+        if ((e = cudaMalloc(&P.lev_pk, sizeof(int64_t) * cap))) return e;
+        if ((e = cudaMalloc(&P.flag, sizeof(int32_t)))) return e;
+        P.grp_cap = cap;
     }
-    L.pk_ng = ng;
-    if ((e = cudaMemcpyAsync(L.pk_grp, grp.data(), sizeof(int32_t) * grp.size(), cudaMemcpyHostToDevice, st)))
+    P.ng = ng;
+    if (ng > 0 && (e = cudaMemcpyAsync(P.grp, grp.data(), sizeof(int2) * ng, cudaMemcpyHostToDevice, st))) return e;
+    if ((e = cudaMemcpyAsync(P.lev_grp, lev_grp.data(), sizeof(int32_t) * lev_grp.size(), cudaMemcpyHostToDevice, st)))
         return e;
-    if ((e = cudaMemsetAsync(L.pk_flag, 0, sizeof(int32_t), st))) return e;
+    if ((e = cudaMemsetAsync(P.flag, 0, sizeof(int32_t), st))) return e;
     if (ng > 0) {
-        PackArgs a = pack_args(m, L, om64_all, om32_all, om32lo_all);
+        PackArgs a = pack_args(m, L, P, transposed, om64_all, om32_all, om32lo_all);
         k_pack<false><<<(unsigned)((ng * 32 + 255) / 256), 256, 0, st>>>(a);
-        if ((e = scan_i32(L.pk_cnt, ng, L.pk_off, L.pk_scan, L.pk_off + ng, st))) return e;
-    } else if ((e = cudaMemsetAsync(L.pk_off, 0, sizeof(int64_t), st))) {
+        if ((e = scan_i32(P.cnt, ng, P.off, P.scan, P.off + ng, st))) return e;
+    } else if ((e = cudaMemsetAsync(P.off, 0, sizeof(int64_t), st))) {
         return e;
     }
     int64_t total = 0;
     int32_t flag = 0;
-    if ((e = cudaMemcpyAsync(&total, L.pk_off + ng, sizeof total, cudaMemcpyDeviceToHost, st))) return e;
-    if ((e = cudaMemcpyAsync(&flag, L.pk_flag, sizeof flag, cudaMemcpyDeviceToHost, st))) return e;
+    if ((e = cudaMemcpyAsync(&total, P.off + ng, sizeof total, cudaMemcpyDeviceToHost, st))) return e;
+    if ((e = cudaMemcpyAsync(&flag, P.flag, sizeof flag, cudaMemcpyDeviceToHost, st))) return e;
     if ((e = cudaStreamSynchronize(st))) return e;
     *n_pk = flag ? -1 : total;
     return cudaSuccess;
 }
 
-cudaError_t pack_write(const DevMesh& m, Levels& L, const double* om64_all, const float4* om32_all,
-                       const float4* om32lo_all, cudaStream_t st) {
-    PackArgs a = pack_args(m, L, om64_all, om32_all, om32lo_all);
-    if (L.pk_ng > 0) k_pack<true><<<(unsigned)((L.pk_ng * 32 + 255) / 256), 256, 0, st>>>(a);
+cudaError_t pack_write(const DevMesh& m, const Levels& L, PackedOp& P, bool transposed, const double* om64_all,
+                       const float4* om32_all, const float4* om32lo_all, cudaStream_t st) {
+    PackArgs a = pack_args(m, L, P, transposed, om64_all, om32_all, om32lo_all);
+    if (P.ng > 0) k_pack<true><<<(unsigned)((P.ng * 32 + 255) / 256), 256, 0, st>>>(a);
     const int nlev = L.n_levels;
-    k_lev_pk<<<(nlev + 1 + 255) / 256, 256, 0, st>>>(L.pk_grp + L.pk_ng + 1, L.pk_off, nlev, L.lev_pk);
+    k_lev_pk<<<(nlev + 1 + 255) / 256, 256, 0, st>>>(P.lev_grp, P.off, nlev, P.lev_pk);
     return cudaGetLastError();
 }
 

@@ -42,7 +42,7 @@ __device__ __forceinline__ double divr(double a, double b) { return __ddiv_rn(a,
 
 // EXP law of one cell and group: outgoing (exp(-tau) F_in + q) / P and cell mean (F_in / P)(1 - exp(-tau)) / tau,
 // tau = kappa_t V / P; with no outflow (P = 0) everything that enters or is emitted stays: (q + F_in) / kappa_t V
-__device__ __noinline__ void exp_law(float fin, float q, float ktv, float P, float& out, float& mean) {
+__device__ __forceinline__ void exp_update(float fin, float q, float ktv, float P, float& out, float& mean) {
     if (P > 0.f) {
         const float tau = ktv / P;
         const float f = tau > 0.f ? -expm1f(-tau) / tau : 1.f;
@@ -52,7 +52,7 @@ __device__ __noinline__ void exp_law(float fin, float q, float ktv, float P, flo
         out = mean = (q + fin) / ktv;
     }
 }
-__device__ __noinline__ void exp_law(double fin, double q, double ktv, double P, double& out, double& mean) {
+__device__ __forceinline__ void exp_update(double fin, double q, double ktv, double P, double& out, double& mean) {
     if (P > 0.0) {
         const double tau = ktv / P;
         const double f = tau > 0.0 ? -expm1(-tau) / tau : 1.0;
@@ -61,6 +61,33 @@ __device__ __noinline__ void exp_law(double fin, double q, double ktv, double P,
     } else {
         out = mean = (q + fin) / ktv;
     }
+}
+// The same law in the packed kernel, where every lane of a packet evaluates it (the head lanes keep the
+// result): one expf and two fast reciprocals, selects instead of branches. The mean factor
+// f = (1 - exp(-tau)) / tau is taken from its Taylor series sum_k (-tau)^k / (k+1)! (seven terms,
+// truncation below 2e-9) where 1 - exp(-tau) would cancel (tau < 1/4), and directly above.
+__device__ __forceinline__ void exp_update_lanes(float fin, float q, float ktv, float P, float& out, float& mean) {
+    const float rP = __fdividef(1.f, P), rK = __fdividef(1.f, ktv);
+    const float tau = ktv * rP;
+    const float e = expf(-tau);
+    const float s = -tau;
+    float ft = fmaf(s, 1.f / 5040.f, 1.f / 720.f);
+    ft = fmaf(s, ft, 1.f / 120.f);
+    ft = fmaf(s, ft, 1.f / 24.f);
+    ft = fmaf(s, ft, 1.f / 6.f);
+    ft = fmaf(s, ft, 0.5f);
+    ft = fmaf(s, ft, 1.f);
+    const float f = tau < 0.25f ? ft : (1.f - e) * P * rK;
+    const float stay = (q + fin) * rK;  // P = 0: no outflow
+    out = P > 0.f ? fmaf(e, fin, q) * rP : stay;
+    mean = P > 0.f ? fin * rP * f : stay;
+}
+// out of line in the mesh-row kernels, whose common path stays short
+__device__ __noinline__ void exp_law(float fin, float q, float ktv, float P, float& out, float& mean) {
+    exp_update(fin, q, ktv, P, out, mean);
+}
+__device__ __noinline__ void exp_law(double fin, double q, double ktv, double P, double& out, double& mean) {
+    exp_update(fin, q, ktv, P, out, mean);
 }
 
 // Rare path, kept out of line so the common path stays short:
@@ -1107,8 +1134,10 @@ __device__ __forceinline__ void pk_wait_all(const SweepArgs& a, PkLane<GC> (&t)[
     }
 }
 
-// segmented sum over each task's lanes, then the head lane solves and stores the cell
-template <int GC>
+// segmented sum over each task's lanes, then the head lane solves and stores the cell: the balance
+// (q + sum) / (P_c + kappa_t V), the EXP law (intensity and cell mean), or the transposed balance
+// (w_d q + sum) / (P_c + kappa_t V) of the adjoint sweep
+template <int GC, int MODE>
 __device__ __forceinline__ void pk_solve(const SweepArgs& a, const PkLane<GC>& t, uint32_t par, uint64_t keep,
                                          bool fail) {
     const float w0 = fabsf(__int_as_float(t.s.y)), w1 = fabsf(__int_as_float(t.s.w));
@@ -1136,9 +1165,26 @@ __device__ __forceinline__ void pk_solve(const SweepArgs& a, const PkLane<GC>& t
     const uint32_t dst = (e >> a.cshift) * (uint32_t)a.N + (e & a.cmask);
     const float P = __int_as_float(t.s.w);
     float v[GC];
+    if constexpr (MODE == PK_EXP) {
+        float m[GC];
 #pragma unroll
-    for (int g = 0; g < GC; ++g)
-        v[g] = __uint_as_float(__float_as_uint(__fdividef(t.q[2 * g] + acc[g], P + t.q[2 * g + 1])) ^ par);
+        for (int g = 0; g < GC; ++g) {
+            exp_update_lanes(acc[g], t.q[2 * g], t.q[2 * g + 1], P, v[g], m[g]);
+            v[g] = __uint_as_float(__float_as_uint(v[g]) ^ par);
+        }
+        float* mo = reinterpret_cast<float*>(a.Imean) + (size_t)dst * GC;
+        if constexpr (GC == 4) st_relaxed_hint_v4_if(mo, make_float4(m[0], m[1], m[2], m[3]), keep, on);
+        else if constexpr (GC == 2) st_relaxed_hint_v2_if(mo, make_float2(m[0], m[1]), keep, on);
+        else st_relaxed_hint_if(mo, m[0], keep, on);
+    } else {
+        float wd = 1.f;
+        if constexpr (MODE == PK_TRANSPOSED) wd = (float)__ldg(a.w64 + (t.head ? (e >> a.cshift) : 0u));
+#pragma unroll
+        for (int g = 0; g < GC; ++g) {
+            const float src = MODE == PK_TRANSPOSED ? wd * t.q[2 * g] : t.q[2 * g];
+            v[g] = __uint_as_float(__float_as_uint(__fdividef(src + acc[g], P + t.q[2 * g + 1])) ^ par);
+        }
+    }
     float* out = reinterpret_cast<float*>(a.I) + (size_t)dst * GC;
     if constexpr (GC == 4) st_relaxed_hint_v4_if(out, make_float4(v[0], v[1], v[2], v[3]), keep, on);
     else if constexpr (GC == 2) st_relaxed_hint_v2_if(out, make_float2(v[0], v[1]), keep, on);
@@ -1147,7 +1193,7 @@ __device__ __forceinline__ void pk_solve(const SweepArgs& a, const PkLane<GC>& t
 
 // Steps [k0, k1) of PK packets, warp w taking k0 + w, k0 + w + W, ...; the packets of the next step
 // are loaded one step ahead into registers and those three steps ahead prefetched into L2.
-template <int GC, int PK>
+template <int GC, int PK, int MODE>
 __device__ __forceinline__ bool pk_steps(const SweepArgs& a, int64_t k0, int64_t k1, int64_t warp, int64_t nwarps) {
     const int lane = threadIdx.x & 31;
     const uint64_t pol = policy_evict_first();
@@ -1188,7 +1234,7 @@ __device__ __forceinline__ bool pk_steps(const SweepArgs& a, int64_t k0, int64_t
         for (int p = 0; p < PK; ++p) nr |= pk_unready<GC>(t[p], par);
         if (__any_sync(0xffffffffu, nr)) pk_wait_all<GC, PK>(a, t, par, fail);
 #pragma unroll
-        for (int p = 0; p < PK; ++p) pk_solve<GC>(a, t[p], par, keep, fail);
+        for (int p = 0; p < PK; ++p) pk_solve<GC, MODE>(a, t[p], par, keep, fail);
 #pragma unroll
         for (int p = 0; p < PK; ++p) {
             cur[p] = nxt[p];
@@ -1198,15 +1244,15 @@ __device__ __forceinline__ bool pk_steps(const SweepArgs& a, int64_t k0, int64_t
     return true;
 }
 
-// resident 256-thread blocks per SM the packed kernel is compiled for (64 registers; 3 with four groups
-// and two packets per step, whose state needs more)
-template <int GC, int PK>
+// resident 256-thread blocks per SM the packed kernel is compiled for (64 registers; 3 with two packets
+// per step and four groups, or two groups under the EXP law, whose state needs more)
+template <int GC, int PK, int MODE>
 struct PkMinBlocks {
-    static constexpr int value = (GC == 4 && PK == 2) ? 3 : 4;
+    static constexpr int value = (PK == 2 && (GC == 4 || (GC == 2 && MODE == PK_EXP))) ? 3 : 4;
 };
 
-template <int GC, int PK>
-__global__ void __launch_bounds__(256, (PkMinBlocks<GC, PK>::value)) k_sweep_pk(const __grid_constant__ SweepArgs a) {
+template <int GC, int PK, int MODE>
+__global__ void __launch_bounds__(256, (PkMinBlocks<GC, PK, MODE>::value)) k_sweep_pk(const __grid_constant__ SweepArgs a) {
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     if (a.debug_stall && warp == 0 && (threadIdx.x & 31) == 0) {  // test hook: a wait on a word nothing writes
@@ -1215,31 +1261,44 @@ __global__ void __launch_bounds__(256, (PkMinBlocks<GC, PK>::value)) k_sweep_pk(
     }
     if (a.level_sync) {
         for (int li = 0; li < a.n_levels; ++li) {
-            pk_steps<GC, PK>(a, a.lev_pk[li] / PK, a.lev_pk[li + 1] / PK, warp, nwarps);
+            pk_steps<GC, PK, MODE>(a, a.lev_pk[li] / PK, a.lev_pk[li + 1] / PK, warp, nwarps);
             if (!grid_sync(a.bar, gridDim.x, a.spin_budget, a.err)) return;
         }
     } else {
-        pk_steps<GC, PK>(a, 0, a.n_pk / PK, warp, nwarps);
+        pk_steps<GC, PK, MODE>(a, 0, a.n_pk / PK, warp, nwarps);
     }
 }
 
+// the packed kernel of a launch: groups (1, 2 or 4; the transposed sweep's 2G split groups: 2 or 4),
+// packets per warp step and cell update
 template <int PK>
-cudaError_t launch_pk(const SweepArgs& a, const cudaLaunchConfig_t& cfg) {
-    switch (a.G) {
-        case 1: return cudaLaunchKernelEx(&cfg, k_sweep_pk<1, PK>, a);
-        case 2: return cudaLaunchKernelEx(&cfg, k_sweep_pk<2, PK>, a);
-        default: return cudaLaunchKernelEx(&cfg, k_sweep_pk<4, PK>, a);
+const void* pk_kernel(int G, int mode) {
+    if (mode == PK_TRANSPOSED) return G == 2 ? (const void*)k_sweep_pk<2, PK, PK_TRANSPOSED>
+                                             : (const void*)k_sweep_pk<4, PK, PK_TRANSPOSED>;
+    if (mode == PK_EXP) {
+        switch (G) {
+            case 1: return (const void*)k_sweep_pk<1, PK, PK_EXP>;
+            case 2: return (const void*)k_sweep_pk<2, PK, PK_EXP>;
+            default: return (const void*)k_sweep_pk<4, PK, PK_EXP>;
+        }
     }
-}
-
-template <int PK>
-int occupancy_pk(int G, int threads, size_t smem) {
-    int n = 0;
     switch (G) {
-        case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_pk<1, PK>, threads, smem); break;
-        case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_pk<2, PK>, threads, smem); break;
-        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_pk<4, PK>, threads, smem); break;
+        case 1: return (const void*)k_sweep_pk<1, PK, PK_BALANCE>;
+        case 2: return (const void*)k_sweep_pk<2, PK, PK_BALANCE>;
+        default: return (const void*)k_sweep_pk<4, PK, PK_BALANCE>;
     }
+}
+
+template <int PK>
+cudaError_t launch_pk(const SweepArgs& a, const cudaLaunchConfig_t& cfg, int mode) {
+    void* args[] = {(void*)&a};
+    return cudaLaunchKernelExC(&cfg, pk_kernel<PK>(a.G, mode), args);
+}
+
+template <int PK>
+int occupancy_pk(int G, int mode, int threads, size_t smem) {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pk_kernel<PK>(G, mode), threads, smem);
     return n;
 }
 
@@ -1383,9 +1442,10 @@ cudaError_t launch_typed(const SweepArgs& a, int blocks, int threads, cudaStream
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (sizeof(real) == 4 && !a.reverse && a.pk) {  // FP32 forward over the packed operator
+    if (sizeof(real) == 4 && a.pk) {  // FP32 over the packed operator (forward or transposed)
         *kid = SWEEP_KERNEL_PACKED;
-        return a.lanes >= 64 ? launch_pk<2>(a, cfg) : launch_pk<1>(a, cfg);
+        const int mode = a.reverse ? PK_TRANSPOSED : (a.law ? PK_EXP : PK_BALANCE);
+        return a.lanes >= 64 ? launch_pk<2>(a, cfg, mode) : launch_pk<1>(a, cfg, mode);
     }
     if (sizeof(real) == 4 && !a.reverse && a.op) {  // FP32 forward over the assembled operator
         if (a.lanes == 16 && a.G == 1 && !a.level_sync) {
@@ -1426,10 +1486,11 @@ int occupancy_lanes(int G, int threads, size_t smem) {
 
 }  // namespace
 
-int sweep_occupancy(int precision, int G, int threads, int nd, int lanes, int reverse, int fmt) {
+int sweep_occupancy(int precision, int G, int threads, int nd, int lanes, int generic, int fmt, int pk_mode) {
     size_t smem = sizeof(float4) * (size_t)nd;
-    if (precision == 32 && !reverse && fmt == OPF_PACKETS)
-        return lanes >= 64 ? occupancy_pk<2>(G, threads, smem) : occupancy_pk<1>(G, threads, smem);
+    if (precision == 32 && fmt == OPF_PACKETS)
+        return lanes >= 64 ? occupancy_pk<2>(G, pk_mode, threads, smem) : occupancy_pk<1>(G, pk_mode, threads, smem);
+    const int reverse = generic;
     if (precision == 32 && !reverse && fmt == OPF_LINES) {
         if (lanes == 16 && G == 1) {
             int n = 0;
