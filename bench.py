@@ -659,6 +659,9 @@ def adjoint_entry(args, stream, peaks: dict, steps: int, warmup: int, cpu: bool 
                        "assemble_ms": st["t_assemble_ms"]}}
         e["forward_roofline"] = _roof(p, sf["t_sweep_ms"] / max(1, sf["sweep_launches"]), peaks,
                                       KERNELS.get(sf["kernel_used"], "?"))
+        n_tr = sum(o["it_pbc"] for o in outs)  # transposed passes
+        e["transposed_roofline"] = _roof_sweeps(p, sum(o["t_transposed_ms"] for o in outs), n_tr,
+                                                float(N * D * 2 * G * n_tr), peaks, KERNELS.get(st["kernel_used"], "?"))
         # accuracy of the FP32 gradients against the FP64 adjoint of the same inputs
         gk64, ge64 = torch.empty_like(J), torch.empty_like(J)
         ctx.adjoint_dev(gk64, ge64, None, dg, default_opts(precision=64))
@@ -685,6 +688,16 @@ def adjoint_entry(args, stream, peaks: dict, steps: int, warmup: int, cpu: bool 
             te = time.perf_counter() - t0
             e["e2e"] = {"value": u2 / te, "unit": "updates/s", "h2d_bytes_per_step": dgp.nbytes,
                         "d2h_bytes_per_step": 2 * N * G * 8, "ms_per_step": 1e3 * te / steps}
+        # the forward sweep at the transposed sweep's width (2G groups, same mesh): the like-for-like comparison
+        ka2, em2 = np.tile(p.kappa_abs, (1, 2)), np.tile(p.emissivity, (1, 2))
+        ctx.set_material(ka2, em2)
+        J2 = torch.empty((N, 2 * G), dtype=torch.float64, device="cuda")
+        G2m = torch.empty_like(J2)
+        ctx.solve_dev(J2, G2m, default_opts(precision=32))
+        s2, _ = ctx.solve_dev(J2, G2m, default_opts(precision=32))
+        p2 = dataclasses.replace(p, kappa_abs=ka2, emissivity=em2)
+        e["forward_roofline_2G"] = _roof(p2, s2["t_sweep_ms"] / max(1, s2["sweep_launches"]), peaks,
+                                         KERNELS.get(s2["kernel_used"], "?"))
     if cpu:
         # the oracle's adjoint (forward solve + transposed sweep) on the host cores, on a sample of directions
         cores = os.cpu_count() or 1

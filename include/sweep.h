@@ -130,7 +130,7 @@ typedef struct {
     double emitted, injected, absorbed, escaped; /* photons/s over all cells and groups (FP64) */
     double defect;             /* (emitted + injected - absorbed - escaped) / (emitted + injected) */
     double t_ms[8];            /* 0 classify, 1 levelise, 2 sweeps, 3 tallies+updates, 4 total, 5 operator
-                                  assembly (CUDA events) */
+                                  assembly, 6 (adjoint) the transposed sweeps within 2 (CUDA events) */
     double updates;            /* cell x direction x group updates done by all sweeps */
     double updates_per_s;      /* updates / (t_ms[4] / 1000) */
     int32_t sweep_launches;    /* batched-sweep kernel launches timed in t_ms[2] */

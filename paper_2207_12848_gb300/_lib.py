@@ -63,7 +63,7 @@ class sweep_stats(ctypes.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "t_ms"}
         t = list(self.t_ms)
         d.update(t_classify_ms=t[0], t_levelise_ms=t[1], t_sweep_ms=t[2], t_update_ms=t[3], t_total_ms=t[4],
-                 t_assemble_ms=t[5])
+                 t_assemble_ms=t[5], t_transposed_ms=t[6])
         return d
 
 

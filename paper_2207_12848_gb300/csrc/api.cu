@@ -1521,9 +1521,12 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
         if (sb != SWEEP_OK) return sb;
         bc32 = c->bc32;
     }
-    float t_sweep = 0.f, tcl = 0.f, tlv = 0.f, tasm = 0.f;
-    // the packed kernels take whole warps per packet: 32 lanes x packets per warp step
-    const int pk_lanes = 32 * (o.packets_per_step ? o.packets_per_step : 2);
+    float t_sweep = 0.f, tcl = 0.f, tlv = 0.f, tasm = 0.f, t_tr = 0.f;
+    // the packed kernels take whole warps per packet: 32 lanes x packets per warp step; unless given, the
+    // forward solve's autotuned choice for this mesh (one packet per step on narrow levels, two on wide)
+    const int* tuned = c->tuned[0][G][OPF_PACKETS];
+    const int pk_lanes = o.packets_per_step ? 32 * o.packets_per_step : (tuned[0] && tuned[2] >= 32 ? tuned[2] : 64);
+    const int pk_bpsm = o.blocks_per_sm ? o.blocks_per_sm : (tuned[0] ? tuned[3] : 0);
     int n_sweeps = it_fwd, it_adj = 0;
     bool conv_adj = true;
     double res_adj = 0.0;
@@ -1554,8 +1557,8 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
             int pI = !signI;
             SweepArgs a = make_args(c, *L, prec, cm, c->adjI, nullptr, G, pI, 0, 0, &o);
             a.debug_stall = 0;
-            s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, a.pk ? pk_lanes : lanes, 0, a,
-                          bc32, &t_sweep);
+            s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, a.pk ? pk_lanes : lanes,
+                          a.pk ? pk_bpsm : 0, a, bc32, &t_sweep);
             if (s != SWEEP_OK) return s;
             signI = pI;
             ++n_sweeps;
@@ -1570,8 +1573,11 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
             int pL = !signL[kl];
             SweepArgs r = make_args(c, *L, prec, cm, lbuf[kl], pbc ? lbuf[1 - kl] : nullptr, 2 * G, pL, 1, 0, &o);
             r.debug_stall = 0;
-            s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, r.pk ? pk_lanes : lanes, 0, r,
-                          nullptr, &t_sweep);
+            float t1 = 0.f;
+            s = run_sweep(c, *L, prec, plain ? SWEEP_SCHED_PLAIN : sched, threads, r.pk ? pk_lanes : lanes,
+                          r.pk ? pk_bpsm : 0, r, nullptr, &t1);
+            t_sweep += t1;
+            t_tr += t1;
             if (s != SWEEP_OK) return s;
             signL[kl] = pL;
             ++n_sweeps;
@@ -1615,6 +1621,7 @@ sweep_status adjoint_impl(sweep_ctx* c, const sweep_opts* opts_in, const double*
     S.t_ms[2] = t_sweep;
     S.t_ms[4] = ttot;
     S.t_ms[5] = tasm;  // forward and transposed operators
+    S.t_ms[6] = t_tr;  // the transposed sweeps alone
     S.updates = (double)N * D * G * (it_fwd + 2.0 * it_adj);  // forward, transposed over 2G split groups
     {
         const Levels& Ld = B == D ? c->lev : c->adj_lev;  // depths of the (last) batch levelised
