@@ -146,6 +146,14 @@ __device__ __forceinline__ float ld_relaxed_keep_if(const float* p, bool on, flo
                  : "+f"(v) : "l"(p), "r"((unsigned)on));
     return v;
 }
+__device__ __forceinline__ void ld_relaxed_keep_v2_if(const float* p, bool on, float* x) {
+    asm volatile("{ .reg .pred q; setp.ne.u32 q, %3, 0; @q ld.relaxed.gpu.global.v2.f32 {%0, %1}, [%2]; }"
+                 : "+f"(x[0]), "+f"(x[1]) : "l"(p), "r"((unsigned)on));
+}
+__device__ __forceinline__ void ld_relaxed_keep_v4_if(const float* p, bool on, float* x) {
+    asm volatile("{ .reg .pred q; setp.ne.u32 q, %5, 0; @q ld.relaxed.gpu.global.v4.f32 {%0, %1, %2, %3}, [%4]; }"
+                 : "+f"(x[0]), "+f"(x[1]), "+f"(x[2]), "+f"(x[3]) : "l"(p), "r"((unsigned)on));
+}
 // read-only data of the launch (not written by the kernel itself)
 __device__ __forceinline__ float4 ld_nc_v4_if(const void* p, bool on) {
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);

@@ -1091,22 +1091,34 @@ __device__ __forceinline__ void pk_decode(const SweepArgs& a, const int4 s, cons
     }
 }
 
+// any of a slot's GC values lacks this sweep's parity
+template <int GC>
+__device__ __forceinline__ bool pk_slot_unready(const float* x, uint32_t par) {
+    uint32_t m = 0u;
+#pragma unroll
+    for (int g = 0; g < GC; ++g) m |= __float_as_uint(x[g]) ^ par;
+    return m >> 31;
+}
+
 // sign bit of any gathered interior value differs from this sweep's parity: not written yet
 template <int GC>
 __device__ __forceinline__ bool pk_unready(const PkLane<GC>& t, uint32_t par) {
-    bool nr = false;
-#pragma unroll
-    for (int g = 0; g < GC; ++g) {
-        nr |= t.h0 && t.in0 && ((__float_as_uint(t.x0[g]) ^ par) >> 31);
-        nr |= t.h1 && t.in1 && ((__float_as_uint(t.x1[g]) ^ par) >> 31);
-    }
-    return nr;
+    return (t.h0 && t.in0 && pk_slot_unready<GC>(t.x0, par)) | (t.h1 && t.in1 && pk_slot_unready<GC>(t.x1, par));
+}
+
+// re-read of a slot's GC values (one vector load) where `on`, keeping them otherwise
+template <int GC>
+__device__ __forceinline__ void pk_reload(const float* p, bool on, float* x) {
+    if constexpr (GC == 4) ld_relaxed_keep_v4_if(p, on, x);
+    else if constexpr (GC == 2) ld_relaxed_keep_v2_if(p, on, x);
+    else x[0] = ld_relaxed_keep_if(p, on, x[0]);
 }
 
 // The step's gathered interior values not yet written by this sweep: all of them are re-read together,
-// one round trip per poll, until every one carries this sweep's parity (a serial wait per value would
-// cost a round trip per value after its producer finished). Bounded: after spin_budget polls, or when
-// another warp has set the device error word, the step gives up and the error word is set.
+// one round trip per poll (a slot's GC values as one vector load), until every one carries this
+// sweep's parity (a serial wait per value would cost a round trip per value after its producer
+// finished). Bounded: after spin_budget polls, or when another warp has set the device error word, the
+// step gives up and the error word is set.
 template <int GC, int PK>
 __device__ __forceinline__ void pk_wait_all(const SweepArgs& a, PkLane<GC> (&t)[PK], uint32_t par, bool& fail) {
     const float* I = reinterpret_cast<const float*>(a.I);
@@ -1114,13 +1126,10 @@ __device__ __forceinline__ void pk_wait_all(const SweepArgs& a, PkLane<GC> (&t)[
         bool nr = false;
 #pragma unroll
         for (int p = 0; p < PK; ++p) {
-#pragma unroll
-            for (int g = 0; g < GC; ++g) {
-                const bool u0 = t[p].h0 && t[p].in0 && ((__float_as_uint(t[p].x0[g]) ^ par) >> 31);
-                const bool u1 = t[p].h1 && t[p].in1 && ((__float_as_uint(t[p].x1[g]) ^ par) >> 31);
-                t[p].x0[g] = ld_relaxed_keep_if(I + (size_t)(uint32_t)t[p].s.x * GC + g, u0, t[p].x0[g]);
-                t[p].x1[g] = ld_relaxed_keep_if(I + (size_t)(uint32_t)t[p].s.z * GC + g, u1, t[p].x1[g]);
-            }
+            const bool u0 = t[p].h0 && t[p].in0 && pk_slot_unready<GC>(t[p].x0, par);
+            const bool u1 = t[p].h1 && t[p].in1 && pk_slot_unready<GC>(t[p].x1, par);
+            pk_reload<GC>(I + (size_t)(uint32_t)t[p].s.x * GC, u0, t[p].x0);
+            pk_reload<GC>(I + (size_t)(uint32_t)t[p].s.z * GC, u1, t[p].x1);
         }
 #pragma unroll
         for (int p = 0; p < PK; ++p) nr |= pk_unready<GC>(t[p], par);
