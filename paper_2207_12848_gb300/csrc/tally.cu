@@ -327,17 +327,26 @@ __global__ void k_scat_residual(int64_t NG, const double* J, double* Jold, unsig
     if (e > 0.0) atomicMax(dmax, (unsigned long long)__double_as_longlong(e));
 }
 
-__global__ void k_reduce_sum(const double* partial, int n, double* out) {
-    __shared__ double s0[256], s1[256];
-    double a = 0.0, b = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        a += partial[2 * i];
-        b += partial[2 * i + 1];
+// sum of n pairs in a fixed order: 1024 threads, four independent accumulators each (elements i + u T,
+// u = 0..3, then every 4T), combined pairwise, then a shared-memory tree
+__global__ void __launch_bounds__(1024) k_reduce_sum(const double* partial, int n, double* out) {
+    __shared__ double s0[1024], s1[1024];
+    const int T = blockDim.x;
+    double a[4] = {0.0, 0.0, 0.0, 0.0}, b[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < n; i += 4 * T) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = i + u * T;
+            if (j < n) {
+                a[u] += partial[2 * j];
+                b[u] += partial[2 * j + 1];
+            }
+        }
     }
-    s0[threadIdx.x] = a;
-    s1[threadIdx.x] = b;
+    s0[threadIdx.x] = (a[0] + a[1]) + (a[2] + a[3]);
+    s1[threadIdx.x] = (b[0] + b[1]) + (b[2] + b[3]);
     __syncthreads();
-    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    for (int off = T / 2; off > 0; off >>= 1) {
         if (threadIdx.x < off) {
             s0[threadIdx.x] += s0[threadIdx.x + off];
             s1[threadIdx.x] += s1[threadIdx.x + off];
@@ -539,7 +548,7 @@ cudaError_t launch_periodic_source(int precision, const DevMesh& m, const void* 
 }
 
 cudaError_t launch_reduce_sum(const double* partial, int n, double* out, cudaStream_t st) {
-    k_reduce_sum<<<1, 256, 0, st>>>(partial, n, out);
+    k_reduce_sum<<<1, 1024, 0, st>>>(partial, n, out);
     return cudaGetLastError();
 }
 
