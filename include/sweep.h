@@ -66,9 +66,10 @@ enum {
  *   EXP:     P I = exp(-tau) F_in + q (the source leaves unattenuated), and J is formed from the
  *            cell-mean intensity (F_in / P)(1 - exp(-tau)) / tau, so that kappa_t V times it is the
  *            removed flux; with kappa_a = 0 the scattered fraction is 1 - exp(-kappa_s V / P), the
- *            scattering law of Sec. 3.3. Forward solves only (the adjoint takes BALANCE). EXP runs in
- *            the kernels that read the mesh rows (not the assembled operator), on the DATAFLOW schedule
- *            when the schedule is AUTO (no autotuning), and keeps one more [D][N][G] array. */
+ *            scattering law of Sec. 3.3. Forward solves only (the adjoint takes BALANCE). In FP32 EXP
+ *            runs over the packed operator (1, 2 or 4 groups; otherwise, and in FP64, in the kernels that
+ *            read the mesh rows), on the DATAFLOW schedule when the schedule is AUTO (no autotuning),
+ *            and keeps one more [D][N][G] array. */
 enum { SWEEP_LAW_BALANCE = 0, SWEEP_LAW_EXP = 1 };
 
 typedef struct {
@@ -111,7 +112,9 @@ typedef struct {
 } sweep_opts;
 
 /* Forms of the assembled transport operator (the rows of L_Omega, Sec. 2.3, built once per
- * levelisation and streamed by every FP32 forward BALANCE sweep of the solve):
+ * levelisation and streamed by every FP32 sweep of the solve; the EXP law and scheme (b) take PACKETS
+ * only, and the FP32 adjoint streams a packed transposed operator, the rows of L_Omega^T with the
+ * levels in reverse order, for 2G = 2 or 4 split groups):
  *   AUTO:    PACKETS where they apply (1, 2 or 4 groups, n_cells x n_dir <= 2^31, lanes_per_task 0),
  *            else LINES;
  *   LINES:   one 128-byte line per task (header + 14 entry slots), lanes_per_task lanes per task;
@@ -147,12 +150,13 @@ typedef struct {
 enum {
     SWEEP_KERNEL_NONE = 0,
     SWEEP_KERNEL_PLAIN = 1,          /* one launch per (direction, level), FP64 */
-    SWEEP_KERNEL_GEOMETRY = 2,       /* lane groups reading the mesh rows (FP64, and every adjoint sweep) */
+    SWEEP_KERNEL_GEOMETRY = 2,       /* lane groups reading the mesh rows (FP64; FP32 adjoint or EXP without packets) */
     SWEEP_KERNEL_RECORDS = 3,        /* FP32 forward, lane groups over task records and mesh rows */
     SWEEP_KERNEL_OPERATOR = 4,       /* FP32 forward over the assembled operator, lane groups */
     SWEEP_KERNEL_OPERATOR_LEAN = 5,  /* the same, one group and 8 lanes per task, dataflow schedule */
     SWEEP_KERNEL_OPERATOR_PAIR = 6,  /* the same with two tasks per 8-lane group per step */
-    SWEEP_KERNEL_PACKED = 7          /* FP32 forward over the packed operator (whole warps per packet of tasks) */
+    SWEEP_KERNEL_PACKED = 7          /* FP32 over the packed operator, forward (BALANCE or EXP) or transposed
+                                        (whole warps per packet of tasks) */
 };
 
 /* Fill *opts with defaults: precision 32, AUTO schedule, tolerances 1e-6, 100 iterations. */
