@@ -55,3 +55,25 @@ def test_step_text_names_the_loops():
     assert "fused" in bench.step_text(p, 1)
     q = configs.Problem("box", lattice_mesh(4), np.zeros((1, 3)), np.ones(1), one, 0 * one)
     assert bench.step_text(q, 1).endswith("one sweep")
+
+
+def test_roofline_over_sweeps_of_different_widths():
+    # the adjoint's roofline: per sweep every task reads its row once, per update 12 bytes; with sweeps
+    # of one width it is the per-launch roofline, and a transposed sweep over 2G groups adds only the
+    # per-update bytes of its extra groups
+    n = 6
+    m = lattice_mesh(n, periodic=True)
+    G, D = 2, 3
+    p = configs.Problem("lattice", m, np.zeros((D, 3)), np.ones(D), np.ones((m.n_cells, G)),
+                        np.zeros((m.n_cells, G)))
+    peaks = {"hbm_gbs": 1000.0, "source": "test"}
+    one = bench._roof(p, 2.0, peaks, "k")
+    upd = m.n_cells * D * G
+    same = bench._roof_sweeps(p, 6.0, 3, 3.0 * upd, peaks, "k")
+    assert same["achieved"] == pytest.approx(one["achieved"])
+    assert same["bytes_per_update"] == pytest.approx(one["bytes_per_update"])
+    assert same["avg_launch_ms"] == pytest.approx(2.0)
+    mixed = bench._roof_sweeps(p, 4.0, 2, 3.0 * upd, peaks, "k")  # one sweep over G, one over 2G
+    row = m.n_cells * D * (8.0 + 16.0 * 6.0)
+    assert mixed["achieved"] * 1e9 * 4.0e-3 == pytest.approx(2 * row + 12.0 * 3.0 * upd)
+    assert mixed["frac"] == pytest.approx(mixed["achieved"] / 1000.0)
